@@ -1,0 +1,423 @@
+"""Pins of the CPU oracle against facts outside itself (no GPU).
+
+Each test pins one part of the oracle (the paper's Eq. nabla_loss and
+Algorithm 1) to something the paper or mathematics fixes: exact integer
+products, rational arithmetic, finite differences, closed-form singular
+values, dense SVD, the explicit-sum form of Adam's moment recursions and
+invariances of the loss.  ``test_mutants_are_caught`` plants mistakes in a
+copy of the oracle source and checks that these pins catch each one.
+"""
+import json
+import math
+from fractions import Fraction
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2409_11515_gb300 import synth
+
+GOLDEN = Path(__file__).resolve().parent / "golden"
+CF = json.loads((GOLDEN / "closed_forms.json").read_text())
+B1, B2, LR, EPS = 0.9, 0.999, 1e-2, 1e-12
+
+
+def _int_matrix(m, n, seed, density=0.4):
+    rng = np.random.default_rng(seed)
+    M = rng.integers(-9, 10, size=(m, n)).astype(np.float64)
+    M[rng.random((m, n)) > density] = 0.0
+    return M
+
+
+# ----------------------------------------------------------------- RNG ---
+
+def test_splitmix64_known_answers():
+    for line in (GOLDEN / "splitmix64_seed0.txt").read_text().splitlines():
+        if not line or line.startswith("#"):
+            continue
+        i, hx = line.split()
+        assert oracle.splitmix64_at(0, int(i)) == int(hx, 16)
+
+
+def test_start_vector_unit_and_uniform():
+    x = oracle.start_vector(100000, 42)
+    assert abs(np.linalg.norm(x) - 1.0) < 1e-14
+    # raw entries 2u-1 are uniform on [-1, 1): check mean / second moment
+    raw = x * np.sqrt(100000 / 3.0) * (1.0 / np.sqrt(np.mean((x * np.sqrt(100000 / 3.0)) ** 2)))
+    assert abs(np.mean(raw)) < 0.02
+    assert not np.array_equal(oracle.start_vector(1000, 1), oracle.start_vector(1000, 2))
+
+
+# ------------------------------------------------------------ products ---
+
+@pytest.mark.parametrize("shape", [(7, 7), (13, 5), (5, 13), (40, 40)])
+def test_spmv_exact_on_integers(shape):
+    M = _int_matrix(*shape, seed=sum(shape))
+    A = synth.from_coo(*np.nonzero(M), M[np.nonzero(M)], *shape)
+    x = np.random.default_rng(1).integers(-50, 50, shape[1]).astype(np.float64)
+    y = np.random.default_rng(2).integers(-50, 50, shape[0]).astype(np.float64)
+    assert np.array_equal(oracle.spmv(A, x), M @ x)
+    assert np.array_equal(oracle.spmv_t(A, y), M.T @ y)
+
+
+def test_spmv_empty_rows_and_columns():
+    M = np.zeros((6, 6))
+    M[1, 2] = 3.0
+    M[4, 0] = -2.0
+    A = synth.from_coo(*np.nonzero(M), M[np.nonzero(M)], 6, 6)
+    x = np.arange(1.0, 7.0)
+    assert np.array_equal(oracle.spmv(A, x), M @ x)
+    assert np.array_equal(oracle.spmv_t(A, x), M.T @ x)
+
+
+def test_dd_products_match_rational_arithmetic():
+    # rows built to cancel: terms of size 1e16 summing to O(1)
+    rng = np.random.default_rng(5)
+    n = 12
+    x = rng.uniform(0.5, 1.5, n)
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        big = rng.uniform(1, 2) * 1e16
+        c = [(i + k) % n for k in range(4)]
+        rows += [i, i, i, i]
+        cols += c
+        # the first two products cancel to within their own rounding error
+        vals += [big, -big * x[c[0]] / x[c[1]], rng.uniform(-1, 1), rng.uniform(-1, 1) * 1e-8]
+    A = synth.from_coo(rows, cols, vals, n, n)
+    hi, lo = oracle.spmv(A, x, dd=True)
+    plain = oracle.spmv(A, x)
+    for i in range(n):
+        exact = sum(Fraction(A.val[k]) * Fraction(x[A.col[k]])
+                    for k in range(A.row_ptr[i], A.row_ptr[i + 1]))
+        ref = float(exact)
+        # Dot2: |hi - exact| <= u|exact| + gamma^2 * sum|terms|  (tiny here)
+        terms = sum(abs(A.val[k] * x[A.col[k]]) for k in range(A.row_ptr[i], A.row_ptr[i + 1]))
+        assert abs(hi[i] - ref) <= 2.3e-16 * abs(ref) + 1e-30 * terms + 1e-300
+        assert abs(Fraction(hi[i]) + Fraction(lo[i]) - exact) <= Fraction(1e-28) * Fraction(terms)
+    # plain FP64 loses most digits on these rows, so the test does separate them
+    assert np.max(np.abs(plain - hi) / np.abs(hi)) > 1e-6
+    # transposed dd product against rational arithmetic
+    z = oracle.spmv_t(A, hi, lo)
+    for j in range(n):
+        exact = Fraction(0)
+        for i in range(n):
+            for k in range(A.row_ptr[i], A.row_ptr[i + 1]):
+                if A.col[k] == j:
+                    exact += Fraction(A.val[k]) * (Fraction(hi[i]) + Fraction(lo[i]))
+        assert abs(z[j] - float(exact)) <= 4.5e-16 * abs(float(exact)) + 1e-300
+
+
+# ------------------------------------------------------------ gradient ---
+
+@pytest.mark.parametrize("mode", [oracle.SIGMA_MAX, oracle.SIGMA_MIN])
+@pytest.mark.parametrize("loss", [oracle.LOSS_LOGRATIO, oracle.LOSS_QUADRATIC])
+def test_gradient_matches_finite_differences(mode, loss):
+    rng = np.random.default_rng(3)
+    M = rng.standard_normal((9, 7))
+    A = synth.dense_csr(M)
+    x = rng.standard_normal(7)
+
+    def L(v):  # the loss as defined in the paper (and its negation / the quadratic reading)
+        if loss == oracle.LOSS_LOGRATIO:
+            val = math.log(np.linalg.norm(v)) - math.log(np.linalg.norm(M @ v))
+            return val if mode == oracle.SIGMA_MAX else -val
+        q = float(np.dot(M @ v, M @ v))
+        return -q if mode == oracle.SIGMA_MAX else q
+
+    Lo, g = oracle.loss_grad(A, x, mode, loss)
+    assert abs(Lo - L(x)) <= 1e-13 * max(1.0, abs(L(x)))
+    h = 1e-6
+    fd = np.array([(L(x + h * e) - L(x - h * e)) / (2 * h) for e in np.eye(7)])
+    assert np.allclose(g, fd, rtol=1e-6, atol=1e-8 * np.max(np.abs(fd)))
+
+
+def test_logratio_gradient_is_tangent():
+    # L is scale invariant, so x . grad L(x) = 0 (Euler's theorem, degree 0)
+    rng = np.random.default_rng(8)
+    A = synth.random_sparse(50, 5, seed=8, diag_boost=3.0)
+    x = rng.standard_normal(50)
+    _, g = oracle.loss_grad(A, x, oracle.SIGMA_MAX)
+    assert abs(np.dot(x, g)) <= 1e-13 * np.linalg.norm(x) * np.linalg.norm(g)
+
+
+# ------------------------------------------------ Adam steps, explicitly ---
+
+def _fd_grad(M, v, mode):
+    def L(u):
+        val = math.log(np.linalg.norm(u)) - math.log(np.linalg.norm(M @ u))
+        return val if mode == oracle.SIGMA_MAX else -val
+    h = 1e-6
+    return np.array([(L(v + h * e) - L(v - h * e)) / (2 * h) for e in np.eye(v.size)])
+
+
+@pytest.mark.parametrize("mode", [oracle.SIGMA_MAX, oracle.SIGMA_MIN])
+def test_first_five_steps_match_explicit_adam(mode):
+    """x_t from the closed (explicit-sum) form of Adam's moments with
+    finite-difference gradients: m_t = (1-b1) sum_k b1^(t-k) g_k, likewise v_t
+    with g_k^2, bias-corrected by 1 - b^t; then the tangent projection and the
+    normalisation of Algorithm 1."""
+    rng = np.random.default_rng(21)
+    M = rng.standard_normal((8, 8)) + 2 * np.eye(8)
+    A = synth.dense_csr(M)
+    x0 = oracle.start_vector(8, 9)
+    T = 5
+    r = oracle.projected_adam(A, mode, T, LR, B1, B2, EPS, x_init=x0, n_trace=T)
+    xs = [x0] + [r.x_trace[t] for t in range(T)]
+    gs = []
+    for t in range(1, T + 1):
+        x = xs[t - 1]
+        gs.append(_fd_grad(M, x, mode))
+        assert np.min(np.abs(gs[-1])) > 1e-5  # well away from FD noise and eps
+        w1 = np.array([B1 ** (t - k) for k in range(1, t + 1)])
+        w2 = np.array([B2 ** (t - k) for k in range(1, t + 1)])
+        G = np.array(gs)
+        mh = (1 - B1) * (w1 @ G) / (1 - B1 ** t)
+        vh = (1 - B2) * (w2 @ (G * G)) / (1 - B2 ** t)
+        dx = LR * mh / (np.sqrt(vh) + EPS)
+        dx = dx - np.dot(x, dx) * x
+        xn = x - dx
+        xn = xn / np.linalg.norm(xn)
+        assert np.max(np.abs(xn - xs[t])) < 1e-8, t
+    # t = 1 is projected sign descent: |dx_i| = LR for every coordinate
+    d1 = LR * np.sign(gs[0])
+    x1 = x0 - (d1 - np.dot(x0, d1) * x0)
+    assert np.max(np.abs(x1 / np.linalg.norm(x1) - xs[1])) < 1e-10
+
+
+# ------------------------------------------------------- closed forms ---
+
+@pytest.mark.parametrize("case", CF["lap1d"], ids=lambda c: f"n{c['n']}")
+def test_laplacian_1d_kappa(case):
+    A = synth.laplacian_1d(case["n"])
+    r = oracle.estimate(A, 3000, 3000, seed=1)
+    assert r["status_max"] == 0 and r["status_min"] == 0
+    assert abs(r["sigma_max"] / case["sigma_max"] - 1) < 1e-6
+    assert abs(r["sigma_min"] / case["sigma_min"] - 1) < 1e-6
+    assert abs(r["kappa"] / case["kappa"] - 1) < 1e-6
+
+
+@pytest.mark.parametrize("case", CF["lap2d"], ids=lambda c: f"N{c['N']}")
+def test_laplacian_2d_kappa(case):
+    A = synth.laplacian_2d(case["N"])
+    r = oracle.estimate(A, 3000, 3000, seed=3)
+    assert abs(r["kappa"] / case["kappa"] - 1) < 1e-6
+    assert abs(r["sigma_max"] / case["sigma_max"] - 1) < 1e-6
+
+
+@pytest.mark.parametrize("case", CF["two_by_two"], ids=["a", "b"])
+def test_two_by_two(case):
+    A = synth.dense_csr(np.array(case["M"]))
+    r = oracle.estimate(A, 2000, 2000, seed=4)
+    assert abs(r["sigma_max"] / case["sigma_max"] - 1) < 1e-9
+    assert abs(r["sigma_min"] / case["sigma_min"] - 1) < 1e-9
+
+
+def test_diagonal_exact():
+    rng = np.random.default_rng(0)
+    d = rng.uniform(0.5, 2.0, 50) * np.where(rng.random(50) < 0.5, -1, 1)
+    r = oracle.estimate(synth.diag_csr(d), 5000, 5000, seed=5)
+    assert abs(r["sigma_max"] / np.max(np.abs(d)) - 1) < 1e-9
+    assert abs(r["sigma_min"] / np.min(np.abs(d)) - 1) < 1e-9
+
+
+def test_scalar_identity_never_moves():
+    # A = c I: the log-ratio gradient vanishes up to round-off (|g| ~ 1e-16,
+    # far below eps = 1e-12), so each step moves x by at most ~lr*|g|/eps and
+    # every iterate scores sigma = |c|
+    A = synth.diag_csr(np.full(30, -3.0))
+    x0 = oracle.start_vector(30, 2)
+    _, g = oracle.loss_grad(A, x0, oracle.SIGMA_MAX)
+    assert np.max(np.abs(g)) < 1e-15
+    r = oracle.projected_adam(A, oracle.SIGMA_MAX, 50, x_init=x0)
+    assert np.max(np.abs(r.x_last - x0)) < 50 * LR * 1e-15 / EPS
+    assert abs(r.sigma - 3.0) < 1e-15
+
+
+def test_pow2_identity_exact_fixed_point_and_earliest_minimum():
+    # A = 2 I: A^T A x = 4x and ||Ax||^2 = 4||x||^2 exactly, so the log-ratio
+    # gradient is exactly 0, Adam's step is 0/(0 + eps) = 0, x never moves and
+    # every iterate ties in L; the strict "<" of Algorithm 1 keeps t_min = 1.
+    A = synth.diag_csr(np.full(16, 2.0))
+    x0 = oracle.start_vector(16, 4)
+    _, g = oracle.loss_grad(A, x0, oracle.SIGMA_MAX)
+    assert np.all(g == 0.0)
+    r = oracle.projected_adam(A, oracle.SIGMA_MAX, 20, x_init=x0, trace_L=True)
+    assert np.array_equal(r.x_last, x0)
+    assert np.all(r.L_trace == r.L_trace[0])
+    assert r.t_min == 1
+    assert r.sigma == 2.0
+
+
+@pytest.mark.parametrize("n", [20, 60, 120])
+def test_dense_svd_sigma_max(n):
+    rng = np.random.default_rng(n)
+    U, _, Vt = np.linalg.svd(rng.standard_normal((n, n)))
+    S = np.logspace(0, 2, n)[::-1]
+    M = (U * S) @ Vt
+    r = oracle.projected_adam(synth.dense_csr(M), oracle.SIGMA_MAX, 2000, seed=11)
+    assert abs(r.sigma / S[0] - 1) < 1e-9
+
+
+def test_dense_svd_sigma_min_small():
+    rng = np.random.default_rng(20)
+    U, _, Vt = np.linalg.svd(rng.standard_normal((20, 20)))
+    S = np.logspace(0, 1, 20)[::-1]
+    M = (U * S) @ Vt
+    r = oracle.projected_adam(synth.dense_csr(M), oracle.SIGMA_MIN, 5000, seed=11)
+    assert abs(r.sigma / S[-1] - 1) < 1e-6
+
+
+# --------------------------------------------------------- invariants ---
+
+def test_unit_norm_and_tracking_invariants():
+    A = synth.hydro_operator(9, seed=3)
+    for mode in (oracle.SIGMA_MAX, oracle.SIGMA_MIN):
+        r = oracle.projected_adam(A, mode, 300, seed=7, n_trace=300, trace_L=True)
+        norms = np.linalg.norm(r.x_trace, axis=1)
+        assert np.max(np.abs(norms - 1)) < 1e-14
+        L = r.L_trace
+        assert r.L_min == np.min(L)
+        assert r.t_min == int(np.argmin(L)) + 1  # earliest minimum (strict "<")
+        assert np.array_equal(r.x_min, r.x_trace[r.t_min - 1])
+
+
+def test_objective_monotone_after_warmup_on_closed_form():
+    A = synth.laplacian_1d(8)
+    r = oracle.projected_adam(A, oracle.SIGMA_MAX, 1500, seed=1, trace_L=True)
+    L = r.L_trace[200:]
+    # L decreases to its floor; any rise after warm-up stays at round-off level
+    assert np.all(np.diff(L) <= 1e-12 * np.abs(L[1:]) + 1e-15)
+
+
+def test_pow2_scaling_gives_identical_iterates():
+    A = synth.hydro_operator(7, seed=2)
+    B = synth.CSR(A.row_ptr, A.col, A.val * 2.0 ** 37, A.n_rows, A.n_cols)
+    for mode in (oracle.SIGMA_MAX, oracle.SIGMA_MIN):
+        ra = oracle.projected_adam(A, mode, 200, seed=3)
+        rb = oracle.projected_adam(B, mode, 200, seed=3)
+        assert np.array_equal(ra.x_last, rb.x_last)
+        assert rb.sigma == ra.sigma * 2.0 ** 37
+
+
+def test_transpose_and_permutation_invariance():
+    A = synth.laplacian_2d(4)
+    D = synth.csr_to_dense(A)
+    rng = np.random.default_rng(2)
+    D = D + np.diag(rng.uniform(0, 1, 16)) + 0.3 * np.triu(rng.standard_normal((16, 16)), 1)
+    perm = rng.permutation(16)
+    s = np.linalg.svd(D, compute_uv=False)
+    for M in (D, D.T, D[perm][:, perm]):
+        r = oracle.projected_adam(synth.dense_csr(M), oracle.SIGMA_MAX, 3000, seed=5)
+        assert abs(r.sigma / s[0] - 1) < 1e-9
+
+
+def test_rayleigh_sandwich_on_hydro():
+    A = synth.hydro_operator(21, seed=1)
+    M = synth.csr_to_dense(A)
+    smax = np.linalg.svd(M, compute_uv=False)[0]
+    cn = np.linalg.norm(M, axis=0)
+    rmax = oracle.projected_adam(A, oracle.SIGMA_MAX, 2000, seed=1)
+    rmin = oracle.projected_adam(A, oracle.SIGMA_MIN, 2000, seed=1)
+    # sigma_max converges; sigma_min is an upper bound, below every column norm
+    assert abs(rmax.sigma / smax - 1) < 1e-6
+    assert rmax.sigma >= np.max(cn) * (1 - 1e-15)
+    assert rmax.sigma <= math.sqrt(np.max(np.abs(M).sum(0)) * np.max(np.abs(M).sum(1)))
+    assert rmin.sigma <= np.max(cn)
+    assert rmin.sigma > 0
+
+
+def test_singular_matrix_status():
+    M = np.array([[1.0, 2.0], [2.0, 4.0]])
+    A = synth.dense_csr(M)
+    # start exactly in the null space: sigma_min = 0 at x_init
+    x0 = np.array([2.0, -1.0]) / math.sqrt(5)
+    r = oracle.projected_adam(A, oracle.SIGMA_MIN, 10, x_init=x0)
+    assert r.status == oracle.SINGULAR and r.sigma == 0.0 and r.t_min == 0
+    Z = synth.CSR(np.zeros(4, np.int32), np.zeros(0, np.int32), np.zeros(0), 3, 3)
+    r = oracle.projected_adam(Z, oracle.SIGMA_MAX, 10, seed=1)
+    assert r.status == oracle.SINGULAR
+
+
+def test_nonfinite_status():
+    A = synth.diag_csr([1.0, np.nan, 2.0])
+    r = oracle.projected_adam(A, oracle.SIGMA_MAX, 10, seed=1)
+    assert r.status == oracle.NONFINITE
+
+
+# ------------------------------------------------------ equilibration ---
+
+def test_equilibration_pow2_exact():
+    A = synth.hydro_operator(9, seed=4)
+    dr, dc, vh = oracle.equilibrate_pow2(A)
+    for d in (dr, dc):
+        m, e = np.frexp(d)
+        assert np.all(m == 0.5)
+    rows = np.repeat(np.arange(A.n_rows), np.diff(A.row_ptr))
+    # exact reconstruction (powers of two)
+    assert np.array_equal(vh * dr[rows] * dc[A.col], A.val)
+    M = synth.csr_to_dense(A)
+    rn = np.linalg.norm(M, axis=1)
+    ratio = rn / dr
+    assert np.all(ratio >= 2 ** -0.5 - 1e-12) and np.all(ratio <= 2 ** 0.5 + 1e-12)
+    cn = np.linalg.norm(M / dr[:, None], axis=0)
+    ratio = cn / dc
+    assert np.all(ratio >= 2 ** -0.5 - 1e-12) and np.all(ratio <= 2 ** 0.5 + 1e-12)
+
+
+# ---------------------------------------------- planted-mistake checks ---
+
+MUTANTS = {
+    "no_bias_correction": ("double mh = m[i] / bc1;", "double mh = m[i];"),
+    "gradient_sign": ("gi = x[i] / q - z[i] / s;", "gi = x[i] / q + z[i] / s;"),
+    "transposed_operand": ("z[col[k]] = z[col[k]] + val[k] * y[i];",
+                           "z[i % n_cols] = z[i % n_cols] + val[k] * y[col[k] % n_rows];"),
+    "betas_swapped": ("m[i] = beta1 * m[i] + (1.0 - beta1) * g[i];",
+                      "m[i] = beta2 * m[i] + (1.0 - beta2) * g[i];"),
+    "no_projection": ("for (int64_t i = 0; i < n; ++i) dx[i] = dx[i] - c * x[i];",
+                      "for (int64_t i = 0; i < n; ++i) dx[i] = dx[i] - 0.0 * c * x[i];"),
+    "sqrt_dropped": ("dx[i] = lr * mh / (sqrt(vh) + eps);", "dx[i] = lr * mh / (vh + eps);"),
+    "score_before_update": ("if (L < L_min) {", "if (L <= L_min) {"),
+}
+
+
+def _pins_pass():
+    """A compact run of the pins above, used against a mutated oracle."""
+    checks = []
+    try:
+        test_first_five_steps_match_explicit_adam(oracle.SIGMA_MAX)
+        checks.append(True)
+    except AssertionError:
+        checks.append(False)
+    try:
+        test_gradient_matches_finite_differences(oracle.SIGMA_MAX, oracle.LOSS_LOGRATIO)
+        checks.append(True)
+    except AssertionError:
+        checks.append(False)
+    try:
+        test_unit_norm_and_tracking_invariants()
+        checks.append(True)
+    except AssertionError:
+        checks.append(False)
+    try:
+        test_spmv_exact_on_integers((13, 5))
+        checks.append(True)
+    except AssertionError:
+        checks.append(False)
+    try:
+        test_pow2_identity_exact_fixed_point_and_earliest_minimum()
+        checks.append(True)
+    except AssertionError:
+        checks.append(False)
+    return all(checks)
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutants_are_caught(name, tmp_path):
+    src = oracle.source_text()
+    old, new = MUTANTS[name]
+    assert src.count(old) == 1, name
+    lib = oracle.load(oracle.compile_variant(src.replace(old, new), tmp_path / f"{name}.so"))
+    with oracle.using(lib):
+        assert not _pins_pass(), f"mutant {name} survived the pins"
+    assert _pins_pass()  # the real oracle passes the same checks
