@@ -1,0 +1,322 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 Projected Adam estimator (one JSON line on rank 0).
+
+Workload: the 401 x 401-cell hydro-mechanical operator (964,806 rows, six
+unknowns per cell, 8 inclusions, viscosity 1e18..1e24 Pa s, seed 2), FP64
+throughout, one seeded start vector; one step = one kappa_2 estimate =
+5000 Projected Adam iterations for sigma_max plus 20000 for sigma_min.
+Metric: Projected Adam iterations per second (whole job).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the plain serial FP64 program under
+oracle/) on a bounded sample of the same workload.  Under torchrun with N > 1
+every rank runs an independent replica (the estimate does not shard).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "projected_adam_iterations_per_s"
+UNIT = "iterations/s"
+WORKLOAD = dict(nx=401, ny=401, n_incl=8, eta_lo=1e18, eta_hi=1e24, seed=2)
+ITERS_MAX, ITERS_MIN = 5000, 20000  # per kappa_2 estimate (overridable for profiling)
+HYPER = dict(lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-12)
+START_SEED = 1
+
+
+def _peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def bytes_per_iteration(n_rows, n_cols, nnz):
+    """Algorithmic bytes of one FP64 iteration: A and A^T read once
+    (12 B per entry + 4 B per row pointer) and nine 8-byte vector streams
+    per row (x gather, y write, y gather, x read, m r/w, v r/w, x write)."""
+    return 2 * (12 * nnz + 4 * (n_rows + 1)) + 72 * n_cols
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2409_11515_gb300 import synth
+    A = synth.hydro_operator(WORKLOAD["nx"], WORKLOAD["ny"], n_incl=WORKLOAD["n_incl"],
+                             eta_lo=WORKLOAD["eta_lo"], eta_hi=WORKLOAD["eta_hi"],
+                             seed=WORKLOAD["seed"])
+    oracle.build()
+    x0 = oracle.start_vector(A.n_cols, START_SEED)
+    sample = 40  # iterations per sigma mode per step: a bounded slice of the estimate
+    for _ in range(args.warmup):
+        oracle.projected_adam(A, oracle.SIGMA_MAX, 2, x_init=x0, **HYPER)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.projected_adam(A, oracle.SIGMA_MAX, sample, x_init=x0, **HYPER)
+        oracle.projected_adam(A, oracle.SIGMA_MIN, sample, x_init=x0, **HYPER)
+    dt = time.perf_counter() - t0
+    value = 2 * sample * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded hydro-mechanical operator generator)",
+        "config": _config(A),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{sample} sigma_max + {sample} sigma_min iterations per step "
+                                   "of the 401x401 operator (serial C, -O2, no FMA)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(A):
+    return {"workload": "hydro-mechanical 401x401 cells, 6 unknowns/cell, 964806 rows, "
+                        "kappa_2 estimate = 5000 sigma_max + 20000 sigma_min iterations",
+            "n_rows": int(A.n_rows), "nnz": int(A.nnz), "iters_sigma_max": ITERS_MAX,
+            "iters_sigma_min": ITERS_MIN, "precision": "fp64", "k": 1,
+            "l2": "working set larger than L2 (A + A^T + 9 vectors of 964806 rows = 231 MB > 129 MB)"}
+
+
+def cpu_baseline(A, x0):
+    import oracle
+    oracle.build()
+    it = 150
+    t0 = time.perf_counter()
+    oracle.projected_adam(A, oracle.SIGMA_MAX, it, x_init=x0, **HYPER)
+    oracle.projected_adam(A, oracle.SIGMA_MIN, it, x_init=x0, **HYPER)
+    dt = time.perf_counter() - t0
+    return {"value": 2 * it / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{it} sigma_max + {it} sigma_min iterations of the same operator "
+                      "(serial C oracle, one host core)"}
+
+
+def run_ours(args):
+    ws, rank, local = _dist()
+    import torch
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2409_11515_gb300 import build, pa, synth
+    if rank == 0 or ws == 1:
+        build.build()
+    _barrier(ws)
+    pa.load()
+    A = synth.hydro_operator(WORKLOAD["nx"], WORKLOAD["ny"], n_incl=WORKLOAD["n_incl"],
+                             eta_lo=WORKLOAD["eta_lo"], eta_hi=WORKLOAD["eta_hi"],
+                             seed=WORKLOAD["seed"])
+    stream = torch.cuda.Stream()
+    h = pa.create(A, stream=stream)
+    it_per_step = ITERS_MAX + ITERS_MIN
+
+    def step(handle):
+        handle.estimate(pa.SIGMA_MAX, ITERS_MAX, seed=START_SEED, **HYPER)
+        return handle.estimate(pa.SIGMA_MIN, ITERS_MIN, seed=START_SEED, **HYPER)
+
+    for _ in range(args.warmup):
+        r = step(h)
+    # ---- device-resident timed region
+    sampler = ClockSampler(local)
+    launches0 = h.launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    _barrier(ws)
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        r = step(h)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    _barrier(ws)
+    ms = ev0.elapsed_time(ev1)
+    ms = _max_over_ranks(ms, ws)
+    launches = h.launches() - launches0
+    value = ws * it_per_step * args.steps / (ms / 1e3)
+    # ---- roofline of the persistent kernel: per-launch time on its own stream
+    kms = []
+    for iters, mode in ((ITERS_MAX, pa.SIGMA_MAX), (ITERS_MIN, pa.SIGMA_MIN)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        x0 = None
+        e0.record(stream)
+        h.estimate(mode, iters, seed=START_SEED, **HYPER)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        kms.append((iters, e0.elapsed_time(e1)))
+    B = bytes_per_iteration(A.n_rows, A.n_cols, A.nnz)
+    tot_it = sum(i for i, _ in kms)
+    tot_ms = sum(t for _, t in kms)
+    achieved = B * tot_it / (tot_ms / 1e3) / 1e9
+    peak, peak_kind = _peaks()
+    h.destroy()
+    # ---- end to end through the C ABI with host buffers
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 2))
+    torch.cuda.synchronize()
+    _barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        with pa.create(A, stream=stream) as he:
+            he.estimate(pa.SIGMA_MAX, ITERS_MAX, seed=START_SEED, **HYPER)
+            re = he.estimate(pa.SIGMA_MIN, ITERS_MIN, seed=START_SEED, **HYPER)
+    torch.cuda.synchronize()
+    e2e_s = max(_max_over_ranks(time.perf_counter() - t0, ws), 1e-9)
+    h2d = A.row_ptr.nbytes + A.col.nbytes + A.val.nbytes + 16 * (ITERS_MAX + ITERS_MIN)
+    d2h = 2 * 96 + 4
+    if rank == 0:
+        prof = ROOT / "profiles" / "persistent_hydro401_traffic.json"
+        traffic = None
+        if prof.exists():
+            try:
+                traffic = json.loads(prof.read_text()).get("traffic_bytes_per_launch")
+            except ValueError:
+                traffic = None
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded hydro-mechanical operator generator)",
+            "config": dict(_config(A), parallelism=f"replicas{ws}" if ws > 1 else "single_gpu"),
+            "kappa_estimates_per_s": ws * args.steps / (ms / 1e3),
+            "result": {"sigma_max": r["sigma_max"], "sigma_min": r["sigma_min"],
+                       "kappa": r["kappa"], "status": r["status"]},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": f"{peak_kind} copy bandwidth",
+                         "kernel": "k_persistent (per-launch CUDA events on its stream)",
+                         "bytes_per_iteration": B},
+            "clocks": clocks,
+            "gpu_launches": launches,
+            "e2e": {"value": ws * it_per_step * e2e_steps / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        }
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(A, _start_vector_host(A.n_cols))
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def _start_vector_host(n):
+    import oracle
+    return oracle.start_vector(n, START_SEED)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    ap.add_argument("--iters-max", type=int, default=ITERS_MAX,
+                    help="sigma_max iterations per estimate (short runs for profiling)")
+    ap.add_argument("--iters-min", type=int, default=ITERS_MIN)
+    args = ap.parse_args()
+    globals()["ITERS_MAX"], globals()["ITERS_MIN"] = args.iters_max, args.iters_min
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

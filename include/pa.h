@@ -1,0 +1,186 @@
+/*
+ * pa.h -- C ABI of the GB300-native Projected Adam estimator of the L2
+ * condition number, kappa_2(A) = ||A||_2 ||A^-1||_2 = sigma_max / sigma_min
+ * (paper: section "Computing the condition number of a matrix", the identity
+ * kappa_2 = max sigma / min sigma, Theorem "Equivalent definitions of the L2
+ * matrix norm" and Eq. max_sup_equivalence, the loss and its gradient
+ * Eq. nabla_loss, and Algorithm 1 "Projected Adam Optimizer").
+ *
+ * One library, one GPU.  Every entry point that computes runs CUDA kernels of
+ * this library; there is no CPU fallback.  All work of a handle is enqueued on
+ * the CUDA stream given to pa_create (NULL = the legacy default stream); the
+ * calls that return numbers to host memory synchronise that stream first.
+ *
+ * Conventions (all entry points):
+ *   - CSR is 0-based: row_ptr[0] = 0, row_ptr non-decreasing,
+ *     row_ptr[n_rows] = nnz, 0 <= col_idx[k] < n_cols.  Column indices may be
+ *     unsorted and may repeat (repeats add up).  Violations give
+ *     PA_ERR_INVALID_CSR.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     device memory of the current device.  Which one a call takes is stated
+ *     beside it.  Output pointers documented as "may be NULL" are skipped.
+ *   - Statuses < 0 are errors: outputs are left untouched and
+ *     pa_last_error() holds a message.  PA_WARN_SINGULAR (> 0) is a result.
+ *   - The library copies every input; callers keep ownership of their arrays.
+ *   - Handles are not thread-safe: one thread at a time per handle.
+ */
+#ifndef PA_H
+#define PA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pa_ctx* pa_handle; /* opaque; owned by the library */
+
+typedef enum {
+  PA_SIGMA_MAX = 1, /* maximise L: sigma_max = ||A||_2                   */
+  PA_SIGMA_MIN = 2, /* minimise ||Ax||/||x|| on the sphere: sigma_min   */
+  PA_BOTH = 3
+} pa_mode;
+
+typedef enum {
+  PA_OK = 0,
+  PA_WARN_SINGULAR = 1,      /* ||A x|| == 0 met: sigma_min = 0, kappa = +inf */
+  PA_ERR_INVALID_ARG = -1,
+  PA_ERR_INVALID_CSR = -2,
+  PA_ERR_NOT_SQUARE = -3,    /* sigma_min needs n_rows >= n_cols            */
+  PA_ERR_NONFINITE = -4,     /* a NaN or Inf reached a reduction            */
+  PA_ERR_TIMEOUT = -5,       /* a device-side wait ran out of time          */
+  PA_ERR_CUDA = -6,
+  PA_ERR_OOM = -7,
+  PA_ERR_LAUNCH = -8,        /* the persistent grid does not fit the GPU    */
+  PA_ERR_UNSUPPORTED = -9
+} pa_status;
+
+enum { PA_HOST = 0, PA_DEVICE = 1 };                   /* pointer kinds        */
+enum { PA_LOSS_LOGRATIO = 0, PA_LOSS_QUADRATIC = 1 };  /* loss forms           */
+enum { PA_FP64 = 0, PA_MIXED = 1 };                    /* precision modes      */
+enum { PA_EQ_NONE = 0, PA_EQ_STORAGE = 1 };            /* equilibration        */
+enum { PA_ENGINE_AUTO = 0, PA_ENGINE_GRID = 1, PA_ENGINE_CLUSTER = 2 };
+enum { PA_ABLATE_NO_TANGENT = 1, PA_ABLATE_NO_NORMALISE = 2 };
+
+typedef struct {
+  /* Loss of Algorithm 1.  LOGRATIO (default) is the paper's
+   * L(v) = log||v|| - log||Av|| with gradient Eq. nabla_loss (negated for
+   * sigma_min).  QUADRATIC is L = -||Av||^2 (sigma_max) / +||Av||^2
+   * (sigma_min) with gradient -/+ 2 A^T A v. */
+  int loss;
+  /* FP64 (default): every product, the Adam state and every reduction in
+   * FP64.  MIXED: sigma_max iterates with FP32 products on the
+   * power-of-two-equilibrated matrix; sigma_min uses compensated
+   * (double-double) products; the returned sigma is always ||A x_min|| in
+   * FP64 (compensated for sigma_min). */
+  int precision;
+  int equilibrate;  /* PA_EQ_STORAGE: keep D_r^-1 A D_c^-1 with pow2 D (implied by MIXED) */
+  int engine;       /* AUTO picks CLUSTER for small matrices, else GRID     */
+  int ablation;     /* PA_ABLATE_* bits: drop the tangent projection and/or
+                       the normalisation of Algorithm 1 (the paper's vanilla
+                       Adam comparison); 0 = Algorithm 1 as printed        */
+  int64_t barrier_timeout_ns; /* device wait limit per barrier; <= 0 -> 2 s */
+  int grid_blocks;  /* 0 = fill the GPU; > 0 caps the persistent grid      */
+  int debug_skip_arrival; /* test hook: > 0 makes CTA 0 skip the barrier of
+                             that iteration, so the others time out (0 = off) */
+} pa_options;
+
+/* Fill *opt with the defaults above (LOGRATIO, FP64, no equilibration, AUTO
+ * engine, no ablation, 2 s barrier limit, full grid, no debug hook). */
+void pa_options_default(pa_options* opt);
+
+/* Build a handle for the n_rows x n_cols matrix A given in CSR.
+ * row_ptr (n_rows+1 int32), col_idx (nnz int32) and vals (nnz float64) are
+ * host pointers (ptr_kind = PA_HOST) or device pointers (PA_DEVICE); both are
+ * copied.  On the device the library validates the CSR, builds the explicit
+ * CSR of A^T with a stable (row-ordered) transpose, and, when opt asks for
+ * it, the power-of-two equilibration of the paper's "Row and Column Scaling"
+ * subsection.  opt may be NULL (defaults).  cuda_stream is a cudaStream_t or
+ * NULL.  Errors: PA_ERR_INVALID_ARG (sizes < 0, NULL pointers with nnz > 0),
+ * PA_ERR_INVALID_CSR, PA_ERR_OOM, PA_ERR_CUDA. */
+pa_status pa_create(pa_handle* out, int32_t n_rows, int32_t n_cols, int64_t nnz,
+                    const int32_t* row_ptr, const int32_t* col_idx, const double* vals,
+                    int ptr_kind, const pa_options* opt, void* cuda_stream);
+
+/* Estimate sigma_max and/or sigma_min of A with Algorithm 1: `iters`
+ * iterations of Projected Adam (step size lr, moment decays beta1, beta2,
+ * epsilon eps) from the start vector x_i = 2u_i - 1, u_i the i-th SplitMix64
+ * output of `seed` scaled to [0, 1), normalised to unit length.  Each sigma
+ * is ||A x_min|| / ||x_min|| for the tracked minimiser x_min.  The handle keeps
+ * the latest sigma_max and sigma_min, so kappa = sigma_max / sigma_min once
+ * both modes have run (NaN before).  Host outputs; each may be NULL.
+ * Returns PA_OK, PA_WARN_SINGULAR or an error (PA_ERR_NONFINITE,
+ * PA_ERR_TIMEOUT, PA_ERR_NOT_SQUARE for sigma_min with n_rows < n_cols). */
+pa_status pa_estimate(pa_handle h, pa_mode mode, int iters, double lr, double beta1,
+                      double beta2, double eps, uint64_t seed, double* sigma_max,
+                      double* sigma_min, double* kappa);
+
+/* Algorithm 1 for one mode (PA_SIGMA_MAX or PA_SIGMA_MIN) from a given
+ * start vector x_init (n_cols float64, host or device per x_kind, used as
+ * is: Algorithm 1 does not normalise x_init).  Host outputs, each may be NULL:
+ *   x_min[n_cols]   Algorithm 1's return value
+ *   x_last[n_cols]  the iterate after the last iteration
+ *   info[4]         {L_min, t_min (0 = x_init), L(x_T), iterations run}
+ *   L_trace[iters]  L(x_t) for t = 1..iters
+ *   x_trace[n_trace * n_cols]  x_t for t = 1..n_trace (n_trace <= iters)
+ *   sigma           ||A x_min|| / ||x_min||
+ */
+pa_status pa_run(pa_handle h, pa_mode mode, int iters, double lr, double beta1, double beta2,
+                 double eps, const double* x_init, int x_kind, double* x_min, double* x_last,
+                 double* info, double* L_trace, double* x_trace, int n_trace, double* sigma);
+
+/* Many independent estimates in one persistent launch (captured in a CUDA
+ * graph): item (i, r), i < n_mat, r < k_restarts, runs Algorithm 1 on the
+ * matrix of handles[i] from the start vector of seed s_ir = SplitMix64 output
+ * number (i * k_restarts + r) of `seed`; the k restarts of a matrix advance
+ * together as a block of k vectors (SpMM).  iters[0] iterations for sigma_max
+ * and iters[1] for sigma_min.  All handles must share one stream and the
+ * FP64 precision mode.  Host outputs:
+ *   out[(i * k_restarts + r) * 3 + {0,1,2}] = {sigma_max, sigma_min, kappa}
+ *   item_status[i * k_restarts + r]  (may be NULL)
+ * mode selects which sigmas run (the others are written as NaN). */
+pa_status pa_estimate_batched(int n_mat, const pa_handle* handles, pa_mode mode, int k_restarts,
+                              const int* iters, double lr, double beta1, double beta2, double eps,
+                              uint64_t seed, double* out, pa_status* item_status);
+
+/* x_min of the latest run of `which` (PA_SIGMA_MAX or PA_SIGMA_MIN) into the
+ * host array x_min_host[n_cols] (Algorithm 1's output). */
+pa_status pa_get_vector(pa_handle h, pa_mode which, double* x_min_host);
+
+/* y = A x (n_rows outputs) or z = A^T y over the explicit transpose (n_cols
+ * outputs) with the library's CSR product kernels; ptr_kind says whether x/y
+ * are host or device pointers.  Used to check the product kernels. */
+pa_status pa_spmv(pa_handle h, const double* x, double* y, int ptr_kind);
+pa_status pa_spmv_t(pa_handle h, const double* y, double* z, int ptr_kind);
+
+/* The CSR of A^T as built on the device (host outputs: row_ptr_t[n_cols+1],
+ * col_t[nnz], val_t[nnz]; each may be NULL). */
+pa_status pa_get_transpose(pa_handle h, int32_t* row_ptr_t, int32_t* col_t, double* val_t);
+
+/* The power-of-two equilibration factors D_r (n_rows) and D_c (n_cols) of the
+ * handle (host outputs); PA_ERR_INVALID_ARG when the handle has none. */
+pa_status pa_get_equilibration(pa_handle h, double* d_row, double* d_col);
+
+/* Launches of this library's kernels since the handle was created (a
+ * counter kept by the host code at every launch). */
+int64_t pa_kernel_launches(pa_handle h);
+
+/* Release the handle and its device memory (NULL-safe). */
+void pa_destroy(pa_handle h);
+
+/* Message of the latest error on this thread ("" if none). */
+const char* pa_last_error(void);
+
+/* Device allocator hooks (for example the PyTorch caching allocator).  With
+ * none installed the library uses cudaMallocAsync/cudaFreeAsync on the
+ * handle's stream.  alloc returns NULL on failure.  Affects handles created
+ * after the call. */
+typedef void* (*pa_alloc_fn)(size_t bytes, void* cuda_stream, void* ctx);
+typedef void (*pa_free_fn)(void* ptr, size_t bytes, void* cuda_stream, void* ctx);
+void pa_set_allocator(pa_alloc_fn alloc, pa_free_fn free_fn, void* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PA_H */

@@ -13,6 +13,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import platform
 import subprocess
 import threading
 from pathlib import Path
@@ -83,14 +84,43 @@ class using:
         _active.lib = self.prev
 
 
-def compile_variant(source_text: str, out_path) -> Path:
-    """Compile an edited copy of the oracle source (used by mutation tests)."""
+def compile_variant(source_text: str, out_path, contract_fma: bool = False) -> Path:
+    """Compile an edited copy of the oracle source (mutation tests), or the
+    unchanged source with fused multiply-add contraction (contract_fma): the
+    same algorithm under a different rounding, used to measure how strongly
+    an iteration amplifies round-off."""
     out_path = Path(out_path)
     src = out_path.with_suffix(".c")
     src.write_text(source_text)
-    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-shared",
+    flags = ["-ffp-contract=fast"] if contract_fma else ["-ffp-contract=off"]
+    if contract_fma and platform.machine() in ("x86_64", "AMD64"):
+        flags.append("-mfma")  # aarch64 has FMA in its base ISA
+    subprocess.run(["gcc", "-O2", *flags, "-fno-fast-math", "-std=c11", "-shared",
                     "-fPIC", str(src), "-o", str(out_path), "-lm"], check=True)
     return out_path
+
+
+def rounding_ensemble(A, mode: int, iters: int, x_init, workdir, loss: int = LOSS_LOGRATIO,
+                      n_perturbed: int = 2, n_entries: int = 3, **hyper):
+    """Runs of the same Algorithm 1 that differ from the oracle only in
+    round-off: the FMA-contracted build of this source, and x_init with a few
+    entries moved by one ulp.  Returns (reference run, [variant runs])."""
+    x_init = np.ascontiguousarray(x_init, dtype=np.float64)
+    ref = projected_adam(A, mode, iters, x_init=x_init, loss=loss, n_trace=iters, trace_L=True,
+                         **hyper)
+    runs = []
+    fma = load(compile_variant(source_text(), Path(workdir) / "oracle_fma.so", contract_fma=True))
+    with using(fma):
+        runs.append(projected_adam(A, mode, iters, x_init=x_init, loss=loss, n_trace=iters,
+                                   trace_L=True, **hyper))
+    rng = np.random.default_rng(12345)
+    for _ in range(n_perturbed):
+        xp = x_init.copy()
+        idx = rng.choice(xp.size, size=min(n_entries, xp.size), replace=False)
+        xp[idx] = np.nextafter(xp[idx], np.inf)
+        runs.append(projected_adam(A, mode, iters, x_init=xp, loss=loss, n_trace=iters,
+                                   trace_L=True, **hyper))
+    return ref, runs
 
 
 def source_text() -> str:

@@ -1,0 +1,566 @@
+// pa_api.cu -- host runtime behind include/pa.h: handles, argument and CSR
+// validation, device memory, the start vector, launch orchestration of the
+// persistent Projected Adam kernel, and result read-back.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "pa_internal.h"
+
+using namespace pa;
+
+// ------------------------------------------------------------ errors --
+
+static thread_local std::string g_err;
+
+static pa_status fail(pa_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+static pa_status cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation)
+    return fail(PA_ERR_OOM, "%s: out of device memory", what);
+  return fail(PA_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                              \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+extern "C" const char* pa_last_error(void) { return g_err.c_str(); }
+
+// --------------------------------------------------------- allocator --
+
+static pa_alloc_fn g_alloc = nullptr;
+static pa_free_fn g_free = nullptr;
+static void* g_alloc_ctx = nullptr;
+
+extern "C" void pa_set_allocator(pa_alloc_fn alloc, pa_free_fn free_fn, void* ctx) {
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_alloc_ctx = ctx;
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct pa_ctx {
+  cudaStream_t stream = nullptr;
+  pa_alloc_fn alloc = nullptr;
+  pa_free_fn free_fn = nullptr;
+  void* alloc_ctx = nullptr;
+  pa_options opt{};
+  int32_t n_rows = 0, n_cols = 0;
+  int64_t nnz = 0;
+  int64_t launches = 0;
+  std::vector<DevBuf> bufs;  // everything allocated, freed in pa_destroy
+
+  // matrix
+  int32_t *rp = nullptr, *ci = nullptr, *rpt = nullptr, *cit = nullptr;
+  double *va = nullptr, *vat = nullptr;
+
+  // run buffers (sized for n = max(n_rows, n_cols))
+  bool run_ready = false;
+  double *X0 = nullptr, *X1 = nullptr, *X2 = nullptr, *Xinit = nullptr;
+  double *m = nullptr, *v = nullptr, *y = nullptr, *ylo = nullptr, *dx = nullptr;
+  double *partials = nullptr, *blockpart = nullptr;
+  double *xmin_max = nullptr, *xmin_min = nullptr;
+  RunState* st = nullptr;
+  int G = 0;
+  int32_t *part_a = nullptr, *part_t = nullptr;
+  double2* bias = nullptr;
+  int bias_cap = 0;
+  bool have_max = false, have_min = false;
+  double sigma_max = NAN, sigma_min = NAN;
+};
+
+static void* dev_alloc(pa_ctx* h, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~(size_t)255;
+  void* p = nullptr;
+  if (h->alloc) {
+    p = h->alloc(bytes, (void*)h->stream, h->alloc_ctx);
+  } else if (cudaMallocAsync(&p, bytes, h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) h->bufs.push_back({p, bytes});
+  return p;
+}
+
+template <class T>
+static pa_status alloc_n(pa_ctx* h, T** out, size_t count, const char* what) {
+  *out = (T*)dev_alloc(h, sizeof(T) * count);
+  if (!*out) return fail(PA_ERR_OOM, "out of device memory allocating %s (%zu bytes)", what,
+                         sizeof(T) * count);
+  return PA_OK;
+}
+
+static void dev_free(pa_ctx* h, void* p) {
+  for (size_t i = 0; i < h->bufs.size(); ++i) {
+    if (h->bufs[i].p == p) {
+      if (h->free_fn) h->free_fn(p, h->bufs[i].bytes, (void*)h->stream, h->alloc_ctx);
+      else cudaFreeAsync(p, h->stream);
+      h->bufs.erase(h->bufs.begin() + i);
+      return;
+    }
+  }
+}
+
+extern "C" void pa_options_default(pa_options* opt) {
+  if (!opt) return;
+  memset(opt, 0, sizeof *opt);
+  opt->loss = PA_LOSS_LOGRATIO;
+  opt->precision = PA_FP64;
+  opt->equilibrate = PA_EQ_NONE;
+  opt->engine = PA_ENGINE_AUTO;
+  opt->barrier_timeout_ns = 2000000000LL;
+}
+
+extern "C" void pa_destroy(pa_handle h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  for (auto& b : h->bufs) {
+    if (h->free_fn) h->free_fn(b.p, b.bytes, (void*)h->stream, h->alloc_ctx);
+    else cudaFreeAsync(b.p, h->stream);
+  }
+  cudaStreamSynchronize(h->stream);
+  delete h;
+}
+
+extern "C" int64_t pa_kernel_launches(pa_handle h) { return h ? h->launches : -1; }
+
+// ---------------------------------------------------------- pa_create --
+
+extern "C" pa_status pa_create(pa_handle* out, int32_t n_rows, int32_t n_cols, int64_t nnz,
+                               const int32_t* row_ptr, const int32_t* col_idx, const double* vals,
+                               int ptr_kind, const pa_options* opt, void* cuda_stream) {
+  g_err.clear();
+  if (!out) return fail(PA_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_rows < 0 || n_cols < 0 || nnz < 0)
+    return fail(PA_ERR_INVALID_ARG, "negative size (n_rows=%d n_cols=%d nnz=%lld)", n_rows, n_cols,
+                (long long)nnz);
+  if (n_rows == 0 || n_cols == 0)
+    return fail(PA_ERR_INVALID_ARG, "empty matrix (%d x %d)", n_rows, n_cols);
+  if (nnz > 2147483647LL) return fail(PA_ERR_INVALID_ARG, "nnz %lld exceeds int32 CSR", (long long)nnz);
+  if (!row_ptr || (nnz > 0 && (!col_idx || !vals)))
+    return fail(PA_ERR_INVALID_ARG, "NULL CSR array");
+  if (ptr_kind != PA_HOST && ptr_kind != PA_DEVICE)
+    return fail(PA_ERR_INVALID_ARG, "ptr_kind must be PA_HOST or PA_DEVICE");
+  pa_options o;
+  pa_options_default(&o);
+  if (opt) o = *opt;
+  if (o.barrier_timeout_ns <= 0) o.barrier_timeout_ns = 2000000000LL;
+  if (o.loss != PA_LOSS_LOGRATIO && o.loss != PA_LOSS_QUADRATIC)
+    return fail(PA_ERR_INVALID_ARG, "unknown loss %d", o.loss);
+  if (o.precision != PA_FP64)
+    return fail(PA_ERR_UNSUPPORTED, "precision mode %d is not available in this build", o.precision);
+  if (o.equilibrate != PA_EQ_NONE)
+    return fail(PA_ERR_UNSUPPORTED, "equilibration is not available in this build");
+
+  pa_ctx* h = new pa_ctx();
+  h->stream = (cudaStream_t)cuda_stream;
+  h->alloc = g_alloc;
+  h->free_fn = g_free;
+  h->alloc_ctx = g_alloc_ctx;
+  h->opt = o;
+  h->n_rows = n_rows;
+  h->n_cols = n_cols;
+  h->nnz = nnz;
+  pa_status st = PA_OK;
+  auto bail = [&](pa_status s) {
+    pa_destroy(h);
+    return s;
+  };
+  // +4 entries of padding on the nnz arrays keeps every vector load in bounds
+  if ((st = alloc_n(h, &h->rp, (size_t)n_rows + 1, "row_ptr")) ||
+      (st = alloc_n(h, &h->ci, (size_t)nnz + 4, "col_idx")) ||
+      (st = alloc_n(h, &h->va, (size_t)nnz + 4, "values")) ||
+      (st = alloc_n(h, &h->rpt, (size_t)n_cols + 1, "row_ptr of A^T")) ||
+      (st = alloc_n(h, &h->cit, (size_t)nnz + 4, "col_idx of A^T")) ||
+      (st = alloc_n(h, &h->vat, (size_t)nnz + 4, "values of A^T")))
+    return bail(st);
+  const cudaMemcpyKind kind = ptr_kind == PA_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(h->rp, row_ptr, sizeof(int32_t) * ((size_t)n_rows + 1), kind, h->stream)) ||
+      (nnz && (e = cudaMemcpyAsync(h->ci, col_idx, sizeof(int32_t) * nnz, kind, h->stream))) ||
+      (nnz && (e = cudaMemcpyAsync(h->va, vals, sizeof(double) * nnz, kind, h->stream))) ||
+      (e = cudaMemsetAsync(h->ci + nnz, 0, sizeof(int32_t) * 4, h->stream)) ||
+      (e = cudaMemsetAsync(h->va + nnz, 0, sizeof(double) * 4, h->stream)))
+    return bail(cuda_fail(e, "copying the CSR arrays"));
+
+  // validate on the device before any kernel walks the rows
+  int* flag = nullptr;
+  if ((st = alloc_n(h, &flag, 1, "flag"))) return bail(st);
+  if ((e = cudaMemsetAsync(flag, 0, sizeof(int), h->stream)) ||
+      (e = launch_validate_csr(n_rows, n_cols, nnz, h->rp, h->ci, flag, h->stream, &h->launches)))
+    return bail(cuda_fail(e, "validating the CSR"));
+  int hflag = 0;
+  if ((e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream)) ||
+      (e = cudaStreamSynchronize(h->stream)))
+    return bail(cuda_fail(e, "validating the CSR"));
+  if (hflag) {
+    return bail(fail(PA_ERR_INVALID_CSR, "invalid CSR:%s%s%s",
+                     (hflag & 1) ? " row_ptr[0] != 0 or row_ptr[n_rows] != nnz;" : "",
+                     (hflag & 2) ? " row_ptr decreases;" : "",
+                     (hflag & 4) ? " column index out of range;" : ""));
+  }
+  dev_free(h, flag);
+
+  // explicit CSR of A^T (stable: entries of each row of A^T in row order of A)
+  int32_t *cursor = nullptr, *src = nullptr, *rowid = nullptr, *bsums = nullptr;
+  if ((st = alloc_n(h, &cursor, (size_t)n_cols + 1, "transpose scratch")) ||
+      (st = alloc_n(h, &src, (size_t)nnz + 1, "transpose scratch")) ||
+      (st = alloc_n(h, &rowid, (size_t)nnz + 1, "transpose scratch")) ||
+      (st = alloc_n(h, &bsums, (size_t)scan_blocks((int64_t)n_cols) + 1, "transpose scratch")))
+    return bail(st);
+  if ((e = launch_transpose(n_rows, n_cols, nnz, h->rp, h->ci, h->va, h->rpt, h->cit, h->vat,
+                            cursor, src, rowid, bsums, nullptr, h->stream, &h->launches)) ||
+      (e = cudaMemsetAsync(h->cit + nnz, 0, sizeof(int32_t) * 4, h->stream)) ||
+      (e = cudaMemsetAsync(h->vat + nnz, 0, sizeof(double) * 4, h->stream)) ||
+      (e = cudaStreamSynchronize(h->stream)))
+    return bail(cuda_fail(e, "building the transpose"));
+  dev_free(h, cursor);
+  dev_free(h, src);
+  dev_free(h, rowid);
+  dev_free(h, bsums);
+  *out = h;
+  return PA_OK;
+}
+
+// ------------------------------------------------------------- runs --
+
+static pa_status ensure_run_buffers(pa_ctx* h) {
+  if (h->run_ready) return PA_OK;
+  const size_t n = (size_t)std::max(h->n_rows, h->n_cols);
+  pa_status st;
+  if ((st = alloc_n(h, &h->X0, n, "iterate")) || (st = alloc_n(h, &h->X1, n, "iterate")) ||
+      (st = alloc_n(h, &h->X2, n, "iterate")) || (st = alloc_n(h, &h->Xinit, n, "x_init")) ||
+      (st = alloc_n(h, &h->m, n, "first moment")) || (st = alloc_n(h, &h->v, n, "second moment")) ||
+      (st = alloc_n(h, &h->y, (size_t)h->n_rows, "A x")) ||
+      (st = alloc_n(h, &h->dx, n, "step")) ||
+      (st = alloc_n(h, &h->xmin_max, (size_t)h->n_cols, "x_min")) ||
+      (st = alloc_n(h, &h->xmin_min, (size_t)h->n_cols, "x_min")) ||
+      (st = alloc_n(h, &h->st, 1, "run state")) ||
+      (st = alloc_n(h, &h->blockpart, (size_t)2 * 152 * 8 + 64, "block partials")))
+    return st;
+  h->run_ready = true;
+  return PA_OK;
+}
+
+static int choose_grid(pa_ctx* h, int* maxG_out) {
+  int per = 0;
+  const int maxG = persistent_max_blocks(h->opt.loss, &per);
+  if (maxG_out) *maxG_out = maxG;
+  if (maxG <= 0) return -1;
+  const int64_t n = std::max(h->n_rows, h->n_cols);
+  int64_t want = (n + 2047) / 2048;  // about four rows per thread
+  if (want < 1) want = 1;
+  int G = (int)std::min<int64_t>(want, maxG);
+  if (h->opt.grid_blocks > 0) G = std::min(G, h->opt.grid_blocks);
+  return G;
+}
+
+static pa_status ensure_partitions(pa_ctx* h, int G) {
+  if (h->G == G && h->part_a) return PA_OK;
+  if (h->part_a) dev_free(h, h->part_a);
+  if (h->part_t) dev_free(h, h->part_t);
+  if (h->partials) dev_free(h, h->partials);
+  h->part_a = h->part_t = nullptr;
+  h->partials = nullptr;
+  pa_status st;
+  if ((st = alloc_n(h, &h->part_a, (size_t)G + 1, "partition")) ||
+      (st = alloc_n(h, &h->part_t, (size_t)G + 1, "partition")) ||
+      (st = alloc_n(h, &h->partials, (size_t)G * kPartSlots, "partials")))
+    return st;
+  cudaError_t e;
+  // phase A rows weigh their non-zeros plus 2; phase B/C rows carry the Adam
+  // update as well (about 24 FP64 operations), hence the heavier row weight.
+  if ((e = launch_partition(h->rp, h->n_rows, G, 2, h->part_a, h->stream, &h->launches)) ||
+      (e = launch_partition(h->rpt, h->n_cols, G, 24, h->part_t, h->stream, &h->launches)))
+    return cuda_fail(e, "partitioning rows");
+  h->G = G;
+  return PA_OK;
+}
+
+static pa_status ensure_bias(pa_ctx* h, int iters, double lr, double b1, double b2) {
+  std::vector<double2> tab((size_t)std::max(iters, 1));
+  for (int t = 1; t <= iters; ++t)
+    tab[t - 1] = make_double2(lr / (1.0 - pow(b1, (double)t)), 1.0 / (1.0 - pow(b2, (double)t)));
+  if (h->bias_cap < iters) {
+    if (h->bias) dev_free(h, h->bias);
+    h->bias = nullptr;
+    pa_status st;
+    if ((st = alloc_n(h, &h->bias, (size_t)std::max(iters, 1), "bias table"))) return st;
+    h->bias_cap = iters;
+  }
+  if (iters > 0) {
+    cudaError_t e = cudaMemcpyAsync(h->bias, tab.data(), sizeof(double2) * iters,
+                                    cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // tab is pageable host memory
+    if (e != cudaSuccess) return cuda_fail(e, "uploading the bias corrections");
+  }
+  return PA_OK;
+}
+
+static pa_status check_hyper(int iters, double lr, double b1, double b2, double eps) {
+  if (iters < 0) return fail(PA_ERR_INVALID_ARG, "iters < 0");
+  if (!(lr > 0) || !isfinite(lr)) return fail(PA_ERR_INVALID_ARG, "lr must be finite and > 0");
+  if (!(b1 >= 0 && b1 < 1) || !(b2 >= 0 && b2 < 1))
+    return fail(PA_ERR_INVALID_ARG, "beta1, beta2 must lie in [0, 1)");
+  if (!(eps >= 0) || !isfinite(eps)) return fail(PA_ERR_INVALID_ARG, "eps must be finite and >= 0");
+  return PA_OK;
+}
+
+// One Algorithm 1 run from the device vector h->Xinit.
+static pa_status run_one(pa_ctx* h, pa_mode mode, int iters, double lr, double b1, double b2,
+                         double eps, double* L_trace_dev, double* x_trace_dev, int n_trace,
+                         RunState* out) {
+  if (mode == PA_SIGMA_MIN && h->n_rows < h->n_cols)
+    return fail(PA_ERR_NOT_SQUARE, "sigma_min needs n_rows >= n_cols (%d x %d)", h->n_rows,
+                h->n_cols);
+  int maxG = 0;
+  const int G = choose_grid(h, &maxG);
+  if (G <= 0) return fail(PA_ERR_LAUNCH, "the persistent kernel does not fit on this GPU");
+  pa_status st;
+  if ((st = ensure_partitions(h, G)) || (st = ensure_bias(h, iters, lr, b1, b2))) return st;
+  const size_t n = (size_t)h->n_cols;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(h->X0, h->Xinit, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream)) ||
+      (e = cudaMemsetAsync(h->m, 0, sizeof(double) * n, h->stream)) ||
+      (e = cudaMemsetAsync(h->v, 0, sizeof(double) * n, h->stream)) ||
+      (e = cudaMemsetAsync(h->st, 0, sizeof(RunState), h->stream)))
+    return cuda_fail(e, "preparing the run");
+  IterParams p{};
+  p.n_rows = h->n_rows;
+  p.n_cols = h->n_cols;
+  p.rp = h->rp; p.ci = h->ci; p.va = h->va;
+  p.rpt = h->rpt; p.cit = h->cit; p.vat = h->vat;
+  p.part_a = h->part_a; p.part_t = h->part_t;
+  p.X0 = h->X0; p.X1 = h->X1; p.X2 = h->X2;
+  p.m = h->m; p.v = h->v; p.y = h->y; p.ylo = h->ylo; p.dx = h->dx;
+  p.partials = h->partials;
+  p.bias = h->bias;
+  p.L_trace = L_trace_dev;
+  p.x_trace = x_trace_dev;
+  p.n_trace = n_trace;
+  p.st = h->st;
+  p.iters = iters;
+  p.mode = mode;
+  p.ablation = h->opt.ablation;
+  p.beta1 = b1; p.beta2 = b2; p.eps = eps;
+  p.timeout_ns = h->opt.barrier_timeout_ns;
+  p.skip_arrival = h->opt.debug_skip_arrival;
+  e = launch_persistent(p, h->opt.loss, G, h->stream, &h->launches);
+  if (e == cudaErrorCooperativeLaunchTooLarge)
+    return fail(PA_ERR_LAUNCH, "cooperative grid of %d CTAs does not fit (max %d)", G, maxG);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the persistent kernel");
+  if ((e = launch_sigma(h->n_rows, h->n_cols, h->rp, h->ci, h->va, h->X0, h->X1, h->X2, 1, h->st,
+                        h->blockpart, h->stream, &h->launches)))
+    return cuda_fail(e, "launching the sigma kernel");
+  if ((e = cudaMemcpyAsync(out, h->st, sizeof(RunState), cudaMemcpyDeviceToHost, h->stream)) ||
+      (e = cudaStreamSynchronize(h->stream)))
+    return cuda_fail(e, "running Projected Adam");
+  double* keep = mode == PA_SIGMA_MAX ? h->xmin_max : h->xmin_min;
+  double* src = out->minb == 0 ? h->X0 : (out->minb == 1 ? h->X1 : h->X2);
+  if ((e = cudaMemcpyAsync(keep, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream)))
+    return cuda_fail(e, "keeping x_min");
+  if (out->status == PA_ERR_TIMEOUT)
+    return fail(PA_ERR_TIMEOUT, "a grid barrier wait ran out of time (barrier %d)", out->timeout_site);
+  if (out->status == PA_ERR_NONFINITE)
+    return fail(PA_ERR_NONFINITE, "a NaN or Inf reached a reduction");
+  if (mode == PA_SIGMA_MAX) { h->sigma_max = out->sigma; h->have_max = true; }
+  else { h->sigma_min = out->sigma; h->have_min = true; }
+  return (pa_status)out->status;
+}
+
+extern "C" pa_status pa_run(pa_handle h, pa_mode mode, int iters, double lr, double beta1,
+                            double beta2, double eps, const double* x_init, int x_kind,
+                            double* x_min, double* x_last, double* info, double* L_trace,
+                            double* x_trace, int n_trace, double* sigma) {
+  g_err.clear();
+  if (!h) return fail(PA_ERR_INVALID_ARG, "NULL handle");
+  if (mode != PA_SIGMA_MAX && mode != PA_SIGMA_MIN)
+    return fail(PA_ERR_INVALID_ARG, "pa_run takes PA_SIGMA_MAX or PA_SIGMA_MIN");
+  if (!x_init) return fail(PA_ERR_INVALID_ARG, "x_init is NULL");
+  if (x_kind != PA_HOST && x_kind != PA_DEVICE) return fail(PA_ERR_INVALID_ARG, "bad x_kind");
+  if (n_trace < 0 || n_trace > iters) return fail(PA_ERR_INVALID_ARG, "n_trace must lie in [0, iters]");
+  pa_status st;
+  if ((st = check_hyper(iters, lr, beta1, beta2, eps)) || (st = ensure_run_buffers(h))) return st;
+  const size_t n = (size_t)h->n_cols;
+  cudaError_t e = cudaMemcpyAsync(h->Xinit, x_init, sizeof(double) * n,
+                                  x_kind == PA_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                  h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "copying x_init");
+  double *Ld = nullptr, *Xd = nullptr;
+  if (L_trace && iters > 0 && (st = alloc_n(h, &Ld, (size_t)iters, "L trace"))) return st;
+  if (x_trace && n_trace > 0 && (st = alloc_n(h, &Xd, (size_t)n_trace * n, "x trace"))) {
+    if (Ld) dev_free(h, Ld);
+    return st;
+  }
+  RunState rs{};
+  pa_status rst = run_one(h, mode, iters, lr, beta1, beta2, eps, Ld, Xd, x_trace ? n_trace : 0, &rs);
+  if (rst >= 0) {
+    double* xs[3] = {h->X0, h->X1, h->X2};
+    if (x_min) e = cudaMemcpyAsync(x_min, xs[rs.minb], sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && x_last)
+      e = cudaMemcpyAsync(x_last, xs[rs.cur], sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && Ld)
+      e = cudaMemcpyAsync(L_trace, Ld, sizeof(double) * iters, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && Xd)
+      e = cudaMemcpyAsync(x_trace, Xd, sizeof(double) * n_trace * n, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) rst = cuda_fail(e, "reading results");
+    if (rst >= 0) {
+      if (info) {
+        info[0] = rs.L_min;
+        info[1] = rs.t_min;
+        info[2] = rs.L_last;
+        info[3] = rs.iters_run;
+      }
+      if (sigma) *sigma = rs.sigma;
+    }
+  }
+  if (Ld) dev_free(h, Ld);
+  if (Xd) dev_free(h, Xd);
+  return rst;
+}
+
+extern "C" pa_status pa_estimate(pa_handle h, pa_mode mode, int iters, double lr, double beta1,
+                                 double beta2, double eps, uint64_t seed, double* sigma_max,
+                                 double* sigma_min, double* kappa) {
+  g_err.clear();
+  if (!h) return fail(PA_ERR_INVALID_ARG, "NULL handle");
+  if (mode != PA_SIGMA_MAX && mode != PA_SIGMA_MIN && mode != PA_BOTH)
+    return fail(PA_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
+  pa_status st;
+  if ((st = check_hyper(iters, lr, beta1, beta2, eps)) || (st = ensure_run_buffers(h))) return st;
+  if ((mode & PA_SIGMA_MIN) && h->n_rows < h->n_cols)
+    return fail(PA_ERR_NOT_SQUARE, "sigma_min needs n_rows >= n_cols (%d x %d)", h->n_rows, h->n_cols);
+  cudaError_t e = launch_start_vector(h->n_cols, seed, h->Xinit, h->blockpart, h->stream, &h->launches);
+  if (e != cudaSuccess) return cuda_fail(e, "building the start vector");
+  pa_status worst = PA_OK;
+  RunState rs{};
+  for (int md : {PA_SIGMA_MAX, PA_SIGMA_MIN}) {
+    if (!(mode & md)) continue;
+    st = run_one(h, (pa_mode)md, iters, lr, beta1, beta2, eps, nullptr, nullptr, 0, &rs);
+    if (st < 0) return st;
+    if (st > worst) worst = st;
+  }
+  if (sigma_max) *sigma_max = h->have_max ? h->sigma_max : NAN;
+  if (sigma_min) *sigma_min = h->have_min ? h->sigma_min : NAN;
+  if (kappa) {
+    if (h->have_max && h->have_min)
+      *kappa = h->sigma_min > 0 ? h->sigma_max / h->sigma_min : INFINITY;
+    else
+      *kappa = NAN;
+  }
+  return worst;
+}
+
+extern "C" pa_status pa_get_vector(pa_handle h, pa_mode which, double* x_min_host) {
+  g_err.clear();
+  if (!h || !x_min_host) return fail(PA_ERR_INVALID_ARG, "NULL argument");
+  if (which != PA_SIGMA_MAX && which != PA_SIGMA_MIN) return fail(PA_ERR_INVALID_ARG, "bad mode");
+  if ((which == PA_SIGMA_MAX && !h->have_max) || (which == PA_SIGMA_MIN && !h->have_min))
+    return fail(PA_ERR_INVALID_ARG, "no run of that mode yet");
+  double* src = which == PA_SIGMA_MAX ? h->xmin_max : h->xmin_min;
+  cudaError_t e = cudaMemcpyAsync(x_min_host, src, sizeof(double) * h->n_cols,
+                                  cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "reading x_min");
+  return PA_OK;
+}
+
+static pa_status product(pa_handle h, bool transposed, const double* in, double* out, int kind) {
+  g_err.clear();
+  if (!h || !in || !out) return fail(PA_ERR_INVALID_ARG, "NULL argument");
+  if (kind != PA_HOST && kind != PA_DEVICE) return fail(PA_ERR_INVALID_ARG, "bad ptr_kind");
+  const int32_t n_in = transposed ? h->n_rows : h->n_cols;
+  const int32_t n_out = transposed ? h->n_cols : h->n_rows;
+  const double* din = in;
+  double* dout = out;
+  pa_status st;
+  if (kind == PA_HOST) {
+    double *a = nullptr, *b = nullptr;
+    if ((st = alloc_n(h, &a, (size_t)n_in, "product input")) ||
+        (st = alloc_n(h, &b, (size_t)n_out, "product output")))
+      return st;
+    cudaError_t e = cudaMemcpyAsync(a, in, sizeof(double) * n_in, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+      e = transposed ? launch_spmv(h->n_cols, h->rpt, h->cit, h->vat, a, b, h->stream, &h->launches)
+                     : launch_spmv(h->n_rows, h->rp, h->ci, h->va, a, b, h->stream, &h->launches);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out, b, sizeof(double) * n_out, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    dev_free(h, a);
+    dev_free(h, b);
+    if (e != cudaSuccess) return cuda_fail(e, "sparse product");
+    return PA_OK;
+  }
+  cudaError_t e = transposed
+                      ? launch_spmv(h->n_cols, h->rpt, h->cit, h->vat, din, dout, h->stream, &h->launches)
+                      : launch_spmv(h->n_rows, h->rp, h->ci, h->va, din, dout, h->stream, &h->launches);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sparse product");
+  return PA_OK;
+}
+
+extern "C" pa_status pa_spmv(pa_handle h, const double* x, double* y, int ptr_kind) {
+  return product(h, false, x, y, ptr_kind);
+}
+
+extern "C" pa_status pa_spmv_t(pa_handle h, const double* y, double* z, int ptr_kind) {
+  return product(h, true, y, z, ptr_kind);
+}
+
+extern "C" pa_status pa_get_transpose(pa_handle h, int32_t* row_ptr_t, int32_t* col_t, double* val_t) {
+  g_err.clear();
+  if (!h) return fail(PA_ERR_INVALID_ARG, "NULL handle");
+  cudaError_t e = cudaSuccess;
+  if (row_ptr_t)
+    e = cudaMemcpyAsync(row_ptr_t, h->rpt, sizeof(int32_t) * ((size_t)h->n_cols + 1),
+                        cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && col_t && h->nnz)
+    e = cudaMemcpyAsync(col_t, h->cit, sizeof(int32_t) * h->nnz, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && val_t && h->nnz)
+    e = cudaMemcpyAsync(val_t, h->vat, sizeof(double) * h->nnz, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the transpose");
+  return PA_OK;
+}
+
+extern "C" pa_status pa_get_equilibration(pa_handle h, double* d_row, double* d_col) {
+  g_err.clear();
+  (void)d_row;
+  (void)d_col;
+  if (!h) return fail(PA_ERR_INVALID_ARG, "NULL handle");
+  return fail(PA_ERR_INVALID_ARG, "the handle holds no equilibration");
+}
+
+extern "C" pa_status pa_estimate_batched(int n_mat, const pa_handle* handles, pa_mode mode,
+                                         int k_restarts, const int* iters, double lr, double beta1,
+                                         double beta2, double eps, uint64_t seed, double* out,
+                                         pa_status* item_status) {
+  g_err.clear();
+  (void)n_mat; (void)handles; (void)mode; (void)k_restarts; (void)iters; (void)lr;
+  (void)beta1; (void)beta2; (void)eps; (void)seed; (void)out; (void)item_status;
+  return fail(PA_ERR_UNSUPPORTED, "batched estimates are not available in this build");
+}

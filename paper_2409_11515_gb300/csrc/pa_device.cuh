@@ -1,0 +1,97 @@
+// pa_device.cuh -- device helpers shared by the kernel translation units:
+// SplitMix64, deterministic block reductions, CSR row products, timers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pa {
+
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): output i of the generator
+// whose state starts at `seed` and advances by the golden gamma.
+__host__ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ long long globaltimer_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Butterfly sum over a warp: every lane ends with the same bits (each level
+// adds the same two values, and + is commutative), in a fixed order.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+  return v;
+}
+
+// Deterministic block sum of NV values per thread.  `scratch` holds
+// NV * (blockDim.x / 32) doubles.  Result valid in every thread.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = warp_sum(v[i]);
+  __syncthreads();  // scratch may still be read from a previous call
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) scratch[i * nw + warp] = v[i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double a = 0.0;
+    for (int w = lane; w < nw; w += 32) a += scratch[i * nw + w];
+    v[i] = warp_sum(a);
+  }
+}
+
+// Fixed-order sum of part[k * stride + slot], k < count, done by every warp
+// that calls it; all lanes and all callers get identical bits.
+__device__ __forceinline__ double ordered_sum(const double* part, int count, int stride, int slot) {
+  const int lane = threadIdx.x & 31;
+  double a = 0.0;
+  for (int k = lane; k < count; k += 32) a += part[(size_t)k * stride + slot];
+  return warp_sum(a);
+}
+
+// Dot product of one CSR row with a dense vector, entries in storage order,
+// one fused multiply-add each.
+__device__ __forceinline__ double row_dot(const int32_t* __restrict__ ci,
+                                          const double* __restrict__ va, int k0, int k1,
+                                          const double* x) {
+  double acc = 0.0;
+  int k = k0;
+  for (; k + 4 <= k1; k += 4) {
+    const int c0 = __ldg(ci + k), c1 = __ldg(ci + k + 1), c2 = __ldg(ci + k + 2),
+              c3 = __ldg(ci + k + 3);
+    const double v0 = __ldg(va + k), v1 = __ldg(va + k + 1), v2 = __ldg(va + k + 2),
+                 v3 = __ldg(va + k + 3);
+    const double x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
+    acc = fma(v0, x0, acc);
+    acc = fma(v1, x1, acc);
+    acc = fma(v2, x2, acc);
+    acc = fma(v3, x3, acc);
+  }
+  for (; k < k1; ++k) acc = fma(__ldg(va + k), x[__ldg(ci + k)], acc);
+  return acc;
+}
+
+}  // namespace pa

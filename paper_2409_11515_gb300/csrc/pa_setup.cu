@@ -1,0 +1,380 @@
+// pa_setup.cu -- one-time and auxiliary kernels of the Projected Adam library:
+// CSR validation, the stable CSR transpose that gives the explicit A^T used by
+// the transposed product, work partitions of the persistent grid, the seeded
+// start vector, a standalone SpMV, and the final sigma = ||A x|| / ||x||.
+#include "pa_device.cuh"
+#include "pa_internal.h"
+
+namespace pa {
+
+namespace {
+
+constexpr int kT = 256;            // threads per block of the setup kernels
+constexpr int kScanPer = 4;        // elements per thread in the scan
+constexpr int kScanChunk = 1024 * kScanPer;
+
+inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+inline int grid_for(int64_t n, int per_block = kT, int cap = 152 * 32) {
+  int g = cdiv(n, per_block);
+  return g < 1 ? 1 : (g > cap ? cap : g);
+}
+
+// ------------------------------------------------------------- validate --
+// flag bit 1: row_ptr ends wrong, bit 2: row_ptr decreases, bit 4: column
+// index out of range.
+__global__ void k_validate(int32_t n_rows, int32_t n_cols, int64_t nnz,
+                           const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           int* flag) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t0 == 0 && (rp[0] != 0 || (int64_t)rp[n_rows] != nnz)) atomicOr(flag, 1);
+  for (int64_t r = t0; r < n_rows; r += stride)
+    if (rp[r + 1] < rp[r]) atomicOr(flag, 2);
+  for (int64_t k = t0; k < nnz; k += stride) {
+    const int32_t c = ci[k];
+    if (c < 0 || c >= n_cols) atomicOr(flag, 4);
+  }
+}
+
+// ------------------------------------------------------------ transpose --
+__global__ void k_count_cols(int64_t nnz, const int32_t* __restrict__ ci, int32_t* cnt) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += stride)
+    atomicAdd(&cnt[ci[k]], 1);
+}
+
+// Sum of each kScanChunk-element chunk of in[0, n).
+__global__ void __launch_bounds__(1024) k_scan_sums(int64_t n, const int32_t* __restrict__ in,
+                                                    int32_t* sums) {
+  __shared__ int32_t ws[32];
+  const int64_t base = (int64_t)blockIdx.x * kScanChunk;
+  int32_t a = 0;
+  for (int i = 0; i < kScanPer; ++i) {
+    const int64_t idx = base + (int64_t)threadIdx.x * kScanPer + i;
+    if (idx < n) a += in[idx];
+  }
+  for (int d = 16; d > 0; d >>= 1) a += __shfl_xor_sync(0xffffffffu, a, d);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int32_t b = ws[threadIdx.x];
+    for (int d = 16; d > 0; d >>= 1) b += __shfl_xor_sync(0xffffffffu, b, d);
+    if (threadIdx.x == 0) sums[blockIdx.x] = b;
+  }
+}
+
+// Exclusive scan of sums[0, nb) in place, one block.
+__global__ void __launch_bounds__(1024) k_scan_top(int nb, int32_t* sums) {
+  __shared__ int32_t buf[1024];
+  __shared__ int32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nb; base += 1024) {
+    const int i = base + threadIdx.x;
+    const int32_t v = i < nb ? sums[i] : 0;
+    buf[threadIdx.x] = v;
+    __syncthreads();
+    for (int d = 1; d < 1024; d <<= 1) {  // Hillis-Steele inclusive scan
+      const int32_t add = threadIdx.x >= d ? buf[threadIdx.x - d] : 0;
+      __syncthreads();
+      buf[threadIdx.x] += add;
+      __syncthreads();
+    }
+    if (i < nb) sums[i] = carry + buf[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += buf[1023];
+    __syncthreads();
+  }
+}
+
+// out[i] = exclusive prefix of in up to i (i < n), out[n] = total.
+__global__ void __launch_bounds__(1024) k_scan_apply(int64_t n, const int32_t* __restrict__ in,
+                                                     const int32_t* __restrict__ sums,
+                                                     int32_t* out) {
+  __shared__ int32_t ws[32];
+  const int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanPer;
+  int32_t v[kScanPer];
+  int32_t local = 0;
+  for (int i = 0; i < kScanPer; ++i) {
+    v[i] = (base + i < n) ? in[base + i] : 0;
+    local += v[i];
+  }
+  // exclusive scan of `local` across the block
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t inc = local;
+  for (int d = 1; d < 32; d <<= 1) {
+    const int32_t o = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d) inc += o;
+  }
+  if (lane == 31) ws[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    int32_t w = ws[lane];
+    for (int d = 1; d < 32; d <<= 1) {
+      const int32_t o = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= d) w += o;
+    }
+    ws[lane] = w;
+  }
+  __syncthreads();
+  int32_t run = sums[blockIdx.x] + (warp > 0 ? ws[warp - 1] : 0) + inc - local;
+  for (int i = 0; i < kScanPer; ++i) {
+    if (base + i < n) out[base + i] = run;
+    run += v[i];
+  }
+  if (base <= n - 1 && n - 1 < base + kScanPer) out[n] = run - 0;  // total after last element
+}
+
+__global__ void k_copy_i32(int64_t n, const int32_t* __restrict__ a, int32_t* b) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) b[i] = a[i];
+}
+
+__global__ void k_row_ids(int32_t n_rows, const int32_t* __restrict__ rp, int32_t* rowid) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_rows; r += stride)
+    for (int32_t k = rp[r]; k < rp[r + 1]; ++k) rowid[k] = (int32_t)r;
+}
+
+__global__ void k_scatter(int64_t nnz, const int32_t* __restrict__ ci, int32_t* cursor,
+                          int32_t* src) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += stride) {
+    const int32_t pos = atomicAdd(&cursor[ci[k]], 1);
+    src[pos] = (int32_t)k;
+  }
+}
+
+// Sort each row segment of A^T by source position (= row-major order of A),
+// which makes the transpose stable and independent of the scatter's timing.
+// Short segments: insertion sort; long ones: heap sort (in place, O(L log L)).
+__device__ void sift_down(int32_t* a, int root, int len) {
+  while (true) {
+    int c = 2 * root + 1;
+    if (c >= len) return;
+    if (c + 1 < len && a[c + 1] > a[c]) ++c;
+    if (a[root] >= a[c]) return;
+    const int32_t t = a[root];
+    a[root] = a[c];
+    a[c] = t;
+    root = c;
+  }
+}
+
+__global__ void k_segsort(int32_t n_cols, const int32_t* __restrict__ rpt, int32_t* src) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_cols; j += stride) {
+    int32_t* a = src + rpt[j];
+    const int len = rpt[j + 1] - rpt[j];
+    if (len <= 32) {
+      for (int i = 1; i < len; ++i) {
+        const int32_t key = a[i];
+        int p = i - 1;
+        while (p >= 0 && a[p] > key) {
+          a[p + 1] = a[p];
+          --p;
+        }
+        a[p + 1] = key;
+      }
+    } else {
+      for (int r = len / 2 - 1; r >= 0; --r) sift_down(a, r, len);
+      for (int end = len - 1; end > 0; --end) {
+        const int32_t t = a[0];
+        a[0] = a[end];
+        a[end] = t;
+        sift_down(a, 0, end);
+      }
+    }
+  }
+}
+
+__global__ void k_gather_t(int64_t nnz, const int32_t* __restrict__ src,
+                           const int32_t* __restrict__ rowid, const double* __restrict__ va,
+                           int32_t* cit, double* vat) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride) {
+    const int32_t e = src[p];
+    cit[p] = rowid[e];
+    vat[p] = va[e];
+  }
+}
+
+// ------------------------------------------------------------ partition --
+// part[b] = first row r with rp[r] + w*r >= b * (nnz + w*n) / G (b = 0..G).
+__global__ void k_partition(const int32_t* __restrict__ rp, int32_t n, int G, int w,
+                            int32_t* part) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b > G) return;
+  const double total = (double)rp[n] + (double)w * n;
+  const double target = total * b / G;
+  int lo = 0, hi = n;  // smallest r in [0, n] with cost(r) >= target
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const double c = (double)rp[mid] + (double)w * mid;
+    if (c >= target) hi = mid; else lo = mid + 1;
+  }
+  part[b] = (b == G) ? n : lo;
+}
+
+// --------------------------------------------------------- start vector --
+__global__ void __launch_bounds__(kT) k_start_raw(int32_t n, uint64_t seed, double* x,
+                                                  double* blockpart) {
+  __shared__ double scratch[kT / 32];
+  double q[1] = {0.0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double u = (double)(splitmix64_at(seed, (uint64_t)i) >> 11) * 0x1.0p-53;
+    const double xi = 2.0 * u - 1.0;
+    x[i] = xi;
+    q[0] = fma(xi, xi, q[0]);
+  }
+  block_sum<1>(q, scratch);
+  if (threadIdx.x == 0) blockpart[blockIdx.x] = q[0];
+}
+
+__global__ void __launch_bounds__(kT) k_start_scale(int32_t n, double* x,
+                                                    const double* blockpart, int nb) {
+  __shared__ double inv;
+  if (threadIdx.x < 32) {
+    const double q = ordered_sum(blockpart, nb, 1, 0);
+    if (threadIdx.x == 0) inv = 1.0 / sqrt(q);
+  }
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] *= inv;
+}
+
+// ----------------------------------------------------------------- SpMV --
+__global__ void __launch_bounds__(kT) k_spmv(int32_t n_rows, const int32_t* __restrict__ rp,
+                                             const int32_t* __restrict__ ci,
+                                             const double* __restrict__ va,
+                                             const double* __restrict__ x, double* y) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_rows; r += stride)
+    y[r] = row_dot(ci, va, __ldg(rp + r), __ldg(rp + r + 1), x);
+}
+
+// ---------------------------------------------------------------- sigma --
+__device__ __forceinline__ const double* select_x(const double* X0, const double* X1,
+                                                  const double* X2, int k) {
+  return k == 0 ? X0 : (k == 1 ? X1 : X2);
+}
+
+__global__ void __launch_bounds__(kT) k_sigma_part(int32_t n_rows, int32_t n_cols,
+                                                   const int32_t* __restrict__ rp,
+                                                   const int32_t* __restrict__ ci,
+                                                   const double* __restrict__ va,
+                                                   const double* X0, const double* X1,
+                                                   const double* X2, int use_minb,
+                                                   const RunState* st, double* blockpart) {
+  __shared__ double scratch[2 * kT / 32];
+  const double* x = select_x(X0, X1, X2, use_minb ? st->minb : 0);
+  double v[2] = {0.0, 0.0};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_rows; r += stride) {
+    const double yr = row_dot(ci, va, __ldg(rp + r), __ldg(rp + r + 1), x);
+    v[0] = fma(yr, yr, v[0]);
+  }
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_cols; j += stride)
+    v[1] = fma(x[j], x[j], v[1]);
+  block_sum<2>(v, scratch);
+  if (threadIdx.x == 0) {
+    blockpart[2 * blockIdx.x] = v[0];
+    blockpart[2 * blockIdx.x + 1] = v[1];
+  }
+}
+
+__global__ void k_sigma_final(const double* blockpart, int nb, RunState* st) {
+  const double s = ordered_sum(blockpart, nb, 2, 0);
+  const double q = ordered_sum(blockpart, nb, 2, 1);
+  if (threadIdx.x == 0) st->sigma = sqrt(s) / sqrt(q);
+}
+
+}  // namespace
+
+// ====================================================== launch wrappers ==
+
+cudaError_t launch_validate_csr(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t* rp,
+                                const int32_t* ci, int* flag, cudaStream_t s, int64_t* launches) {
+  k_validate<<<grid_for(n_rows > nnz ? n_rows : nnz), kT, 0, s>>>(n_rows, n_cols, nnz, rp, ci,
+                                                                   flag);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+int scan_blocks(int64_t n) { return cdiv(n, kScanChunk) < 1 ? 1 : cdiv(n, kScanChunk); }
+
+cudaError_t launch_transpose(int32_t n_rows, int32_t n_cols, int64_t nnz, const int32_t* rp,
+                             const int32_t* ci, const double* va, int32_t* rpt, int32_t* cit,
+                             double* vat, int32_t* cursor, int32_t* src, int32_t* rowid,
+                             int32_t* blocksums, int* /*long_flag*/, cudaStream_t s,
+                             int64_t* launches) {
+  cudaError_t e = cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (size_t)n_cols, s);
+  if (e != cudaSuccess) return e;
+  if (nnz > 0) {
+    k_count_cols<<<grid_for(nnz), kT, 0, s>>>(nnz, ci, cursor);
+    ++*launches;
+  }
+  const int nb = scan_blocks(n_cols);
+  k_scan_sums<<<nb, 1024, 0, s>>>(n_cols, cursor, blocksums);
+  k_scan_top<<<1, 1024, 0, s>>>(nb, blocksums);
+  k_scan_apply<<<nb, 1024, 0, s>>>(n_cols, cursor, blocksums, rpt);
+  *launches += 3;
+  if (n_cols == 0) {
+    e = cudaMemsetAsync(rpt, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+  }
+  if (nnz > 0) {
+    k_copy_i32<<<grid_for(n_cols), kT, 0, s>>>(n_cols, rpt, cursor);
+    k_row_ids<<<grid_for(n_rows), kT, 0, s>>>(n_rows, rp, rowid);
+    k_scatter<<<grid_for(nnz), kT, 0, s>>>(nnz, ci, cursor, src);
+    k_segsort<<<grid_for(n_cols), kT, 0, s>>>(n_cols, rpt, src);
+    k_gather_t<<<grid_for(nnz), kT, 0, s>>>(nnz, src, rowid, va, cit, vat);
+    *launches += 5;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_partition(const int32_t* rp, int32_t n, int G, int row_weight, int32_t* part,
+                             cudaStream_t s, int64_t* launches) {
+  k_partition<<<cdiv(G + 1, kT), kT, 0, s>>>(rp, n, G, row_weight, part);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+int start_vector_blocks(int32_t n) { return grid_for(n, kT, 152 * 4); }
+
+cudaError_t launch_start_vector(int32_t n, uint64_t seed, double* x, double* blockpart,
+                                cudaStream_t s, int64_t* launches) {
+  const int nb = start_vector_blocks(n);
+  k_start_raw<<<nb, kT, 0, s>>>(n, seed, x, blockpart);
+  k_start_scale<<<nb, kT, 0, s>>>(n, x, blockpart, nb);
+  *launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spmv(int32_t n_rows, const int32_t* rp, const int32_t* ci, const double* va,
+                        const double* x, double* y, cudaStream_t s, int64_t* launches) {
+  if (n_rows == 0) return cudaSuccess;
+  k_spmv<<<grid_for(n_rows), kT, 0, s>>>(n_rows, rp, ci, va, x, y);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+int sigma_blocks(int32_t n_rows, int32_t n_cols) {
+  return grid_for(n_rows > n_cols ? n_rows : n_cols, kT, 152 * 4);
+}
+
+cudaError_t launch_sigma(int32_t n_rows, int32_t n_cols, const int32_t* rp, const int32_t* ci,
+                         const double* va, const double* X0, const double* X1, const double* X2,
+                         int use_minb, RunState* st, double* blockpart, cudaStream_t s,
+                         int64_t* launches) {
+  const int nb = sigma_blocks(n_rows, n_cols);
+  k_sigma_part<<<nb, kT, 0, s>>>(n_rows, n_cols, rp, ci, va, X0, X1, X2, use_minb, st, blockpart);
+  k_sigma_final<<<1, 32, 0, s>>>(blockpart, nb, st);
+  *launches += 2;
+  return cudaGetLastError();
+}
+
+}  // namespace pa
