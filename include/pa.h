@@ -162,6 +162,13 @@ pa_status pa_get_transpose(pa_handle h, int32_t* row_ptr_t, int32_t* col_t, doub
  * handle (host outputs); PA_ERR_INVALID_ARG when the handle has none. */
 pa_status pa_get_equilibration(pa_handle h, double* d_row, double* d_col);
 
+/* Diagnostics of the latest persistent run of the handle: *grid = number of
+ * CTAs, and (when busy_ns is not NULL and holds 2 * *grid entries) the time
+ * each CTA spent working in phase A (y = A x) and in phases B and C (the
+ * transposed product, Adam, the update of x), barrier waits excluded, in
+ * nanoseconds of the GPU's global timer.  Host outputs. */
+pa_status pa_last_run_profile(pa_handle h, int* grid, double* busy_ns);
+
 /* Launches of this library's kernels since the handle was created (a
  * counter kept by the host code at every launch). */
 int64_t pa_kernel_launches(pa_handle h);

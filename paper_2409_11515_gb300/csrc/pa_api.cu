@@ -71,9 +71,11 @@ struct pa_ctx {
   int64_t launches = 0;
   std::vector<DevBuf> bufs;  // everything allocated, freed in pa_destroy
 
-  // matrix
+  // matrix: CSR of A and of A^T (source order), and the sliced-ELL copies
+  // P A Q^T (sa) and Q A^T P^T (st_) that the kernels iterate over
   int32_t *rp = nullptr, *ci = nullptr, *rpt = nullptr, *cit = nullptr;
   double *va = nullptr, *vat = nullptr;
+  Sell sa, sq;
 
   // run buffers (sized for n = max(n_rows, n_cols))
   bool run_ready = false;
@@ -83,7 +85,10 @@ struct pa_ctx {
   double *xmin_max = nullptr, *xmin_min = nullptr;
   RunState* st = nullptr;
   int G = 0;
-  int32_t *part_a = nullptr, *part_t = nullptr;
+  int32_t *part_a = nullptr, *part_t = nullptr, *dep = nullptr;
+  unsigned* ready = nullptr;
+  unsigned long long* cta_ns = nullptr;  // [2G] per-CTA busy time of the last run
+  int last_G = 0;
   double2* bias = nullptr;
   int bias_cap = 0;
   bool have_max = false, have_min = false;
@@ -145,6 +150,60 @@ extern "C" void pa_destroy(pa_handle h) {
 }
 
 extern "C" int64_t pa_kernel_launches(pa_handle h) { return h ? h->launches : -1; }
+
+// Sliced ELL copies P A Q^T and Q A^T P^T: P sorts the rows of A and Q the
+// rows of A^T (the columns of A) by length inside kWindow-row windows.
+static pa_status build_one_sell(pa_ctx* h, int32_t n_rows, const int32_t* rp, const int32_t* ci,
+                                const double* va, const int32_t* lens, const int32_t* col_pos,
+                                Sell* out) {
+  pa_status st;
+  const int32_t ns = sell_slices(n_rows);
+  int32_t *widths = nullptr, *bsums = nullptr;
+  if ((st = alloc_n(h, &out->wp, (size_t)ns + 1, "slice pointers")) ||
+      (st = alloc_n(h, &widths, (size_t)ns + 1, "slice widths")) ||
+      (st = alloc_n(h, &bsums, (size_t)scan_blocks((int64_t)ns + 1) + 1, "scan scratch")))
+    return st;
+  int64_t total = 0;
+  cudaError_t e = launch_sell_build(n_rows, rp, ci, va, lens, col_pos, out, widths, bsums, &total,
+                                    h->stream, &h->launches);
+  if (e != cudaSuccess) return cuda_fail(e, "building slice widths");
+  dev_free(h, widths);
+  dev_free(h, bsums);
+  if ((st = alloc_n(h, &out->col, (size_t)total + 32, "sliced columns")) ||
+      (st = alloc_n(h, &out->val, (size_t)total + 32, "sliced values")))
+    return st;
+  e = launch_sell_fill(n_rows, rp, ci, va, lens, col_pos, *out, h->stream, &h->launches);
+  if (e != cudaSuccess) return cuda_fail(e, "filling the sliced matrix");
+  return PA_OK;
+}
+
+static pa_status build_sell(pa_ctx* h) {
+  pa_status st;
+  int32_t *lens_a = nullptr, *lens_t = nullptr;
+  if ((st = alloc_n(h, &lens_a, (size_t)h->n_rows, "row lengths")) ||
+      (st = alloc_n(h, &lens_t, (size_t)h->n_cols, "column lengths")) ||
+      (st = alloc_n(h, &h->sa.perm, (size_t)h->n_rows, "row permutation")) ||
+      (st = alloc_n(h, &h->sa.pos, (size_t)h->n_rows, "row permutation")) ||
+      (st = alloc_n(h, &h->sq.perm, (size_t)h->n_cols, "column permutation")) ||
+      (st = alloc_n(h, &h->sq.pos, (size_t)h->n_cols, "column permutation")))
+    return st;
+  cudaError_t e;
+  if ((e = launch_row_lengths(h->n_rows, h->rp, lens_a, h->stream, &h->launches)) ||
+      (e = launch_row_lengths(h->n_cols, h->rpt, lens_t, h->stream, &h->launches)) ||
+      (e = launch_window_sort(h->n_rows, lens_a, h->sa.perm, h->sa.pos, h->stream, &h->launches)) ||
+      (e = launch_window_sort(h->n_cols, lens_t, h->sq.perm, h->sq.pos, h->stream, &h->launches)))
+    return cuda_fail(e, "sorting rows by length");
+  // P A Q^T: rows of A in P order, column j of A lands at x position Q(j)
+  if ((st = build_one_sell(h, h->n_rows, h->rp, h->ci, h->va, lens_a, h->sq.pos, &h->sa)))
+    return st;
+  // Q A^T P^T: rows of A^T in Q order, row i of A lands at y position P(i)
+  if ((st = build_one_sell(h, h->n_cols, h->rpt, h->cit, h->vat, lens_t, h->sa.pos, &h->sq)))
+    return st;
+  if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(e, "building the sliced matrices");
+  dev_free(h, lens_a);
+  dev_free(h, lens_t);
+  return PA_OK;
+}
 
 // ---------------------------------------------------------- pa_create --
 
@@ -241,6 +300,7 @@ extern "C" pa_status pa_create(pa_handle* out, int32_t n_rows, int32_t n_cols, i
   dev_free(h, src);
   dev_free(h, rowid);
   dev_free(h, bsums);
+  if ((st = build_sell(h))) return bail(st);
   *out = h;
   return PA_OK;
 }
@@ -283,27 +343,43 @@ static pa_status ensure_partitions(pa_ctx* h, int G) {
   if (h->part_a) dev_free(h, h->part_a);
   if (h->part_t) dev_free(h, h->part_t);
   if (h->partials) dev_free(h, h->partials);
-  h->part_a = h->part_t = nullptr;
+  if (h->dep) dev_free(h, h->dep);
+  if (h->ready) dev_free(h, h->ready);
+  if (h->cta_ns) dev_free(h, h->cta_ns);
+  h->part_a = h->part_t = h->dep = nullptr;
   h->partials = nullptr;
+  h->ready = nullptr;
+  h->cta_ns = nullptr;
   pa_status st;
   if ((st = alloc_n(h, &h->part_a, (size_t)G + 1, "partition")) ||
       (st = alloc_n(h, &h->part_t, (size_t)G + 1, "partition")) ||
+      (st = alloc_n(h, &h->dep, (size_t)2 * G, "dependencies")) ||
+      (st = alloc_n(h, &h->ready, (size_t)G, "ready flags")) ||
+      (st = alloc_n(h, &h->cta_ns, (size_t)2 * G, "CTA timers")) ||
       (st = alloc_n(h, &h->partials, (size_t)G * kPartSlots, "partials")))
     return st;
   cudaError_t e;
-  // phase A rows weigh their non-zeros plus 2; phase B/C rows carry the Adam
-  // update as well (about 24 FP64 operations), hence the heavier row weight.
-  if ((e = launch_partition(h->rp, h->n_rows, G, 2, h->part_a, h->stream, &h->launches)) ||
-      (e = launch_partition(h->rpt, h->n_cols, G, 24, h->part_t, h->stream, &h->launches)))
-    return cuda_fail(e, "partitioning rows");
+  // phase A rows weigh their padded entries plus 2; phase B/C rows carry the
+  // Adam update as well (about 30 FP64 operations), hence the heavier weight.
+  if ((e = launch_partition(h->sa.wp, h->sa.n_slices, G, 2, h->part_a, h->stream, &h->launches)) ||
+      (e = launch_partition(h->sq.wp, h->sq.n_slices, G, 30, h->part_t, h->stream, &h->launches)))
+    return cuda_fail(e, "partitioning slices");
+  if ((e = launch_dependencies(h->sa.wp, h->sa.col, h->sa.val, h->part_a, h->part_t, G, h->dep,
+                               h->stream, &h->launches)))
+    return cuda_fail(e, "finding neighbour dependencies");
   h->G = G;
   return PA_OK;
 }
 
-static pa_status ensure_bias(pa_ctx* h, int iters, double lr, double b1, double b2) {
+// Per-iteration Adam scalars: the step lr m_hat / (sqrt(v_hat) + eps) with
+// m_hat = m / (1 - b1^t), v_hat = v / (1 - b2^t) equals K1 m / (sqrt(v) + K2)
+// with K1 = lr sqrt(1 - b2^t) / (1 - b1^t) and K2 = eps sqrt(1 - b2^t).
+static pa_status ensure_bias(pa_ctx* h, int iters, double lr, double b1, double b2, double eps) {
   std::vector<double2> tab((size_t)std::max(iters, 1));
-  for (int t = 1; t <= iters; ++t)
-    tab[t - 1] = make_double2(lr / (1.0 - pow(b1, (double)t)), 1.0 / (1.0 - pow(b2, (double)t)));
+  for (int t = 1; t <= iters; ++t) {
+    const double r2 = sqrt(1.0 - pow(b2, (double)t));
+    tab[t - 1] = make_double2(lr * r2 / (1.0 - pow(b1, (double)t)), eps * r2);
+  }
   if (h->bias_cap < iters) {
     if (h->bias) dev_free(h, h->bias);
     h->bias = nullptr;
@@ -340,23 +416,28 @@ static pa_status run_one(pa_ctx* h, pa_mode mode, int iters, double lr, double b
   const int G = choose_grid(h, &maxG);
   if (G <= 0) return fail(PA_ERR_LAUNCH, "the persistent kernel does not fit on this GPU");
   pa_status st;
-  if ((st = ensure_partitions(h, G)) || (st = ensure_bias(h, iters, lr, b1, b2))) return st;
+  if ((st = ensure_partitions(h, G)) || (st = ensure_bias(h, iters, lr, b1, b2, eps))) return st;
   const size_t n = (size_t)h->n_cols;
   cudaError_t e;
   if ((e = cudaMemcpyAsync(h->X0, h->Xinit, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream)) ||
       (e = cudaMemsetAsync(h->m, 0, sizeof(double) * n, h->stream)) ||
       (e = cudaMemsetAsync(h->v, 0, sizeof(double) * n, h->stream)) ||
-      (e = cudaMemsetAsync(h->st, 0, sizeof(RunState), h->stream)))
+      (e = cudaMemsetAsync(h->st, 0, sizeof(RunState), h->stream)) ||
+      (e = cudaMemsetAsync(h->ready, 0, sizeof(unsigned) * G, h->stream)))
     return cuda_fail(e, "preparing the run");
   IterParams p{};
   p.n_rows = h->n_rows;
   p.n_cols = h->n_cols;
-  p.rp = h->rp; p.ci = h->ci; p.va = h->va;
-  p.rpt = h->rpt; p.cit = h->cit; p.vat = h->vat;
+  p.a_wp = h->sa.wp; p.a_col = h->sa.col; p.a_val = h->sa.val;
+  p.t_wp = h->sq.wp; p.t_col = h->sq.col; p.t_val = h->sq.val;
   p.part_a = h->part_a; p.part_t = h->part_t;
   p.X0 = h->X0; p.X1 = h->X1; p.X2 = h->X2;
   p.m = h->m; p.v = h->v; p.y = h->y; p.ylo = h->ylo; p.dx = h->dx;
   p.partials = h->partials;
+  p.ready = h->ready;
+  p.cta_ns = h->cta_ns;
+  h->last_G = G;
+  p.dep = h->dep;
   p.bias = h->bias;
   p.L_trace = L_trace_dev;
   p.x_trace = x_trace_dev;
@@ -372,15 +453,15 @@ static pa_status run_one(pa_ctx* h, pa_mode mode, int iters, double lr, double b
   if (e == cudaErrorCooperativeLaunchTooLarge)
     return fail(PA_ERR_LAUNCH, "cooperative grid of %d CTAs does not fit (max %d)", G, maxG);
   if (e != cudaSuccess) return cuda_fail(e, "launching the persistent kernel");
-  if ((e = launch_sigma(h->n_rows, h->n_cols, h->rp, h->ci, h->va, h->X0, h->X1, h->X2, 1, h->st,
-                        h->blockpart, h->stream, &h->launches)))
+  if ((e = launch_sigma(h->sa, h->n_cols, h->X0, h->X1, h->X2, 1, h->st, h->blockpart, h->stream,
+                        &h->launches)))
     return cuda_fail(e, "launching the sigma kernel");
   if ((e = cudaMemcpyAsync(out, h->st, sizeof(RunState), cudaMemcpyDeviceToHost, h->stream)) ||
       (e = cudaStreamSynchronize(h->stream)))
     return cuda_fail(e, "running Projected Adam");
   double* keep = mode == PA_SIGMA_MAX ? h->xmin_max : h->xmin_min;
   double* src = out->minb == 0 ? h->X0 : (out->minb == 1 ? h->X1 : h->X2);
-  if ((e = cudaMemcpyAsync(keep, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream)))
+  if ((e = launch_unpermute(h->n_cols, 1, h->sq.pos, src, keep, h->stream, &h->launches)))
     return cuda_fail(e, "keeping x_min");
   if (out->status == PA_ERR_TIMEOUT)
     return fail(PA_ERR_TIMEOUT, "a grid barrier wait ran out of time (barrier %d)", out->timeout_site);
@@ -405,9 +486,12 @@ extern "C" pa_status pa_run(pa_handle h, pa_mode mode, int iters, double lr, dou
   pa_status st;
   if ((st = check_hyper(iters, lr, beta1, beta2, eps)) || (st = ensure_run_buffers(h))) return st;
   const size_t n = (size_t)h->n_cols;
-  cudaError_t e = cudaMemcpyAsync(h->Xinit, x_init, sizeof(double) * n,
+  // x_init arrives in source order; the kernels work in the column order Q
+  cudaError_t e = cudaMemcpyAsync(h->dx, x_init, sizeof(double) * n,
                                   x_kind == PA_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                                   h->stream);
+  if (e == cudaSuccess)
+    e = launch_permute(h->n_cols, h->sq.pos, h->dx, h->Xinit, h->stream, &h->launches);
   if (e != cudaSuccess) return cuda_fail(e, "copying x_init");
   double *Ld = nullptr, *Xd = nullptr;
   if (L_trace && iters > 0 && (st = alloc_n(h, &Ld, (size_t)iters, "L trace"))) return st;
@@ -419,13 +503,28 @@ extern "C" pa_status pa_run(pa_handle h, pa_mode mode, int iters, double lr, dou
   pa_status rst = run_one(h, mode, iters, lr, beta1, beta2, eps, Ld, Xd, x_trace ? n_trace : 0, &rs);
   if (rst >= 0) {
     double* xs[3] = {h->X0, h->X1, h->X2};
-    if (x_min) e = cudaMemcpyAsync(x_min, xs[rs.minb], sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess && x_last)
-      e = cudaMemcpyAsync(x_last, xs[rs.cur], sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
+    double* keep = mode == PA_SIGMA_MAX ? h->xmin_max : h->xmin_min;  // source order
+    if (x_min) e = cudaMemcpyAsync(x_min, keep, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && x_last) {
+      e = launch_unpermute(h->n_cols, 1, h->sq.pos, xs[rs.cur], h->dx, h->stream, &h->launches);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(x_last, h->dx, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
+    }
     if (e == cudaSuccess && Ld)
       e = cudaMemcpyAsync(L_trace, Ld, sizeof(double) * iters, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess && Xd)
-      e = cudaMemcpyAsync(x_trace, Xd, sizeof(double) * n_trace * n, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && Xd) {
+      double* Xs = nullptr;
+      if (alloc_n(h, &Xs, (size_t)n_trace * n, "x trace") != PA_OK) {
+        e = cudaErrorMemoryAllocation;
+      } else {
+        e = launch_unpermute(h->n_cols, n_trace, h->sq.pos, Xd, Xs, h->stream, &h->launches);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(x_trace, Xs, sizeof(double) * n_trace * n, cudaMemcpyDeviceToHost,
+                              h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        dev_free(h, Xs);
+      }
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) rst = cuda_fail(e, "reading results");
     if (rst >= 0) {
@@ -454,7 +553,8 @@ extern "C" pa_status pa_estimate(pa_handle h, pa_mode mode, int iters, double lr
   if ((st = check_hyper(iters, lr, beta1, beta2, eps)) || (st = ensure_run_buffers(h))) return st;
   if ((mode & PA_SIGMA_MIN) && h->n_rows < h->n_cols)
     return fail(PA_ERR_NOT_SQUARE, "sigma_min needs n_rows >= n_cols (%d x %d)", h->n_rows, h->n_cols);
-  cudaError_t e = launch_start_vector(h->n_cols, seed, h->Xinit, h->blockpart, h->stream, &h->launches);
+  cudaError_t e = launch_start_vector(h->n_cols, seed, h->sq.pos, h->Xinit, h->blockpart, h->stream,
+                                      &h->launches);
   if (e != cudaSuccess) return cuda_fail(e, "building the start vector");
   pa_status worst = PA_OK;
   RunState rs{};
@@ -489,36 +589,37 @@ extern "C" pa_status pa_get_vector(pa_handle h, pa_mode which, double* x_min_hos
   return PA_OK;
 }
 
+// y = A x (or z = A^T y) through the sliced copies: permute the input into
+// the kernel order, multiply, map the output back to source order.
 static pa_status product(pa_handle h, bool transposed, const double* in, double* out, int kind) {
   g_err.clear();
   if (!h || !in || !out) return fail(PA_ERR_INVALID_ARG, "NULL argument");
   if (kind != PA_HOST && kind != PA_DEVICE) return fail(PA_ERR_INVALID_ARG, "bad ptr_kind");
+  const Sell& M = transposed ? h->sq : h->sa;
+  const int32_t* pos_in = transposed ? h->sa.pos : h->sq.pos;
   const int32_t n_in = transposed ? h->n_rows : h->n_cols;
   const int32_t n_out = transposed ? h->n_cols : h->n_rows;
-  const double* din = in;
-  double* dout = out;
   pa_status st;
-  if (kind == PA_HOST) {
-    double *a = nullptr, *b = nullptr;
-    if ((st = alloc_n(h, &a, (size_t)n_in, "product input")) ||
-        (st = alloc_n(h, &b, (size_t)n_out, "product output")))
-      return st;
-    cudaError_t e = cudaMemcpyAsync(a, in, sizeof(double) * n_in, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess)
-      e = transposed ? launch_spmv(h->n_cols, h->rpt, h->cit, h->vat, a, b, h->stream, &h->launches)
-                     : launch_spmv(h->n_rows, h->rp, h->ci, h->va, a, b, h->stream, &h->launches);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(out, b, sizeof(double) * n_out, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    dev_free(h, a);
-    dev_free(h, b);
-    if (e != cudaSuccess) return cuda_fail(e, "sparse product");
-    return PA_OK;
-  }
-  cudaError_t e = transposed
-                      ? launch_spmv(h->n_cols, h->rpt, h->cit, h->vat, din, dout, h->stream, &h->launches)
-                      : launch_spmv(h->n_rows, h->rp, h->ci, h->va, din, dout, h->stream, &h->launches);
+  double *a = nullptr, *ap = nullptr, *bp = nullptr, *b = nullptr;
+  if ((st = alloc_n(h, &a, (size_t)n_in, "product input")) ||
+      (st = alloc_n(h, &ap, (size_t)n_in, "product input")) ||
+      (st = alloc_n(h, &bp, (size_t)n_out, "product output")) ||
+      (st = alloc_n(h, &b, (size_t)n_out, "product output")))
+    return st;
+  cudaError_t e = cudaMemcpyAsync(a, in, sizeof(double) * n_in,
+                                  kind == PA_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                  h->stream);
+  if (e == cudaSuccess) e = launch_permute(n_in, pos_in, a, ap, h->stream, &h->launches);
+  if (e == cudaSuccess) e = launch_sell_spmv(M, ap, bp, h->stream, &h->launches);
+  if (e == cudaSuccess) e = launch_unpermute(n_out, 1, M.pos, bp, b, h->stream, &h->launches);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, b, sizeof(double) * n_out,
+                        kind == PA_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  dev_free(h, a);
+  dev_free(h, ap);
+  dev_free(h, bp);
+  dev_free(h, b);
   if (e != cudaSuccess) return cuda_fail(e, "sparse product");
   return PA_OK;
 }
@@ -544,6 +645,20 @@ extern "C" pa_status pa_get_transpose(pa_handle h, int32_t* row_ptr_t, int32_t* 
     e = cudaMemcpyAsync(val_t, h->vat, sizeof(double) * h->nnz, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "reading the transpose");
+  return PA_OK;
+}
+
+extern "C" pa_status pa_last_run_profile(pa_handle h, int* grid, double* busy_ns) {
+  g_err.clear();
+  if (!h || !grid) return fail(PA_ERR_INVALID_ARG, "NULL argument");
+  *grid = h->last_G;
+  if (!busy_ns || h->last_G == 0) return PA_OK;
+  std::vector<unsigned long long> t((size_t)2 * h->last_G);
+  cudaError_t e = cudaMemcpyAsync(t.data(), h->cta_ns, sizeof(unsigned long long) * t.size(),
+                                  cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the run profile");
+  for (size_t i = 0; i < t.size(); ++i) busy_ns[i] = (double)t[i];
   return PA_OK;
 }
 

@@ -94,4 +94,52 @@ __device__ __forceinline__ double row_dot(const int32_t* __restrict__ ci,
   return acc;
 }
 
+// Dot product of lane `lane`'s row of slice s of a sliced-ELL matrix with x:
+// entry k sits at 32 * (wp[s] + k) + lane; padding entries hold 0.0.
+__device__ __forceinline__ double slice_dot(const int32_t* __restrict__ wp,
+                                            const int32_t* __restrict__ col,
+                                            const double* __restrict__ val, int s, int lane,
+                                            const double* x) {
+  const int w0 = __ldg(wp + s), w = __ldg(wp + s + 1) - w0;
+  const int64_t base = 32ll * w0 + lane;
+  const int32_t* __restrict__ c = col + base;
+  const double* __restrict__ v = val + base;
+  double acc = 0.0;
+  int k = 0;
+  for (; k + 4 <= w; k += 4) {
+    const int c0 = __ldg(c + 32 * k), c1 = __ldg(c + 32 * (k + 1)), c2 = __ldg(c + 32 * (k + 2)),
+              c3 = __ldg(c + 32 * (k + 3));
+    const double v0 = __ldg(v + 32 * k), v1 = __ldg(v + 32 * (k + 1)),
+                 v2 = __ldg(v + 32 * (k + 2)), v3 = __ldg(v + 32 * (k + 3));
+    const double x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
+    acc = fma(v0, x0, acc);
+    acc = fma(v1, x1, acc);
+    acc = fma(v2, x2, acc);
+    acc = fma(v3, x3, acc);
+  }
+  for (; k < w; ++k) acc = fma(__ldg(v + 32 * k), x[__ldg(c + 32 * k)], acc);
+  return acc;
+}
+
+// Block sum of NV per-thread values, result in thread 0 only.  Every thread
+// stores its values in `scratch` (NV * blockDim.x doubles); warp 0 adds them
+// in a fixed order (lane l sums threads l, l+32, ... sequentially, then a
+// butterfly), so the result does not depend on timing.
+template <int NV>
+__device__ __forceinline__ void block_sum_to0(double (&v)[NV], double* scratch) {
+  const int nt = blockDim.x;
+  __syncthreads();  // scratch may still be read from a previous call
+#pragma unroll
+  for (int i = 0; i < NV; ++i) scratch[i * nt + threadIdx.x] = v[i];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double a = 0.0;
+      for (int t = threadIdx.x; t < nt; t += 32) a += scratch[i * nt + t];
+      v[i] = warp_sum(a);
+    }
+  }
+}
+
 }  // namespace pa

@@ -29,19 +29,38 @@ struct RunState {
   double pad;
 };
 
+// A row- and column-permuted copy P A Q^T of a matrix in sliced ELL form:
+// rows are stable-sorted by length (descending) inside windows of kWindow
+// rows, cut into slices of 32 rows, and each slice is stored column-major
+// (entry k of lane l at 32 * (wp[s] + k) + l) padded to its longest row with
+// zero values.  Entry order inside a row is the order of the source CSR.
+constexpr int kWindow = 1024;
+struct Sell {
+  int32_t n_rows = 0;      // rows of the permuted matrix
+  int32_t n_slices = 0;    // ceil(n_rows / 32)
+  int32_t* wp = nullptr;   // [n_slices + 1] exclusive scan of slice widths
+  int32_t* col = nullptr;  // [32 * wp[n_slices]] permuted column positions
+  double* val = nullptr;   // [32 * wp[n_slices]]
+  int32_t* perm = nullptr; // [n_rows] position -> source row
+  int32_t* pos = nullptr;  // [n_rows] source row -> position
+};
+
 // Everything one Projected Adam run needs; passed by value to the kernels.
 struct IterParams {
   int32_t n_rows, n_cols;
-  const int32_t* rp;  const int32_t* ci;  const double* va;   // A (CSR)
-  const int32_t* rpt; const int32_t* cit; const double* vat;  // A^T (CSR)
-  const int32_t* part_a;   // [G+1] row ranges of A per CTA
-  const int32_t* part_t;   // [G+1] row ranges of A^T per CTA
+  const int32_t* a_wp; const int32_t* a_col; const double* a_val;  // P A Q^T (sliced ELL)
+  const int32_t* t_wp; const int32_t* t_col; const double* t_val;  // Q A^T P^T
+  const int32_t* part_a;   // [G+1] slice ranges of P A Q^T per CTA
+  const int32_t* part_t;   // [G+1] slice ranges of Q A^T P^T per CTA (own x rows)
   double* X0; double* X1; double* X2;  // three iterate buffers
   double* m; double* v;                // Adam moments
   double* y; double* ylo;              // y = A x (ylo: low part, compensated mode)
   double* dx;                          // Adam step of the current iteration
   double* partials;                    // [G][kPartSlots]
-  const double2* bias;                 // [iters]: {lr/(1-b1^t), 1/(1-b2^t)}
+  unsigned* ready;                     // [G] last iteration whose x_t each CTA has written
+  unsigned long long* cta_ns;          // [2G] per-CTA time in phases A and B+C (ns), or null
+  const int32_t* dep;                  // [2G] CTAs whose x rows CTA b's phase A reads: [lo, hi]
+  const double2* bias;                 // [iters]: {lr sqrt(1-b2^t)/(1-b1^t), eps sqrt(1-b2^t)}
   double* L_trace;                     // [iters] or null
   double* x_trace;                     // [n_trace][n_cols] or null
   int n_trace;
@@ -71,23 +90,56 @@ cudaError_t launch_transpose(int32_t n_rows, int32_t n_cols, int64_t nnz, const 
                              int32_t* blocksums, int* long_flag, cudaStream_t s,
                              int64_t* launches);
 
-cudaError_t launch_partition(const int32_t* rp, int32_t n, int G, int row_weight, int32_t* part,
-                             cudaStream_t s, int64_t* launches);
+// Slice partition of the persistent grid: part[b] = first slice whose
+// cumulative cost 32 * wp[s] + row_weight * 32 * s reaches b / G of the total.
+cudaError_t launch_partition(const int32_t* wp, int32_t n_slices, int G, int row_weight,
+                             int32_t* part, cudaStream_t s, int64_t* launches);
 
-cudaError_t launch_start_vector(int32_t n, uint64_t seed, double* x, double* blockpart,
-                                cudaStream_t s, int64_t* launches);
+// Sliced ELL of P M Q^T from CSR(M): perm/pos of the rows (window sort by
+// length), then slice widths, their scan and the column-major fill; col
+// indices go through col_pos (the column permutation).  `lens` and `widths`
+// are scratch of n_rows and n_slices + 1 entries, `blocksums` of
+// scan_blocks(n_slices + 1).
+int32_t sell_slices(int32_t n_rows);
+cudaError_t launch_row_lengths(int32_t n_rows, const int32_t* rp, int32_t* lens, cudaStream_t s,
+                               int64_t* launches);
+cudaError_t launch_window_sort(int32_t n, const int32_t* lens, int32_t* perm, int32_t* pos,
+                               cudaStream_t s, int64_t* launches);
+cudaError_t launch_sell_build(int32_t n_rows, const int32_t* rp, const int32_t* ci,
+                              const double* va, const int32_t* lens, const int32_t* col_pos,
+                              Sell* out, int32_t* widths, int32_t* blocksums, int64_t* total,
+                              cudaStream_t s, int64_t* launches);
+cudaError_t launch_sell_fill(int32_t n_rows, const int32_t* rp, const int32_t* ci,
+                             const double* va, const int32_t* lens, const int32_t* col_pos,
+                             const Sell& out, cudaStream_t s, int64_t* launches);
+
+// out[pos[i]] = in[i] (to permuted order) and out[i] = in[pos[i]] (back).
+cudaError_t launch_permute(int32_t n, const int32_t* pos, const double* in, double* out,
+                           cudaStream_t s, int64_t* launches);
+cudaError_t launch_unpermute(int32_t n, int32_t count, const int32_t* pos, const double* in,
+                             double* out, cudaStream_t s, int64_t* launches);
+
+// Start vector in source coordinates i, written at position pos[i], normalised.
+cudaError_t launch_start_vector(int32_t n, uint64_t seed, const int32_t* pos, double* x,
+                                double* blockpart, cudaStream_t s, int64_t* launches);
 int start_vector_blocks(int32_t n);
 
-cudaError_t launch_spmv(int32_t n_rows, const int32_t* rp, const int32_t* ci, const double* va,
-                        const double* x, double* y, cudaStream_t s, int64_t* launches);
+// y = M x for a sliced-ELL matrix (permuted coordinates on both sides).
+cudaError_t launch_sell_spmv(const Sell& m, const double* x, double* y, cudaStream_t s,
+                             int64_t* launches);
 
-// sigma = ||A x_sel|| / ||x_sel|| where x_sel is the buffer st->minb of
+// sigma = ||M x_sel|| / ||x_sel|| where x_sel is the buffer st->minb of
 // {X0, X1, X2} (or X0 when use_minb == 0); result into st->sigma.
-int sigma_blocks(int32_t n_rows, int32_t n_cols);
-cudaError_t launch_sigma(int32_t n_rows, int32_t n_cols, const int32_t* rp, const int32_t* ci,
-                         const double* va, const double* X0, const double* X1, const double* X2,
-                         int use_minb, RunState* st, double* blockpart, cudaStream_t s,
-                         int64_t* launches);
+int sigma_blocks(int32_t n_slices, int32_t n_cols);
+cudaError_t launch_sigma(const Sell& m, int32_t n_cols, const double* X0, const double* X1,
+                         const double* X2, int use_minb, RunState* st, double* blockpart,
+                         cudaStream_t s, int64_t* launches);
+
+// dep[2b], dep[2b+1] = first and last CTA owning an x position that a
+// non-zero of CTA b's slices of the (permuted) matrix reads.
+cudaError_t launch_dependencies(const int32_t* wp, const int32_t* col, const double* val,
+                                const int32_t* part_a, const int32_t* part_t, int G,
+                                int32_t* dep, cudaStream_t s, int64_t* launches);
 
 // Persistent cooperative Projected Adam run (Algorithm 1) over a grid of G CTAs.
 int persistent_max_blocks(int loss, int* blocks_per_sm);

@@ -1,20 +1,30 @@
 // pa_iter.cu -- the persistent cooperative Projected Adam kernel (the paper's
 // Algorithm 1 with the gradient of Eq. nabla_loss) for one vector.
 //
-// One launch runs every iteration without returning to the host.  CTA b owns
-// a contiguous block of rows of A (phase A) and of A^T (phases B and C); the
-// blocks are balanced by non-zeros.  Per iteration t:
+// The matrix is held as P A Q^T and Q A^T P^T in sliced ELL form (rows sorted
+// by length inside windows, 32-row slices stored column-major), so the 32
+// lanes of a warp walk rows of equal length with coalesced loads; sigma and
+// Algorithm 1 are unchanged by the permutations, which only relabel the
+// coordinates of x (Q) and of y (P).
 //
-//   A  y = A x_{t-1} (own rows); partial s = sum y_i^2         | grid barrier
+// One launch runs every iteration without returning to the host.  CTA b owns
+// a contiguous range of slices of P A Q^T (phase A) and of Q A^T P^T (phases
+// B and C); the ranges are balanced by padded entries plus a per-row weight.
+// Per iteration t:
+//
+//   A  y = A x_{t-1} (own rows); partials s = sum y_i^2, q = ||x||^2 | grid barrier
 //      every CTA sums the partials in the same fixed order -> s, q = ||x||^2;
 //      L(x_{t-1}) is scored against L_min (Algorithm 1's tracking, lagged by
 //      one product so that y serves both the score and the gradient).
-//   B  z = A^T y over the explicit CSR of A^T (own rows), the gradient
+//   B  z = A^T y over the explicit transpose (own rows), the gradient
 //      g = a x + b z, Adam's moments and step dx (kept in `dx`), partials
 //      p1 = x.dx, p2 = dx.dx                                  | grid barrier
 //   C  x_t = ((1 + p1) x - dx) / ||.||, the tangent projection and the
 //      normalisation of Algorithm 1 in one pass; ||.||^2 comes from the
-//      partials: (1 + p1)^2 q - 2 (1 + p1) p1 + p2; partial q of x_t  | barrier
+//      partials: (1 + p1)^2 q - 2 (1 + p1) p1 + p2.  The CTA then publishes
+//      "x_t written" on its ready flag; the next phase A waits only for the
+//      flags of the CTAs whose x rows its products read (a banded operator
+//      reads a few neighbours), not for the whole grid.
 //
 // Three iterate buffers rotate so that x_min never needs a copy: the buffer
 // holding the best iterate is kept out of the rotation until it is beaten.
@@ -32,8 +42,19 @@ namespace pa {
 namespace {
 
 struct Shared {
-  double scratch[4 * kBlock / 32];
+  double scratch[2 * kBlock];
+  // per-iteration scalars, computed once by thread 0 and read by all threads
+  double ca, cb;      // g = ca * x + cb * z
+  double c, inv;      // projection coefficient and 1 / ||x'||
+  int brk;            // leave the iteration loop
+  int cur, nb;        // buffer of x_{t-1}, buffer for x_t
   int ok;
+  // Algorithm 1's tracking state, owned by thread 0
+  double L_min, L_last;
+  int minb, t_min, iters_run, status;
+  // busy time per phase (barrier waits excluded), read by the partition tuner
+  unsigned long long busy_a, busy_b;
+  long long tmark;
 };
 
 // Grid-wide barrier with a time limit.  Returns false when the wait gave up
@@ -71,6 +92,44 @@ __device__ __forceinline__ bool grid_barrier(RunState* st, unsigned& target, uns
   return sh.ok != 0;
 }
 
+// Wait until every CTA in [lo, hi] has published iterate t (its ready flag
+// reaches t), with the same time limit and abort flag as grid_barrier.  Only
+// the CTAs whose x rows this CTA's products read take part, so this replaces
+// a grid-wide barrier between the update of x and the next product.
+__device__ __forceinline__ bool wait_ready(RunState* st, const unsigned* ready, int lo, int hi,
+                                           unsigned t, long long timeout_ns, int site,
+                                           Shared& sh) {
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const long long t0 = globaltimer_ns();
+    int spins = 0;
+    for (int j = lo; j <= hi && ok; ++j) {
+      while (true) {
+        const unsigned c = ld_acquire_u32(ready + j);
+        if ((int)(c - t) >= 0) break;
+        if (ld_relaxed_u32(&st->abort) != 0u) { ok = 0; break; }
+        if (++spins > 64) {
+          if (globaltimer_ns() - t0 > timeout_ns) {
+            if (atomicExch(&st->abort, 1u) == 0u) st->timeout_site = site;
+            ok = 0;
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+    }
+    __threadfence();
+    sh.ok = ok;
+  }
+  __syncthreads();
+  return sh.ok != 0;
+}
+
+__device__ __forceinline__ void publish_ready(unsigned* flag, unsigned t) {
+  __threadfence();
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(flag), "r"(t) : "memory");
+}
+
 __device__ __forceinline__ double* pick(const IterParams& p, int k) {
   return k == 0 ? p.X0 : (k == 1 ? p.X1 : p.X2);
 }
@@ -84,155 +143,218 @@ __device__ __forceinline__ double loss_value(int mode, int loss, double s, doubl
 template <int LOSS>
 __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const IterParams p) {
   __shared__ Shared sh;
+  constexpr int NW = kBlock / 32;
   const unsigned G = gridDim.x;
-  const int b = blockIdx.x, tid = threadIdx.x;
-  const int a0 = p.part_a[b], a1 = p.part_a[b + 1];
-  const int c0 = p.part_t[b], c1 = p.part_t[b + 1];
+  const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int sa0 = p.part_a[b], sa1 = p.part_a[b + 1];
+  const int st0 = p.part_t[b], st1 = p.part_t[b + 1];
   const int n = p.n_cols;
+  const int r0 = 32 * st0, r1 = min(32 * st1, n);  // own rows of x (positions)
   RunState* st = p.st;
   double* __restrict__ part = p.partials;
 
-  int cur = 0, minb = 0, t_min = 0, iters_run = 0;
-  double L_min = INFINITY, L_last = NAN;
-  int status = PA_OK;
+  // Algorithm 1's scalar state lives in shared memory, written by thread 0
+  // of every CTA (each CTA computes the same values from the same
+  // fixed-order sums).
   unsigned target = 0;
   int site = 0;
+  int status = PA_OK;  // this thread's view; thread 0 keeps the run's status in sh
+  if (tid == 0) {
+    sh.cur = 0;
+    sh.brk = 0;
+    sh.minb = 0;
+    sh.t_min = 0;
+    sh.iters_run = 0;
+    sh.status = PA_OK;
+    sh.L_min = INFINITY;
+    sh.L_last = NAN;
+    sh.busy_a = sh.busy_b = 0;
+  }
 
-  // ||x_init||^2, partial over the own rows of A^T
+  const int dlo = p.dep[2 * b], dhi = p.dep[2 * b + 1];
+
+
+  // per-thread partial of ||x||^2 over the own rows, carried into phase A
+  double qloc = 0.0;
   {
-    double v[1] = {0.0};
-    const double* x = pick(p, cur);
-    for (int j = c0 + tid; j < c1; j += kBlock) v[0] = fma(x[j], x[j], v[0]);
-    block_sum<1>(v, sh.scratch);
-    if (tid == 0) part[b * kPartSlots + 1] = v[0];
+    const double* x = pick(p, 0);
+    for (int j = r0 + tid; j < r1; j += kBlock) qloc = fma(x[j], x[j], qloc);
   }
 
   for (int t = 1;; ++t) {
-    const double* x = pick(p, cur);
-    // ---- phase A: y = A x, partial ||y||^2
+    // x_{t-1} of the neighbours must be written before the gathers below
+    if (t > 1 && !wait_ready(st, p.ready, dlo, dhi, (unsigned)(t - 1), p.timeout_ns, site++, sh)) {
+      status = PA_ERR_TIMEOUT;
+      break;
+    }
+    const double* x = pick(p, sh.cur);
+    if (tid == 0) sh.tmark = globaltimer_ns();
+    // ---- phase A: y = A x, partials ||y||^2 and ||x||^2
     {
-      double v[1] = {0.0};
-      for (int r = a0 + tid; r < a1; r += kBlock) {
-        const double yr = row_dot(p.ci, p.va, __ldg(p.rp + r), __ldg(p.rp + r + 1), x);
-        p.y[r] = yr;
-        v[0] = fma(yr, yr, v[0]);
+      double v[2] = {0.0, qloc};
+      for (int s = sa0 + warp; s < sa1; s += NW) {
+        const double yr = slice_dot(p.a_wp, p.a_col, p.a_val, s, lane, x);
+        const int r = 32 * s + lane;
+        if (r < p.n_rows) {
+          p.y[r] = yr;
+          v[0] = fma(yr, yr, v[0]);
+        }
       }
-      block_sum<1>(v, sh.scratch);
-      if (tid == 0) part[b * kPartSlots + 0] = v[0];
+      block_sum_to0<2>(v, sh.scratch);
+      if (tid == 0) {
+        part[b * kPartSlots + 0] = v[0];
+        part[b * kPartSlots + 1] = v[1];
+        sh.busy_a += (unsigned long long)(globaltimer_ns() - sh.tmark);
+      }
     }
     const bool skip = (p.skip_arrival == t) && (b == 0);
     if (!grid_barrier(st, target, G, p.timeout_ns, skip, site++, sh)) { status = PA_ERR_TIMEOUT; break; }
-    double s, q;
-    {
-      if (tid < 32) {
-        const double s_ = ordered_sum(part, G, kPartSlots, 0);
-        const double q_ = ordered_sum(part, G, kPartSlots, 1);
-        if (tid == 0) { sh.scratch[0] = s_; sh.scratch[1] = q_; }
+    if (tid < 32) {
+      const double s_ = ordered_sum(part, G, kPartSlots, 0);
+      const double q = ordered_sum(part, G, kPartSlots, 1);
+      if (tid == 0) {
+        int brk = 0;
+        const int cur = sh.cur;
+        if (!isfinite(s_) || !isfinite(q)) {
+          sh.status = PA_ERR_NONFINITE;
+          brk = 1;
+        } else {
+          if (t > 1) {  // score x_{t-1}, the iterate produced by the previous iteration
+            const double L = loss_value(p.mode, LOSS, s_, q);
+            sh.L_last = L;
+            if (p.L_trace && b == 0) p.L_trace[t - 2] = L;
+            if (L < sh.L_min) { sh.L_min = L; sh.t_min = t - 1; sh.minb = cur; }
+          }
+          if (s_ == 0.0) {
+            if (p.mode == PA_SIGMA_MIN && t == 1) {
+              sh.L_min = loss_value(p.mode, LOSS, s_, q);
+              sh.t_min = 0;
+              sh.minb = cur;
+            }
+            sh.status = PA_WARN_SINGULAR;
+            brk = 1;
+          } else if (t == p.iters + 1) {
+            brk = 1;
+          }
+        }
+        // g' = (1 - beta1) g = ca x + cb z: the first moment's weight is
+        // folded into the gradient coefficients
+        double ca, cb;
+        if (LOSS == PA_LOSS_QUADRATIC) { ca = 0.0; cb = -2.0; }
+        else { ca = 1.0 / q; cb = -1.0 / s_; }
+        if (p.mode == PA_SIGMA_MIN) { ca = -ca; cb = -cb; }
+        const double omb1 = 1.0 - p.beta1;
+        sh.ca = omb1 * ca;
+        sh.cb = omb1 * cb;
+        sh.scratch[0] = q;  // kept for the normalisation below
+        sh.brk = brk;
       }
-      __syncthreads();
-      s = sh.scratch[0];
-      q = sh.scratch[1];
-      __syncthreads();
     }
-    if (!isfinite(s) || !isfinite(q)) { status = PA_ERR_NONFINITE; break; }
-    if (t > 1) {  // score x_{t-1}, the iterate produced by the previous iteration
-      const double L = loss_value(p.mode, LOSS, s, q);
-      L_last = L;
-      if (p.L_trace && b == 0 && tid == 0) p.L_trace[t - 2] = L;
-      if (L < L_min) { L_min = L; t_min = t - 1; minb = cur; }
-    }
-    if (s == 0.0) {
-      if (p.mode == PA_SIGMA_MIN && t == 1) {
-        L_min = loss_value(p.mode, LOSS, s, q);
-        t_min = 0;
-        minb = cur;
-      }
-      status = PA_WARN_SINGULAR;
-      break;
-    }
-    if (t == p.iters + 1) break;
+    __syncthreads();
+    if (sh.brk) break;
+    const double q_keep = (tid == 0) ? sh.scratch[0] : 0.0;
 
     // ---- phase B: z = A^T y, gradient, Adam, partial x.dx and dx.dx
+    if (tid == 0) sh.tmark = globaltimer_ns();
     {
-      double ca, cb;  // g = ca * x + cb * z
-      if (LOSS == PA_LOSS_QUADRATIC) { ca = 0.0; cb = -2.0; }
-      else { ca = 1.0 / q; cb = -1.0 / s; }
-      if (p.mode == PA_SIGMA_MIN) { ca = -ca; cb = -cb; }
-      const double2 bc = p.bias[t - 1];  // {lr/(1-b1^t), 1/(1-b2^t)}
-      const double b1 = p.beta1, b2 = p.beta2, omb1 = 1.0 - b1, omb2 = 1.0 - b2, eps = p.eps;
+      const double ca = sh.ca, cb = sh.cb;
+      // lr m_hat / (sqrt(v_hat) + eps) = K1 m / (sqrt(v) + K2) with
+      // K1 = lr sqrt(1-b2^t) / (1-b1^t) and K2 = eps sqrt(1-b2^t)
+      const double2 bc = p.bias[t - 1];
+      const double b1 = p.beta1, b2 = p.beta2;
+      // (1 - beta2) g^2 = w2 g'^2 with g' = (1 - beta1) g
+      const double w2 = (1.0 - b2) / ((1.0 - b1) * (1.0 - b1));
       double v[2] = {0.0, 0.0};
-      for (int j = c0 + tid; j < c1; j += kBlock) {
-        const double z = row_dot(p.cit, p.vat, __ldg(p.rpt + j), __ldg(p.rpt + j + 1), p.y);
-        const double xj = x[j];
-        const double g = (LOSS == PA_LOSS_QUADRATIC) ? cb * z : fma(ca, xj, cb * z);
-        const double mj = fma(b1, p.m[j], omb1 * g);
-        const double vj = fma(b2, p.v[j], omb2 * (g * g));
-        p.m[j] = mj;
-        p.v[j] = vj;
-        const double d = (bc.x * mj) / (sqrt(bc.y * vj) + eps);
-        p.dx[j] = d;
-        v[0] = fma(xj, d, v[0]);
-        v[1] = fma(d, d, v[1]);
+      for (int s = st0 + warp; s < st1; s += NW) {
+        const double z = slice_dot(p.t_wp, p.t_col, p.t_val, s, lane, p.y);
+        const int j = 32 * s + lane;
+        if (j < n) {
+          const double xj = x[j];
+          const double g = (LOSS == PA_LOSS_QUADRATIC) ? cb * z : fma(ca, xj, cb * z);
+          const double mj = fma(b1, p.m[j], g);
+          const double vj = fma(b2, p.v[j], w2 * (g * g));
+          p.m[j] = mj;
+          p.v[j] = vj;
+          const double d = (bc.x * mj) / (sqrt(vj) + bc.y);
+          p.dx[j] = d;
+          v[0] = fma(xj, d, v[0]);
+          v[1] = fma(d, d, v[1]);
+        }
       }
-      block_sum<2>(v, sh.scratch);
+      block_sum_to0<2>(v, sh.scratch);
       if (tid == 0) {
         part[b * kPartSlots + 2] = v[0];
         part[b * kPartSlots + 3] = v[1];
+        sh.busy_b += (unsigned long long)(globaltimer_ns() - sh.tmark);
       }
     }
     if (!grid_barrier(st, target, G, p.timeout_ns, false, site++, sh)) { status = PA_ERR_TIMEOUT; break; }
-    double p1, p2;
-    {
-      if (tid < 32) {
-        const double a_ = ordered_sum(part, G, kPartSlots, 2);
-        const double b_ = ordered_sum(part, G, kPartSlots, 3);
-        if (tid == 0) { sh.scratch[0] = a_; sh.scratch[1] = b_; }
+    if (tid < 32) {
+      const double p1 = ordered_sum(part, G, kPartSlots, 2);
+      const double p2 = ordered_sum(part, G, kPartSlots, 3);
+      if (tid == 0) {
+        int brk = 0;
+        if (!isfinite(p1) || !isfinite(p2)) {
+          sh.status = PA_ERR_NONFINITE;
+          brk = 1;
+        }
+        const double c = (p.ablation & PA_ABLATE_NO_TANGENT) ? 0.0 : p1;
+        double inv = 1.0;
+        if (!(p.ablation & PA_ABLATE_NO_NORMALISE)) {
+          const double a1c = 1.0 + c;
+          // ||(1+c) x - dx||^2 = (1+c)^2 q - 2 (1+c) p1 + p2
+          const double nrm2 = fma(a1c * a1c, q_keep, fma(-2.0 * a1c, p1, p2));
+          inv = 1.0 / sqrt(nrm2);
+        }
+        sh.c = c;
+        sh.inv = inv;
+        const int cur = sh.cur, minb = sh.minb;
+        sh.nb = (cur != 0 && minb != 0) ? 0 : ((cur != 1 && minb != 1) ? 1 : 2);
+        sh.brk = brk;
       }
-      __syncthreads();
-      p1 = sh.scratch[0];
-      p2 = sh.scratch[1];
-      __syncthreads();
     }
-    if (!isfinite(p1) || !isfinite(p2)) { status = PA_ERR_NONFINITE; break; }
+    __syncthreads();
+    if (sh.brk) break;
 
     // ---- phase C: project, update, normalise; partial ||x_t||^2
+    if (tid == 0) sh.tmark = globaltimer_ns();
     {
-      const double c = (p.ablation & PA_ABLATE_NO_TANGENT) ? 0.0 : p1;
-      double inv = 1.0;
-      if (!(p.ablation & PA_ABLATE_NO_NORMALISE)) {
-        const double a1c = 1.0 + c;
-        // ||(1+c) x - dx||^2 = (1+c)^2 q - 2 (1+c) p1 + p2
-        const double nrm2 = fma(a1c * a1c, q, fma(-2.0 * a1c, p1, p2));
-        inv = 1.0 / sqrt(nrm2);
-      }
-      const int nb = (cur != 0 && minb != 0) ? 0 : ((cur != 1 && minb != 1) ? 1 : 2);
+      const double a1c = 1.0 + sh.c, inv = sh.inv;
+      const int nb = sh.nb;
       double* xo = pick(p, nb);
       double* tr = (p.x_trace && t <= p.n_trace) ? p.x_trace + (size_t)(t - 1) * n : nullptr;
-      double v[1] = {0.0};
-      for (int j = c0 + tid; j < c1; j += kBlock) {
+      qloc = 0.0;
+      for (int j = r0 + tid; j < r1; j += kBlock) {
         const double xj = x[j];
-        const double xn = (xj - (p.dx[j] - c * xj)) * inv;
+        const double xn = fma(a1c, xj, -p.dx[j]) * inv;  // (x - (dx - c x)) / ||.||
         xo[j] = xn;
         if (tr) tr[j] = xn;
-        v[0] = fma(xn, xn, v[0]);
+        qloc = fma(xn, xn, qloc);
       }
-      block_sum<1>(v, sh.scratch);
-      if (tid == 0) part[b * kPartSlots + 1] = v[0];
-      cur = nb;
-      iters_run = t;
+      __syncthreads();  // every x_t row of this CTA is written
+      if (tid == 0) {
+        publish_ready(p.ready + b, (unsigned)t);
+        sh.cur = nb;
+        sh.iters_run = t;
+        sh.busy_b += (unsigned long long)(globaltimer_ns() - sh.tmark);
+      }
+      __syncthreads();
     }
-    if (!grid_barrier(st, target, G, p.timeout_ns, false, site++, sh)) { status = PA_ERR_TIMEOUT; break; }
   }
 
+  if (tid == 0 && p.cta_ns) {
+    p.cta_ns[2 * b] = sh.busy_a;
+    p.cta_ns[2 * b + 1] = sh.busy_b;
+  }
   if (b == 0 && tid == 0) {
-    if (status != PA_ERR_TIMEOUT && ld_relaxed_u32(&st->abort) != 0u) status = PA_ERR_TIMEOUT;
-    st->status = status;
-    st->minb = minb;
-    st->cur = cur;
-    st->t_min = t_min;
-    st->L_min = L_min;
-    st->L_last = L_last;
-    st->iters_run = iters_run;
+    if (status == PA_ERR_TIMEOUT || ld_relaxed_u32(&st->abort) != 0u) sh.status = PA_ERR_TIMEOUT;
+    st->status = sh.status;
+    st->minb = sh.minb;
+    st->cur = sh.cur;
+    st->t_min = sh.t_min;
+    st->L_min = sh.L_min;
+    st->L_last = sh.L_last;
+    st->iters_run = sh.iters_run;
   }
 }
 

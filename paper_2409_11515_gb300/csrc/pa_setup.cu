@@ -200,35 +200,187 @@ __global__ void k_gather_t(int64_t nnz, const int32_t* __restrict__ src,
 }
 
 // ------------------------------------------------------------ partition --
-// part[b] = first row r with rp[r] + w*r >= b * (nnz + w*n) / G (b = 0..G).
-__global__ void k_partition(const int32_t* __restrict__ rp, int32_t n, int G, int w,
+// part[b] = first slice s with cost(s) >= b * cost(n_slices) / G, where
+// cost(s) = 32 * wp[s] + w * 32 * s (padded entries plus a per-row weight).
+__global__ void k_partition(const int32_t* __restrict__ wp, int32_t ns, int G, int w,
                             int32_t* part) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b > G) return;
-  const double total = (double)rp[n] + (double)w * n;
+  const double total = 32.0 * wp[ns] + 32.0 * w * ns;
   const double target = total * b / G;
-  int lo = 0, hi = n;  // smallest r in [0, n] with cost(r) >= target
+  int lo = 0, hi = ns;
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    const double c = (double)rp[mid] + (double)w * mid;
+    const double c = 32.0 * wp[mid] + 32.0 * w * mid;
     if (c >= target) hi = mid; else lo = mid + 1;
   }
-  part[b] = (b == G) ? n : lo;
+  part[b] = (b == G) ? ns : lo;
+}
+
+// One block per CTA b of the persistent grid: smallest and largest x
+// position read by a non-zero of b's slices, mapped to the owning CTAs
+// (CTA j owns positions [32 part_t[j], 32 part_t[j+1])).
+__global__ void __launch_bounds__(kT) k_dependencies(const int32_t* __restrict__ wp,
+                                                     const int32_t* __restrict__ col,
+                                                     const double* __restrict__ val,
+                                                     const int32_t* __restrict__ part_a,
+                                                     const int32_t* __restrict__ part_t, int G,
+                                                     int32_t* dep) {
+  __shared__ int32_t smin[kT], smax[kT];
+  const int b = blockIdx.x;
+  const int64_t e0 = 32ll * wp[part_a[b]], e1 = 32ll * wp[part_a[b + 1]];
+  int32_t lo = 0x7fffffff, hi = -1;
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    if (val[e] != 0.0) {
+      const int32_t c = col[e];
+      lo = c < lo ? c : lo;
+      hi = c > hi ? c : hi;
+    }
+  }
+  smin[threadIdx.x] = lo;
+  smax[threadIdx.x] = hi;
+  __syncthreads();
+  for (int d = blockDim.x / 2; d > 0; d >>= 1) {
+    if (threadIdx.x < d) {
+      smin[threadIdx.x] = min(smin[threadIdx.x], smin[threadIdx.x + d]);
+      smax[threadIdx.x] = max(smax[threadIdx.x], smax[threadIdx.x + d]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (smax[0] < 0) {  // no non-zero: depends on nobody
+      dep[2 * b] = 1;
+      dep[2 * b + 1] = 0;
+      return;
+    }
+    // owner(p) = largest j with 32 part_t[j] <= p
+    auto owner = [&](int32_t p) {
+      int l = 0, h = G - 1;
+      while (l < h) {
+        const int m = (l + h + 1) >> 1;
+        if (32 * part_t[m] <= p) l = m; else h = m - 1;
+      }
+      return l;
+    };
+    dep[2 * b] = owner(smin[0]);
+    dep[2 * b + 1] = owner(smax[0]);
+  }
+}
+
+// ------------------------------------------------------ sliced ELL build --
+__global__ void k_row_lengths(int32_t n, const int32_t* __restrict__ rp, int32_t* lens) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride)
+    lens[r] = rp[r + 1] - rp[r];
+}
+
+// One block per window of kWindow rows: bitonic sort of the keys
+// (INT32_MAX - len) << 32 | local index, i.e. length descending and, among
+// equal lengths, source order (a stable sort).  perm[p] = source row at
+// position p; pos[row] = p.
+__global__ void __launch_bounds__(kWindow / 2) k_window_sort(int32_t n,
+                                                             const int32_t* __restrict__ lens,
+                                                             int32_t* perm, int32_t* pos) {
+  __shared__ unsigned long long key[kWindow];
+  const int64_t base = (int64_t)blockIdx.x * kWindow;
+  for (int i = threadIdx.x; i < kWindow; i += blockDim.x) {
+    const int64_t r = base + i;
+    const unsigned long long len = r < n ? (unsigned long long)lens[r] : 0ull;
+    key[i] = r < n ? (((0x7fffffffull - len) << 32) | (unsigned long long)i) : ~0ull;
+  }
+  __syncthreads();
+  for (int k = 2; k <= kWindow; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < kWindow; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const bool up = (i & k) == 0;
+          const unsigned long long a = key[i], b = key[ixj];
+          if ((a > b) == up) { key[i] = b; key[ixj] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < kWindow; i += blockDim.x) {
+    const unsigned long long k = key[i];
+    if (k != ~0ull) {
+      const int32_t src = (int32_t)(base + (int64_t)(k & 0xffffffffull));
+      perm[base + i] = src;
+      pos[src] = (int32_t)(base + i);
+    }
+  }
+}
+
+// Width of each slice = length of its first (longest) row; widths[ns] = 0.
+__global__ void k_slice_widths(int32_t n, int32_t ns, const int32_t* __restrict__ perm,
+                               const int32_t* __restrict__ lens, int32_t* widths) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s <= ns; s += stride)
+    widths[s] = (s < ns) ? lens[perm[32 * s]] : 0;
+}
+
+// One thread per (slice, lane): copy the row's entries column-major into the
+// slice and pad with (column 0, value 0.0) up to the slice width.
+__global__ void k_sell_fill(int32_t n, int32_t ns, const int32_t* __restrict__ rp,
+                            const int32_t* __restrict__ ci, const double* __restrict__ va,
+                            const int32_t* __restrict__ perm, const int32_t* __restrict__ col_pos,
+                            const int32_t* __restrict__ wp, int32_t* col, double* val) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 32ll * ns; t += stride) {
+    const int64_t s = t >> 5;
+    const int lane = (int)(t & 31);
+    const int64_t p = 32 * s + lane;
+    const int w0 = wp[s], w = wp[s + 1] - w0;
+    const int64_t out = 32ll * w0 + lane;
+    int k = 0;
+    if (p < n) {
+      const int32_t r = perm[p];
+      const int32_t k0 = rp[r], len = rp[r + 1] - k0;
+      for (; k < len; ++k) {
+        col[out + 32ll * k] = col_pos[ci[k0 + k]];
+        val[out + 32ll * k] = va[k0 + k];
+      }
+    }
+    for (; k < w; ++k) {
+      col[out + 32ll * k] = 0;
+      val[out + 32ll * k] = 0.0;
+    }
+  }
+}
+
+__global__ void k_permute(int32_t n, const int32_t* __restrict__ pos, const double* __restrict__ in,
+                          double* out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    out[pos[i]] = in[i];
+}
+
+// `count` vectors of length n (row-major), each mapped back to source order.
+__global__ void k_unpermute(int32_t n, int32_t count, const int32_t* __restrict__ pos,
+                            const double* __restrict__ in, double* out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t total = (int64_t)n * count;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+    const int64_t v = t / n, i = t - v * n;
+    out[t] = in[v * n + pos[i]];
+  }
 }
 
 // --------------------------------------------------------- start vector --
-__global__ void __launch_bounds__(kT) k_start_raw(int32_t n, uint64_t seed, double* x,
+__global__ void __launch_bounds__(kT) k_start_raw(int32_t n, uint64_t seed,
+                                                  const int32_t* __restrict__ pos, double* x,
                                                   double* blockpart) {
-  __shared__ double scratch[kT / 32];
+  __shared__ double scratch[kT];
   double q[1] = {0.0};
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double u = (double)(splitmix64_at(seed, (uint64_t)i) >> 11) * 0x1.0p-53;
     const double xi = 2.0 * u - 1.0;
-    x[i] = xi;
+    x[pos[i]] = xi;
     q[0] = fma(xi, xi, q[0]);
   }
-  block_sum<1>(q, scratch);
+  block_sum_to0<1>(q, scratch);
   if (threadIdx.x == 0) blockpart[blockIdx.x] = q[0];
 }
 
@@ -245,14 +397,20 @@ __global__ void __launch_bounds__(kT) k_start_scale(int32_t n, double* x,
     x[i] *= inv;
 }
 
-// ----------------------------------------------------------------- SpMV --
-__global__ void __launch_bounds__(kT) k_spmv(int32_t n_rows, const int32_t* __restrict__ rp,
-                                             const int32_t* __restrict__ ci,
-                                             const double* __restrict__ va,
-                                             const double* __restrict__ x, double* y) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_rows; r += stride)
-    y[r] = row_dot(ci, va, __ldg(rp + r), __ldg(rp + r + 1), x);
+// ------------------------------------------------------- sliced product --
+__global__ void __launch_bounds__(kT) k_sell_spmv(int32_t n, int32_t ns,
+                                                  const int32_t* __restrict__ wp,
+                                                  const int32_t* __restrict__ col,
+                                                  const double* __restrict__ val,
+                                                  const double* __restrict__ x, double* y) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < ns;
+       s += warps) {
+    const double a = slice_dot(wp, col, val, (int)s, lane, x);
+    const int64_t p = 32 * s + lane;
+    if (p < n) y[p] = a;
+  }
 }
 
 // ---------------------------------------------------------------- sigma --
@@ -261,24 +419,27 @@ __device__ __forceinline__ const double* select_x(const double* X0, const double
   return k == 0 ? X0 : (k == 1 ? X1 : X2);
 }
 
-__global__ void __launch_bounds__(kT) k_sigma_part(int32_t n_rows, int32_t n_cols,
-                                                   const int32_t* __restrict__ rp,
-                                                   const int32_t* __restrict__ ci,
-                                                   const double* __restrict__ va,
+__global__ void __launch_bounds__(kT) k_sigma_part(int32_t n_rows, int32_t ns, int32_t n_cols,
+                                                   const int32_t* __restrict__ wp,
+                                                   const int32_t* __restrict__ col,
+                                                   const double* __restrict__ val,
                                                    const double* X0, const double* X1,
                                                    const double* X2, int use_minb,
                                                    const RunState* st, double* blockpart) {
-  __shared__ double scratch[2 * kT / 32];
+  __shared__ double scratch[2 * kT];
   const double* x = select_x(X0, X1, X2, use_minb ? st->minb : 0);
   double v[2] = {0.0, 0.0};
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_rows; r += stride) {
-    const double yr = row_dot(ci, va, __ldg(rp + r), __ldg(rp + r + 1), x);
-    v[0] = fma(yr, yr, v[0]);
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < ns;
+       s += warps) {
+    const double a = slice_dot(wp, col, val, (int)s, lane, x);
+    if (32 * s + lane < n_rows) v[0] = fma(a, a, v[0]);
   }
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_cols; j += stride)
     v[1] = fma(x[j], x[j], v[1]);
-  block_sum<2>(v, scratch);
+  block_sum_to0<2>(v, scratch);
   if (threadIdx.x == 0) {
     blockpart[2 * blockIdx.x] = v[0];
     blockpart[2 * blockIdx.x + 1] = v[1];
@@ -336,42 +497,116 @@ cudaError_t launch_transpose(int32_t n_rows, int32_t n_cols, int64_t nnz, const 
   return cudaGetLastError();
 }
 
-cudaError_t launch_partition(const int32_t* rp, int32_t n, int G, int row_weight, int32_t* part,
-                             cudaStream_t s, int64_t* launches) {
-  k_partition<<<cdiv(G + 1, kT), kT, 0, s>>>(rp, n, G, row_weight, part);
+cudaError_t launch_partition(const int32_t* wp, int32_t n_slices, int G, int row_weight,
+                             int32_t* part, cudaStream_t s, int64_t* launches) {
+  k_partition<<<cdiv(G + 1, kT), kT, 0, s>>>(wp, n_slices, G, row_weight, part);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+int32_t sell_slices(int32_t n_rows) { return (n_rows + 31) / 32; }
+
+cudaError_t launch_dependencies(const int32_t* wp, const int32_t* col, const double* val,
+                                const int32_t* part_a, const int32_t* part_t, int G,
+                                int32_t* dep, cudaStream_t s, int64_t* launches) {
+  k_dependencies<<<G, kT, 0, s>>>(wp, col, val, part_a, part_t, G, dep);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_lengths(int32_t n_rows, const int32_t* rp, int32_t* lens, cudaStream_t s,
+                               int64_t* launches) {
+  k_row_lengths<<<grid_for(n_rows), kT, 0, s>>>(n_rows, rp, lens);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_window_sort(int32_t n, const int32_t* lens, int32_t* perm, int32_t* pos,
+                               cudaStream_t s, int64_t* launches) {
+  k_window_sort<<<cdiv(n, kWindow), kWindow / 2, 0, s>>>(n, lens, perm, pos);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sell_build(int32_t n_rows, const int32_t* /*rp*/, const int32_t* /*ci*/,
+                              const double* /*va*/, const int32_t* lens,
+                              const int32_t* /*col_pos*/, Sell* out, int32_t* widths,
+                              int32_t* blocksums, int64_t* total, cudaStream_t s,
+                              int64_t* launches) {
+  const int32_t ns = sell_slices(n_rows);
+  out->n_rows = n_rows;
+  out->n_slices = ns;
+  k_slice_widths<<<grid_for((int64_t)ns + 1), kT, 0, s>>>(n_rows, ns, out->perm, lens, widths);
+  // exclusive scan of the ns widths: wp[0..ns-1], and wp[ns] = total
+  const int nb = scan_blocks((int64_t)ns);
+  k_scan_sums<<<nb, 1024, 0, s>>>((int64_t)ns, widths, blocksums);
+  k_scan_top<<<1, 1024, 0, s>>>(nb, blocksums);
+  k_scan_apply<<<nb, 1024, 0, s>>>((int64_t)ns, widths, blocksums, out->wp);
+  *launches += 4;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int32_t tot = 0;
+  e = cudaMemcpyAsync(&tot, out->wp + ns, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  *total = 32ll * tot;
+  return e;
+}
+
+cudaError_t launch_sell_fill(int32_t n_rows, const int32_t* rp, const int32_t* ci,
+                             const double* va, const int32_t* /*lens*/, const int32_t* col_pos,
+                             const Sell& out, cudaStream_t s, int64_t* launches) {
+  k_sell_fill<<<grid_for(32ll * out.n_slices), kT, 0, s>>>(n_rows, out.n_slices, rp, ci, va,
+                                                            out.perm, col_pos, out.wp, out.col,
+                                                            out.val);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute(int32_t n, const int32_t* pos, const double* in, double* out,
+                           cudaStream_t s, int64_t* launches) {
+  k_permute<<<grid_for(n), kT, 0, s>>>(n, pos, in, out);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpermute(int32_t n, int32_t count, const int32_t* pos, const double* in,
+                             double* out, cudaStream_t s, int64_t* launches) {
+  k_unpermute<<<grid_for((int64_t)n * count), kT, 0, s>>>(n, count, pos, in, out);
   ++*launches;
   return cudaGetLastError();
 }
 
 int start_vector_blocks(int32_t n) { return grid_for(n, kT, 152 * 4); }
 
-cudaError_t launch_start_vector(int32_t n, uint64_t seed, double* x, double* blockpart,
-                                cudaStream_t s, int64_t* launches) {
+cudaError_t launch_start_vector(int32_t n, uint64_t seed, const int32_t* pos, double* x,
+                                double* blockpart, cudaStream_t s, int64_t* launches) {
   const int nb = start_vector_blocks(n);
-  k_start_raw<<<nb, kT, 0, s>>>(n, seed, x, blockpart);
+  k_start_raw<<<nb, kT, 0, s>>>(n, seed, pos, x, blockpart);
   k_start_scale<<<nb, kT, 0, s>>>(n, x, blockpart, nb);
   *launches += 2;
   return cudaGetLastError();
 }
 
-cudaError_t launch_spmv(int32_t n_rows, const int32_t* rp, const int32_t* ci, const double* va,
-                        const double* x, double* y, cudaStream_t s, int64_t* launches) {
-  if (n_rows == 0) return cudaSuccess;
-  k_spmv<<<grid_for(n_rows), kT, 0, s>>>(n_rows, rp, ci, va, x, y);
+cudaError_t launch_sell_spmv(const Sell& m, const double* x, double* y, cudaStream_t s,
+                             int64_t* launches) {
+  if (m.n_rows == 0) return cudaSuccess;
+  k_sell_spmv<<<grid_for(32ll * m.n_slices), kT, 0, s>>>(m.n_rows, m.n_slices, m.wp, m.col,
+                                                          m.val, x, y);
   ++*launches;
   return cudaGetLastError();
 }
 
-int sigma_blocks(int32_t n_rows, int32_t n_cols) {
-  return grid_for(n_rows > n_cols ? n_rows : n_cols, kT, 152 * 4);
+int sigma_blocks(int32_t n_slices, int32_t n_cols) {
+  const int64_t a = 32ll * n_slices, b = n_cols;
+  return grid_for(a > b ? a : b, kT, 152 * 4);
 }
 
-cudaError_t launch_sigma(int32_t n_rows, int32_t n_cols, const int32_t* rp, const int32_t* ci,
-                         const double* va, const double* X0, const double* X1, const double* X2,
-                         int use_minb, RunState* st, double* blockpart, cudaStream_t s,
-                         int64_t* launches) {
-  const int nb = sigma_blocks(n_rows, n_cols);
-  k_sigma_part<<<nb, kT, 0, s>>>(n_rows, n_cols, rp, ci, va, X0, X1, X2, use_minb, st, blockpart);
+cudaError_t launch_sigma(const Sell& m, int32_t n_cols, const double* X0, const double* X1,
+                         const double* X2, int use_minb, RunState* st, double* blockpart,
+                         cudaStream_t s, int64_t* launches) {
+  const int nb = sigma_blocks(m.n_slices, n_cols);
+  k_sigma_part<<<nb, kT, 0, s>>>(m.n_rows, m.n_slices, n_cols, m.wp, m.col, m.val, X0, X1, X2,
+                                 use_minb, st, blockpart);
   k_sigma_final<<<1, 32, 0, s>>>(blockpart, nb, st);
   *launches += 2;
   return cudaGetLastError();

@@ -37,7 +37,8 @@ STATUS_NAMES = {0: "PA_OK", 1: "PA_WARN_SINGULAR", -1: "PA_ERR_INVALID_ARG",
 
 EXPORTS = ("pa_options_default", "pa_create", "pa_estimate", "pa_run", "pa_estimate_batched",
            "pa_get_vector", "pa_spmv", "pa_spmv_t", "pa_get_transpose", "pa_get_equilibration",
-           "pa_kernel_launches", "pa_destroy", "pa_last_error", "pa_set_allocator")
+           "pa_kernel_launches", "pa_destroy", "pa_last_error", "pa_set_allocator",
+           "pa_last_run_profile")
 
 
 class LibraryMissing(RuntimeError):
@@ -104,6 +105,8 @@ def _declare(L):
     L.pa_get_transpose.argtypes = [vp, vp, vp, vp]
     L.pa_get_equilibration.restype = C.c_int
     L.pa_get_equilibration.argtypes = [vp, vp, vp]
+    L.pa_last_run_profile.restype = C.c_int
+    L.pa_last_run_profile.argtypes = [vp, C.POINTER(C.c_int), vp]
     L.pa_kernel_launches.restype = i64
     L.pa_kernel_launches.argtypes = [vp]
     L.pa_destroy.restype = None
@@ -272,6 +275,14 @@ class Handle:
         vat = np.empty(max(self.nnz, 1))
         _check(load().pa_get_transpose(self._h, rpt.ctypes.data, cit.ctypes.data, vat.ctypes.data))
         return rpt, cit[:self.nnz], vat[:self.nnz]
+
+    def last_run_profile(self):
+        """(grid, busy_ns[grid, 2]) of the latest persistent run (phase A, phases B+C)."""
+        g = C.c_int()
+        _check(load().pa_last_run_profile(self._h, C.byref(g), None))
+        t = np.zeros((max(g.value, 1), 2))
+        _check(load().pa_last_run_profile(self._h, C.byref(g), t.ctypes.data))
+        return g.value, t[:g.value]
 
     def get_equilibration(self):
         dr, dc = np.empty(self.n_rows), np.empty(self.n_cols)
