@@ -173,6 +173,29 @@ pa_status pa_last_run_profile(pa_handle h, int* grid, double* busy_ns);
  * counter kept by the host code at every launch). */
 int64_t pa_kernel_launches(pa_handle h);
 
+/* sigma = ||A x||_2 / ||x||_2 for a CSR matrix and a vector already in
+ * device memory, with no device memory allocated by the call.  (The paper has
+ * no counterpart: this exists for callers that cannot allocate at this point,
+ * e.g. because their device memory is fully held by another allocator or
+ * because cudaMalloc's implicit device-wide synchronisation is not
+ * acceptable there.)
+ *   row_ptr (n_rows+1 int32), col_idx and vals (nnz int32 / float64), x
+ *   (n_cols float64): device pointers, read only; the CSR is not validated.
+ *   sigma: device pointer to one float64, written by the call's kernels.
+ *   cuda_stream: cudaStream_t (NULL = legacy default stream); the call only
+ *   enqueues work and returns without synchronising.
+ * Scratch: a fixed 128 KiB array of device memory inside the library (held
+ * on every GPU that loads it until the process exits) limits
+ * max(n_rows, n_cols) to 2,097,152; larger sizes give PA_ERR_INVALID_ARG.
+ * The first call on a device looks up that array's address (once per
+ * device); make that first call before any stream capture.  All calls share
+ * the array: calls whose kernels may overlap on the GPU race and must be
+ * ordered by the caller (same stream or events).  Errors: PA_ERR_INVALID_ARG,
+ * PA_ERR_CUDA, PA_ERR_UNSUPPORTED (device index 64 or above). */
+pa_status pa_sigma_noalloc(int32_t n_rows, int32_t n_cols, const int32_t* row_ptr,
+                           const int32_t* col_idx, const double* vals, const double* x,
+                           double* sigma, void* cuda_stream);
+
 /* Release the handle and its device memory (NULL-safe). */
 void pa_destroy(pa_handle h);
 

@@ -43,6 +43,16 @@ static pa_status cuda_fail(cudaError_t e, const char* what) {
 
 extern "C" const char* pa_last_error(void) { return g_err.c_str(); }
 
+pa_status pa::set_error(pa_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
 // --------------------------------------------------------- allocator --
 
 static pa_alloc_fn g_alloc = nullptr;

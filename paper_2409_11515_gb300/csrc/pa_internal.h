@@ -73,6 +73,9 @@ struct IterParams {
   int skip_arrival;
 };
 
+// Record a message for pa_last_error() (printf-style) and return st.
+pa_status set_error(pa_status st, const char* fmt, ...);
+
 // ---- launch wrappers implemented in the kernel translation units --------
 // Each returns the CUDA error of its launch(es) and adds its launch count to
 // *launches.

@@ -38,7 +38,7 @@ STATUS_NAMES = {0: "PA_OK", 1: "PA_WARN_SINGULAR", -1: "PA_ERR_INVALID_ARG",
 EXPORTS = ("pa_options_default", "pa_create", "pa_estimate", "pa_run", "pa_estimate_batched",
            "pa_get_vector", "pa_spmv", "pa_spmv_t", "pa_get_transpose", "pa_get_equilibration",
            "pa_kernel_launches", "pa_destroy", "pa_last_error", "pa_set_allocator",
-           "pa_last_run_profile")
+           "pa_last_run_profile", "pa_sigma_noalloc")
 
 
 class LibraryMissing(RuntimeError):
@@ -107,6 +107,8 @@ def _declare(L):
     L.pa_get_equilibration.argtypes = [vp, vp, vp]
     L.pa_last_run_profile.restype = C.c_int
     L.pa_last_run_profile.argtypes = [vp, C.POINTER(C.c_int), vp]
+    L.pa_sigma_noalloc.restype = C.c_int
+    L.pa_sigma_noalloc.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp]
     L.pa_kernel_launches.restype = i64
     L.pa_kernel_launches.argtypes = [vp]
     L.pa_destroy.restype = None
@@ -323,3 +325,12 @@ def estimate_batched(handles, mode=BOTH, k_restarts=8, iters=(2000, 2000), lr=1e
                                            seed & (2**64 - 1), out.ctypes.data, stat.ctypes.data))
     return {"status": st, "sigma_max": out[:, :, 0], "sigma_min": out[:, :, 1],
             "kappa": out[:, :, 2], "item_status": stat}
+
+
+def sigma_noalloc(row_ptr, col, val, x, out, n_rows: int, n_cols: int, stream=None) -> int:
+    """pa_sigma_noalloc: ||A x|| / ||x|| into out[0]; every argument is a CUDA
+    torch tensor (row_ptr/col int32, val/x/out float64).  Enqueues only; the
+    caller synchronises.  Returns the status (raises PAError on errors)."""
+    return _check(load().pa_sigma_noalloc(int(n_rows), int(n_cols), row_ptr.data_ptr(),
+                                          col.data_ptr(), val.data_ptr(), x.data_ptr(),
+                                          out.data_ptr(), _stream_ptr(stream)))
