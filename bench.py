@@ -123,6 +123,38 @@ def _max_over_ranks(x, ws):
     return float(t.item())
 
 
+def flops_per_iteration(n_rows, n_cols, nnz):
+    """Algorithmic FP64 flops of one iteration: 2 per entry for each of the
+    two products, plus the per-row arithmetic of Algorithm 1 as written
+    (gradient 3, moments 7, bias corrections 2, step 4 counting the square
+    root and the division as one each, projection 4, update 1, norm 3,
+    ||y||^2 and ||x||^2 partials 2 each): 26 per row."""
+    return 4 * nnz + 26 * n_cols
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("pa_iter.cu", "pa_device.cuh", "pa_internal.h"):
+        h.update((ROOT / "paper_2409_11515_gb300" / "csrc" / f).read_bytes())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic_per_iteration():
+    """DRAM bytes per iteration of k_persistent from the committed ncu summary,
+    or None when the kernel source changed since that capture."""
+    prof = ROOT / "profiles" / "k_persistent_hydro401.md"
+    if not prof.exists():
+        return None
+    src = dram = None
+    for line in prof.read_text().splitlines():
+        if line.startswith("kernel source sha256[:16]:"):
+            src = line.split(":", 1)[1].strip()
+        if line.startswith("dram bytes per iteration:"):
+            dram = float(line.split(":", 1)[1].strip())
+    return dram if (src == kernel_source_hash() and dram) else None
+
+
 def bytes_per_iteration(n_rows, n_cols, nnz):
     """Algorithmic bytes of one FP64 iteration: A and A^T read once
     (12 B per entry + 4 B per row pointer) and nine 8-byte vector streams
@@ -241,10 +273,17 @@ def run_ours(args):
         torch.cuda.synchronize()
         kms.append((iters, e0.elapsed_time(e1)))
     B = bytes_per_iteration(A.n_rows, A.n_cols, A.nnz)
+    F = flops_per_iteration(A.n_rows, A.n_cols, A.nnz)
     tot_it = sum(i for i, _ in kms)
     tot_ms = sum(t for _, t in kms)
     achieved = B * tot_it / (tot_ms / 1e3) / 1e9
+    achieved_f = F * tot_it / (tot_ms / 1e3) / 1e12
     peak, peak_kind = _peaks()
+    clk = clocks.get("sm_mhz") or 2070.0
+    # FP64 pipe: 2 FMA lanes per SM per clock (ncu: dfma peak 2/cycle/SM), 152 SMs
+    fp64_peak = 2 * 2 * 152 * clk * 1e6 / 1e12
+    tpi = profiled_traffic_per_iteration()
+    launch_iters = tot_it / len(kms)
     h.destroy()
     # ---- end to end through the C ABI with host buffers
     e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 2))
@@ -260,13 +299,7 @@ def run_ours(args):
     h2d = A.row_ptr.nbytes + A.col.nbytes + A.val.nbytes + 16 * (ITERS_MAX + ITERS_MIN)
     d2h = 2 * 96 + 4
     if rank == 0:
-        prof = ROOT / "profiles" / "persistent_hydro401_traffic.json"
-        traffic = None
-        if prof.exists():
-            try:
-                traffic = json.loads(prof.read_text()).get("traffic_bytes_per_launch")
-            except ValueError:
-                traffic = None
+        traffic = tpi * launch_iters if tpi else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -276,11 +309,17 @@ def run_ours(args):
             "kappa_estimates_per_s": ws * args.steps / (ms / 1e3),
             "result": {"sigma_max": r["sigma_max"], "sigma_min": r["sigma_min"],
                        "kappa": r["kappa"], "status": r["status"]},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "peak_source": f"{peak_kind} copy bandwidth",
-                         "kernel": "k_persistent (per-launch CUDA events on its stream)",
-                         "bytes_per_iteration": B},
+            "roofline": {"bound": "alu", "achieved": achieved_f, "peak": fp64_peak,
+                         "unit": "TFLOP/s", "frac": achieved_f / fp64_peak, "traffic": traffic,
+                         "kernel": "k_persistent, FP64 (per-launch CUDA events on its stream)",
+                         "peak_source": "FP64 pipe: 2 FMA lanes/SM/clock x 152 SMs x 2 flops "
+                                        "x median SM clock under load",
+                         "flops_per_iteration": F, "iterations_per_launch": launch_iters,
+                         "traffic_source": "ncu dram bytes per iteration x iterations per launch "
+                                           "(profiles/k_persistent_hydro401.md)"},
+            "roofline_hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "bytes_per_iteration": B,
+                             "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json)"},
             "clocks": clocks,
             "gpu_launches": launches,
             "e2e": {"value": ws * it_per_step * e2e_steps / e2e_s, "unit": UNIT,
