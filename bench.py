@@ -264,14 +264,42 @@ def run_ours(args):
     value = ws * it_per_step * args.steps / (ms / 1e3)
     # ---- roofline of the persistent kernel: per-launch time on its own stream
     kms = []
+    r_fp64 = None
     for iters, mode in ((ITERS_MAX, pa.SIGMA_MAX), (ITERS_MIN, pa.SIGMA_MIN)):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        x0 = None
         e0.record(stream)
-        h.estimate(mode, iters, seed=START_SEED, **HYPER)
+        rr = h.estimate(mode, iters, seed=START_SEED, **HYPER)
         e1.record(stream)
         torch.cuda.synchronize()
         kms.append((iters, e0.elapsed_time(e1)))
+        r_fp64 = rr
+    # ---- mixed precision on the same workload (PA_MIXED): FP32 sigma_max with
+    # an FP64 tail, compensated sigma_min; errors against this run's FP64 sigmas
+    variants = None
+    if not args.no_variants:
+        with pa.create(A, stream=stream, precision=pa.MIXED) as hm:
+            hm.estimate(pa.SIGMA_MAX, 50, seed=START_SEED, **HYPER)  # warm-up
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rm = hm.estimate(pa.SIGMA_MAX, ITERS_MAX, seed=START_SEED, **HYPER)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_max = e0.elapsed_time(e1) / 1e3
+            it_dd = max(1, ITERS_MIN // 10)
+            e0.record(stream)
+            rd = hm.estimate(pa.SIGMA_MIN, it_dd, seed=START_SEED, **HYPER)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_dd = e0.elapsed_time(e1) / 1e3
+        variants = {
+            "mixed_sigma_max": {"iterations_per_s": ITERS_MAX / t_max, "iters": ITERS_MAX,
+                                "sigma_max": rm["sigma_max"],
+                                "rel_err_vs_fp64": abs(rm["sigma_max"] / r_fp64["sigma_max"] - 1),
+                                "precision": "FP32 products and Adam state on D_r^-1 A D_c^-1, "
+                                             "FP64 norms, last iters/10 in FP64"},
+            "compensated_sigma_min": {"iterations_per_s": it_dd / t_dd, "iters": it_dd,
+                                      "precision": "FP64 with double-double (Dot2) products"},
+        }
     B = bytes_per_iteration(A.n_rows, A.n_cols, A.nnz)
     F = flops_per_iteration(A.n_rows, A.n_cols, A.nnz)
     tot_it = sum(i for i, _ in kms)
@@ -320,6 +348,7 @@ def run_ours(args):
             "roofline_hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "bytes_per_iteration": B,
                              "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json)"},
+            "variants_same_workload": variants,
             "clocks": clocks,
             "gpu_launches": launches,
             "e2e": {"value": ws * it_per_step * e2e_steps / e2e_s, "unit": UNIT,
@@ -347,6 +376,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision leg")
     ap.add_argument("--iters-max", type=int, default=ITERS_MAX,
                     help="sigma_max iterations per estimate (short runs for profiling)")
     ap.add_argument("--iters-min", type=int, default=ITERS_MIN)

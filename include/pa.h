@@ -70,10 +70,13 @@ typedef struct {
    * (sigma_min) with gradient -/+ 2 A^T A v. */
   int loss;
   /* FP64 (default): every product, the Adam state and every reduction in
-   * FP64.  MIXED: sigma_max iterates with FP32 products on the
-   * power-of-two-equilibrated matrix; sigma_min uses compensated
-   * (double-double) products; the returned sigma is always ||A x_min|| in
-   * FP64 (compensated for sigma_min). */
+   * FP64.  MIXED (log-ratio loss only): sigma_max iterates with FP32
+   * products and FP32 Adam state on the power-of-two-equilibrated matrix
+   * D_r^-1 A D_c^-1 (norms reduced in FP64), then runs its last fp64_tail
+   * iterations in FP64 from that state; x_min is whichever tracked iterate
+   * of the two stages scores the larger ||A x|| / ||x|| in FP64.  sigma_min
+   * uses compensated (double-double, Dot2) products for A x and A^T y and
+   * for its final sigma. */
   int precision;
   int equilibrate;  /* PA_EQ_STORAGE: keep D_r^-1 A D_c^-1 with pow2 D (implied by MIXED) */
   int engine;       /* AUTO picks CLUSTER for small matrices, else GRID     */
@@ -84,10 +87,14 @@ typedef struct {
   int grid_blocks;  /* 0 = fill the GPU; > 0 caps the persistent grid      */
   int debug_skip_arrival; /* test hook: > 0 makes CTA 0 skip the barrier of
                              that iteration, so the others time out (0 = off) */
+  int fp64_tail;    /* MIXED sigma_max: the last iterations, run in FP64 from
+                       the FP32 state (x, m, v) near convergence; < 0 (default)
+                       = iters / 10, 0 = none */
 } pa_options;
 
 /* Fill *opt with the defaults above (LOGRATIO, FP64, no equilibration, AUTO
- * engine, no ablation, 2 s barrier limit, full grid, no debug hook). */
+ * engine, no ablation, 2 s barrier limit, full grid, no debug hook, FP64 tail
+ * of iters / 10 in MIXED mode). */
 void pa_options_default(pa_options* opt);
 
 /* Build a handle for the n_rows x n_cols matrix A given in CSR.

@@ -101,25 +101,25 @@ def compile_variant(source_text: str, out_path, contract_fma: bool = False) -> P
 
 
 def rounding_ensemble(A, mode: int, iters: int, x_init, workdir, loss: int = LOSS_LOGRATIO,
-                      n_perturbed: int = 2, n_entries: int = 3, **hyper):
+                      n_perturbed: int = 2, n_entries: int = 3, flags: int = 0, **hyper):
     """Runs of the same Algorithm 1 that differ from the oracle only in
     round-off: the FMA-contracted build of this source, and x_init with a few
     entries moved by one ulp.  Returns (reference run, [variant runs])."""
     x_init = np.ascontiguousarray(x_init, dtype=np.float64)
     ref = projected_adam(A, mode, iters, x_init=x_init, loss=loss, n_trace=iters, trace_L=True,
-                         **hyper)
+                         flags=flags, **hyper)
     runs = []
     fma = load(compile_variant(source_text(), Path(workdir) / "oracle_fma.so", contract_fma=True))
     with using(fma):
         runs.append(projected_adam(A, mode, iters, x_init=x_init, loss=loss, n_trace=iters,
-                                   trace_L=True, **hyper))
+                                   trace_L=True, flags=flags, **hyper))
     rng = np.random.default_rng(12345)
     for _ in range(n_perturbed):
         xp = x_init.copy()
         idx = rng.choice(xp.size, size=min(n_entries, xp.size), replace=False)
         xp[idx] = np.nextafter(xp[idx], np.inf)
         runs.append(projected_adam(A, mode, iters, x_init=xp, loss=loss, n_trace=iters,
-                                   trace_L=True, **hyper))
+                                   trace_L=True, flags=flags, **hyper))
     return ref, runs
 
 

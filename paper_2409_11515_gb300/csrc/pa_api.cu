@@ -103,6 +103,14 @@ struct pa_ctx {
   int bias_cap = 0;
   bool have_max = false, have_min = false;
   double sigma_max = NAN, sigma_min = NAN;
+
+  // power-of-two equilibration (source order, FP64) and the FP32 copies the
+  // mixed-precision sigma_max kernel iterates over
+  double *d_row = nullptr, *d_col = nullptr;
+  float *drp32 = nullptr, *dcp32 = nullptr, *a_val32 = nullptr, *t_val32 = nullptr;
+  float *X0f = nullptr, *X1f = nullptr, *X2f = nullptr, *Wf = nullptr;
+  float *mf = nullptr, *vf = nullptr, *yf = nullptr, *dxf = nullptr;
+  int64_t a_entries = 0, t_entries = 0;  // padded entries of the sliced copies
 };
 
 static void* dev_alloc(pa_ctx* h, size_t bytes) {
@@ -146,6 +154,7 @@ extern "C" void pa_options_default(pa_options* opt) {
   opt->equilibrate = PA_EQ_NONE;
   opt->engine = PA_ENGINE_AUTO;
   opt->barrier_timeout_ns = 2000000000LL;
+  opt->fp64_tail = -1;
 }
 
 extern "C" void pa_destroy(pa_handle h) {
@@ -182,6 +191,7 @@ static pa_status build_one_sell(pa_ctx* h, int32_t n_rows, const int32_t* rp, co
   if ((st = alloc_n(h, &out->col, (size_t)total + 32, "sliced columns")) ||
       (st = alloc_n(h, &out->val, (size_t)total + 32, "sliced values")))
     return st;
+  if (out == &h->sa) h->a_entries = total; else h->t_entries = total;
   e = launch_sell_fill(n_rows, rp, ci, va, lens, col_pos, *out, h->stream, &h->launches);
   if (e != cudaSuccess) return cuda_fail(e, "filling the sliced matrix");
   return PA_OK;
@@ -215,6 +225,43 @@ static pa_status build_sell(pa_ctx* h) {
   return PA_OK;
 }
 
+// Power-of-two equilibration D_r, D_c (source order), and for the mixed
+// precision mode the permuted FP32 factors and FP32 values of the sliced
+// copies of D_r^-1 A D_c^-1.
+static pa_status build_equilibration(pa_ctx* h, bool fp32_copies) {
+  pa_status st;
+  if ((st = alloc_n(h, &h->d_row, (size_t)h->n_rows, "row scaling")) ||
+      (st = alloc_n(h, &h->d_col, (size_t)h->n_cols, "column scaling")))
+    return st;
+  cudaError_t e = launch_equilibrate(h->n_rows, h->n_cols, h->rp, h->va, h->rpt, h->cit, h->vat,
+                                     h->d_row, h->d_col, h->stream, &h->launches);
+  if (e != cudaSuccess) return cuda_fail(e, "equilibrating");
+  if (!fp32_copies) return PA_OK;
+  int* flag = nullptr;
+  if ((st = alloc_n(h, &h->drp32, (size_t)h->n_rows, "row scaling (FP32)")) ||
+      (st = alloc_n(h, &h->dcp32, (size_t)h->n_cols, "column scaling (FP32)")) ||
+      (st = alloc_n(h, &h->a_val32, (size_t)h->a_entries + 32, "FP32 values")) ||
+      (st = alloc_n(h, &h->t_val32, (size_t)h->t_entries + 32, "FP32 values")) ||
+      (st = alloc_n(h, &flag, 1, "flag")))
+    return st;
+  int hflag = 0;
+  if ((e = cudaMemsetAsync(flag, 0, sizeof(int), h->stream)) ||
+      (e = launch_permute_factors(h->n_rows, h->sa.perm, h->d_row, h->drp32, flag, h->stream,
+                                  &h->launches)) ||
+      (e = launch_permute_factors(h->n_cols, h->sq.perm, h->d_col, h->dcp32, flag, h->stream,
+                                  &h->launches)) ||
+      (e = launch_sell_scale32(h->sa, h->drp32, h->dcp32, h->a_val32, h->stream, &h->launches)) ||
+      (e = launch_sell_scale32(h->sq, h->dcp32, h->drp32, h->t_val32, h->stream, &h->launches)) ||
+      (e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream)) ||
+      (e = cudaStreamSynchronize(h->stream)))
+    return cuda_fail(e, "building the FP32 equilibrated copies");
+  dev_free(h, flag);
+  if (hflag)
+    return fail(PA_ERR_UNSUPPORTED,
+                "mixed precision: an equilibration factor lies outside the FP32 normal range");
+  return PA_OK;
+}
+
 // ---------------------------------------------------------- pa_create --
 
 extern "C" pa_status pa_create(pa_handle* out, int32_t n_rows, int32_t n_cols, int64_t nnz,
@@ -239,10 +286,13 @@ extern "C" pa_status pa_create(pa_handle* out, int32_t n_rows, int32_t n_cols, i
   if (o.barrier_timeout_ns <= 0) o.barrier_timeout_ns = 2000000000LL;
   if (o.loss != PA_LOSS_LOGRATIO && o.loss != PA_LOSS_QUADRATIC)
     return fail(PA_ERR_INVALID_ARG, "unknown loss %d", o.loss);
-  if (o.precision != PA_FP64)
-    return fail(PA_ERR_UNSUPPORTED, "precision mode %d is not available in this build", o.precision);
-  if (o.equilibrate != PA_EQ_NONE)
-    return fail(PA_ERR_UNSUPPORTED, "equilibration is not available in this build");
+  if (o.precision != PA_FP64 && o.precision != PA_MIXED)
+    return fail(PA_ERR_INVALID_ARG, "unknown precision mode %d", o.precision);
+  if (o.equilibrate != PA_EQ_NONE && o.equilibrate != PA_EQ_STORAGE)
+    return fail(PA_ERR_INVALID_ARG, "unknown equilibration mode %d", o.equilibrate);
+  if (o.precision == PA_MIXED && o.loss != PA_LOSS_LOGRATIO)
+    return fail(PA_ERR_UNSUPPORTED, "mixed precision supports the log-ratio loss only");
+  if (o.precision == PA_MIXED) o.equilibrate = PA_EQ_STORAGE;
 
   pa_ctx* h = new pa_ctx();
   h->stream = (cudaStream_t)cuda_stream;
@@ -311,6 +361,9 @@ extern "C" pa_status pa_create(pa_handle* out, int32_t n_rows, int32_t n_cols, i
   dev_free(h, rowid);
   dev_free(h, bsums);
   if ((st = build_sell(h))) return bail(st);
+  if (o.equilibrate == PA_EQ_STORAGE &&
+      (st = build_equilibration(h, o.precision == PA_MIXED)))
+    return bail(st);
   *out = h;
   return PA_OK;
 }
@@ -331,13 +384,26 @@ static pa_status ensure_run_buffers(pa_ctx* h) {
       (st = alloc_n(h, &h->st, 1, "run state")) ||
       (st = alloc_n(h, &h->blockpart, (size_t)2 * 152 * 8 + 64, "block partials")))
     return st;
+  if (h->opt.precision == PA_MIXED &&
+      ((st = alloc_n(h, &h->ylo, (size_t)h->n_rows, "A x (low part)")) ||
+       (st = alloc_n(h, &h->X0f, n, "iterate (FP32)")) || (st = alloc_n(h, &h->X1f, n, "iterate (FP32)")) ||
+       (st = alloc_n(h, &h->X2f, n, "iterate (FP32)")) || (st = alloc_n(h, &h->Wf, n, "D_c x (FP32)")) ||
+       (st = alloc_n(h, &h->mf, n, "first moment (FP32)")) ||
+       (st = alloc_n(h, &h->vf, n, "second moment (FP32)")) ||
+       (st = alloc_n(h, &h->yf, (size_t)h->n_rows, "A x (FP32)")) ||
+       (st = alloc_n(h, &h->dxf, n, "step (FP32)"))))
+    return st;
   h->run_ready = true;
   return PA_OK;
 }
 
 static int choose_grid(pa_ctx* h, int* maxG_out) {
   int per = 0;
-  const int maxG = persistent_max_blocks(h->opt.loss, &per);
+  int maxG = persistent_max_blocks(h->opt.loss, false, &per);
+  if (h->opt.precision == PA_MIXED) {
+    maxG = std::min(maxG, persistent_max_blocks(h->opt.loss, true, &per));
+    maxG = std::min(maxG, persistent32_max_blocks(&per));
+  }
   if (maxG_out) *maxG_out = maxG;
   if (maxG <= 0) return -1;
   const int64_t n = std::max(h->n_rows, h->n_cols);
@@ -415,24 +481,28 @@ static pa_status check_hyper(int iters, double lr, double b1, double b2, double 
   return PA_OK;
 }
 
-// One Algorithm 1 run from the device vector h->Xinit.
-static pa_status run_one(pa_ctx* h, pa_mode mode, int iters, double lr, double b1, double b2,
-                         double eps, double* L_trace_dev, double* x_trace_dev, int n_trace,
-                         RunState* out) {
-  if (mode == PA_SIGMA_MIN && h->n_rows < h->n_cols)
-    return fail(PA_ERR_NOT_SQUARE, "sigma_min needs n_rows >= n_cols (%d x %d)", h->n_rows,
-                h->n_cols);
-  int maxG = 0;
-  const int G = choose_grid(h, &maxG);
-  if (G <= 0) return fail(PA_ERR_LAUNCH, "the persistent kernel does not fit on this GPU");
-  pa_status st;
-  if ((st = ensure_partitions(h, G)) || (st = ensure_bias(h, iters, lr, b1, b2, eps))) return st;
+static pa_status status_error(const RunState* rs) {
+  if (rs->status == PA_ERR_TIMEOUT)
+    return fail(PA_ERR_TIMEOUT, "a grid barrier wait ran out of time (barrier %d)", rs->timeout_site);
+  if (rs->status == PA_ERR_NONFINITE) return fail(PA_ERR_NONFINITE, "a NaN or Inf reached a reduction");
+  return PA_OK;
+}
+
+// One FP64 launch of the persistent kernel: `iters` iterations continuing at
+// iteration t0 + 1 (the bias table is indexed from there).  With fresh_state
+// X0 = Xinit and m = v = 0; otherwise X0, m and v hold the state to continue
+// from.  Then sigma of the tracked minimiser; the run state comes back in *out.
+static pa_status fp64_run(pa_ctx* h, pa_mode mode, int iters, int t0, bool fresh_state, bool dd,
+                          double b1, double b2, double eps, int G, int maxG, double* L_trace_dev,
+                          double* x_trace_dev, int n_trace, RunState* out) {
   const size_t n = (size_t)h->n_cols;
-  cudaError_t e;
-  if ((e = cudaMemcpyAsync(h->X0, h->Xinit, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream)) ||
-      (e = cudaMemsetAsync(h->m, 0, sizeof(double) * n, h->stream)) ||
-      (e = cudaMemsetAsync(h->v, 0, sizeof(double) * n, h->stream)) ||
-      (e = cudaMemsetAsync(h->st, 0, sizeof(RunState), h->stream)) ||
+  cudaError_t e = cudaSuccess;
+  if (fresh_state &&
+      ((e = cudaMemcpyAsync(h->X0, h->Xinit, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream)) ||
+       (e = cudaMemsetAsync(h->m, 0, sizeof(double) * n, h->stream)) ||
+       (e = cudaMemsetAsync(h->v, 0, sizeof(double) * n, h->stream))))
+    return cuda_fail(e, "preparing the run");
+  if ((e = cudaMemsetAsync(h->st, 0, sizeof(RunState), h->stream)) ||
       (e = cudaMemsetAsync(h->ready, 0, sizeof(unsigned) * G, h->stream)))
     return cuda_fail(e, "preparing the run");
   IterParams p{};
@@ -454,29 +524,145 @@ static pa_status run_one(pa_ctx* h, pa_mode mode, int iters, double lr, double b
   p.n_trace = n_trace;
   p.st = h->st;
   p.iters = iters;
+  p.t0 = t0;
   p.mode = mode;
   p.ablation = h->opt.ablation;
   p.beta1 = b1; p.beta2 = b2; p.eps = eps;
   p.timeout_ns = h->opt.barrier_timeout_ns;
   p.skip_arrival = h->opt.debug_skip_arrival;
-  e = launch_persistent(p, h->opt.loss, G, h->stream, &h->launches);
+  e = launch_persistent(p, h->opt.loss, dd, G, h->stream, &h->launches);
   if (e == cudaErrorCooperativeLaunchTooLarge)
     return fail(PA_ERR_LAUNCH, "cooperative grid of %d CTAs does not fit (max %d)", G, maxG);
   if (e != cudaSuccess) return cuda_fail(e, "launching the persistent kernel");
-  if ((e = launch_sigma(h->sa, h->n_cols, h->X0, h->X1, h->X2, 1, h->st, h->blockpart, h->stream,
-                        &h->launches)))
+  if ((e = launch_sigma(h->sa, h->n_cols, h->X0, h->X1, h->X2, 1, h->st, h->blockpart, dd,
+                        h->stream, &h->launches)))
     return cuda_fail(e, "launching the sigma kernel");
   if ((e = cudaMemcpyAsync(out, h->st, sizeof(RunState), cudaMemcpyDeviceToHost, h->stream)) ||
       (e = cudaStreamSynchronize(h->stream)))
     return cuda_fail(e, "running Projected Adam");
-  double* keep = mode == PA_SIGMA_MAX ? h->xmin_max : h->xmin_min;
-  double* src = out->minb == 0 ? h->X0 : (out->minb == 1 ? h->X1 : h->X2);
-  if ((e = launch_unpermute(h->n_cols, 1, h->sq.pos, src, keep, h->stream, &h->launches)))
+  return PA_OK;
+}
+
+static float* pick32h(pa_ctx* h, int k) { return k == 0 ? h->X0f : (k == 1 ? h->X1f : h->X2f); }
+static double* pick64h(pa_ctx* h, int k) { return k == 0 ? h->X0 : (k == 1 ? h->X1 : h->X2); }
+
+// Mixed-precision sigma_max: FP32 stage (iters - tail iterations), then the
+// FP64 tail from the converted FP32 state.  x_min is the tracked minimiser of
+// whichever stage scores the larger sigma in FP64.
+static pa_status mixed_max_run(pa_ctx* h, int iters, double b1, double b2, double eps, int G,
+                               int maxG, double* L_trace_dev, RunState* out) {
+  const int tail = h->opt.fp64_tail < 0 ? iters / 10 : std::min(h->opt.fp64_tail, iters);
+  const int t32 = iters - tail;
+  const size_t n = (size_t)h->n_cols;
+  cudaError_t e;
+  // ---- FP32 stage
+  if ((e = launch_convert((int64_t)n, h->Xinit, h->X0f, h->stream, &h->launches)) ||
+      (e = cudaMemsetAsync(h->mf, 0, sizeof(float) * n, h->stream)) ||
+      (e = cudaMemsetAsync(h->vf, 0, sizeof(float) * n, h->stream)) ||
+      (e = cudaMemsetAsync(h->st, 0, sizeof(RunState), h->stream)) ||
+      (e = cudaMemsetAsync(h->ready, 0, sizeof(unsigned) * G, h->stream)))
+    return cuda_fail(e, "preparing the FP32 stage");
+  IterParams32 q{};
+  q.n_rows = h->n_rows;
+  q.n_cols = h->n_cols;
+  q.a_wp = h->sa.wp; q.a_col = h->sa.col; q.a_val = h->a_val32;
+  q.t_wp = h->sq.wp; q.t_col = h->sq.col; q.t_val = h->t_val32;
+  q.dr = h->drp32; q.dc = h->dcp32;
+  q.part_a = h->part_a; q.part_t = h->part_t; q.dep = h->dep;
+  q.X0 = h->X0f; q.X1 = h->X1f; q.X2 = h->X2f; q.W = h->Wf;
+  q.m = h->mf; q.v = h->vf; q.y = h->yf; q.dx = h->dxf;
+  q.partials = h->partials;
+  q.ready = h->ready;
+  q.cta_ns = h->cta_ns;
+  q.bias = h->bias;
+  q.L_trace = L_trace_dev;
+  q.st = h->st;
+  q.iters = t32;
+  q.ablation = h->opt.ablation;
+  q.beta1 = b1; q.beta2 = b2;
+  q.timeout_ns = h->opt.barrier_timeout_ns;
+  q.skip_arrival = h->opt.debug_skip_arrival;
+  h->last_G = G;
+  e = launch_persistent32(q, G, h->stream, &h->launches);
+  if (e == cudaErrorCooperativeLaunchTooLarge)
+    return fail(PA_ERR_LAUNCH, "cooperative grid of %d CTAs does not fit (max %d)", G, maxG);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the FP32 persistent kernel");
+  RunState r32{};
+  if ((e = cudaMemcpyAsync(&r32, h->st, sizeof(RunState), cudaMemcpyDeviceToHost, h->stream)) ||
+      (e = cudaStreamSynchronize(h->stream)))
+    return cuda_fail(e, "running the FP32 stage");
+  pa_status st;
+  if ((st = status_error(&r32))) return st;
+  // candidate 1: the FP32 stage's tracked minimiser, scored in FP64 (in X1)
+  if ((e = launch_convert((int64_t)n, pick32h(h, r32.minb), h->X1, h->stream, &h->launches)) ||
+      (e = launch_sigma(h->sa, h->n_cols, h->X1, h->X1, h->X1, 0, h->st, h->blockpart, false,
+                        h->stream, &h->launches)))
+    return cuda_fail(e, "scoring the FP32 stage");
+  double sig32 = 0;
+  if ((e = cudaMemcpyAsync(&sig32, &h->st->sigma, sizeof(double), cudaMemcpyDeviceToHost, h->stream)) ||
+      (e = cudaStreamSynchronize(h->stream)))
+    return cuda_fail(e, "scoring the FP32 stage");
+  if ((e = launch_unpermute(h->n_cols, 1, h->sq.pos, h->X1, h->xmin_max, h->stream, &h->launches)))
     return cuda_fail(e, "keeping x_min");
-  if (out->status == PA_ERR_TIMEOUT)
-    return fail(PA_ERR_TIMEOUT, "a grid barrier wait ran out of time (barrier %d)", out->timeout_site);
-  if (out->status == PA_ERR_NONFINITE)
-    return fail(PA_ERR_NONFINITE, "a NaN or Inf reached a reduction");
+  *out = r32;
+  out->sigma = sig32;
+  out->cur = 0;
+  // the last FP32 iterate, in FP64, continues (or is x_last when there is no tail)
+  if ((e = launch_convert((int64_t)n, pick32h(h, r32.cur), h->X0, h->stream, &h->launches)))
+    return cuda_fail(e, "converting the FP32 state");
+  if (tail == 0 || r32.status != PA_OK) return (pa_status)r32.status;
+  // ---- FP64 tail near convergence
+  if ((e = launch_convert((int64_t)n, h->mf, h->m, h->stream, &h->launches)) ||
+      (e = launch_convert((int64_t)n, h->vf, h->v, h->stream, &h->launches)))
+    return cuda_fail(e, "converting the FP32 state");
+  RunState r64{};
+  if ((st = fp64_run(h, PA_SIGMA_MAX, tail, t32, false, false, b1, b2, eps, G, maxG,
+                     L_trace_dev ? L_trace_dev + t32 : nullptr, nullptr, 0, &r64)))
+    return st;
+  if ((st = status_error(&r64))) return st;
+  out->iters_run = r32.iters_run + r64.iters_run;
+  out->cur = r64.cur;
+  out->L_last = r64.L_last;
+  out->status = r64.status;
+  if (r64.sigma > sig32) {  // the FP64 tail found the better iterate
+    out->sigma = r64.sigma;
+    out->L_min = r64.L_min;
+    out->t_min = t32 + r64.t_min;
+    out->minb = r64.minb;
+    if ((e = launch_unpermute(h->n_cols, 1, h->sq.pos, pick64h(h, r64.minb), h->xmin_max,
+                              h->stream, &h->launches)))
+      return cuda_fail(e, "keeping x_min");
+  }
+  return (pa_status)out->status;
+}
+
+// One Algorithm 1 run from the device vector h->Xinit.
+static pa_status run_one(pa_ctx* h, pa_mode mode, int iters, double lr, double b1, double b2,
+                         double eps, double* L_trace_dev, double* x_trace_dev, int n_trace,
+                         RunState* out) {
+  if (mode == PA_SIGMA_MIN && h->n_rows < h->n_cols)
+    return fail(PA_ERR_NOT_SQUARE, "sigma_min needs n_rows >= n_cols (%d x %d)", h->n_rows,
+                h->n_cols);
+  const bool mixed = h->opt.precision == PA_MIXED;
+  if (mixed && mode == PA_SIGMA_MAX && x_trace_dev)
+    return fail(PA_ERR_INVALID_ARG, "x traces are not available for the mixed-precision sigma_max");
+  int maxG = 0;
+  const int G = choose_grid(h, &maxG);
+  if (G <= 0) return fail(PA_ERR_LAUNCH, "the persistent kernel does not fit on this GPU");
+  pa_status st;
+  if ((st = ensure_partitions(h, G)) || (st = ensure_bias(h, iters, lr, b1, b2, eps))) return st;
+  if (mixed && mode == PA_SIGMA_MAX) {
+    if ((st = mixed_max_run(h, iters, b1, b2, eps, G, maxG, L_trace_dev, out)) < 0) return st;
+  } else {
+    if ((st = fp64_run(h, mode, iters, 0, true, mixed, b1, b2, eps, G, maxG, L_trace_dev,
+                       x_trace_dev, n_trace, out)))
+      return st;
+    double* keep = mode == PA_SIGMA_MAX ? h->xmin_max : h->xmin_min;
+    cudaError_t e = launch_unpermute(h->n_cols, 1, h->sq.pos, pick64h(h, out->minb), keep,
+                                     h->stream, &h->launches);
+    if (e != cudaSuccess) return cuda_fail(e, "keeping x_min");
+    if ((st = status_error(out))) return st;
+  }
   if (mode == PA_SIGMA_MAX) { h->sigma_max = out->sigma; h->have_max = true; }
   else { h->sigma_min = out->sigma; h->have_min = true; }
   return (pa_status)out->status;
@@ -674,10 +860,16 @@ extern "C" pa_status pa_last_run_profile(pa_handle h, int* grid, double* busy_ns
 
 extern "C" pa_status pa_get_equilibration(pa_handle h, double* d_row, double* d_col) {
   g_err.clear();
-  (void)d_row;
-  (void)d_col;
   if (!h) return fail(PA_ERR_INVALID_ARG, "NULL handle");
-  return fail(PA_ERR_INVALID_ARG, "the handle holds no equilibration");
+  if (!h->d_row) return fail(PA_ERR_INVALID_ARG, "the handle holds no equilibration");
+  cudaError_t e = cudaSuccess;
+  if (d_row)
+    e = cudaMemcpyAsync(d_row, h->d_row, sizeof(double) * h->n_rows, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && d_col)
+    e = cudaMemcpyAsync(d_col, h->d_col, sizeof(double) * h->n_cols, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the equilibration");
+  return PA_OK;
 }
 
 extern "C" pa_status pa_estimate_batched(int n_mat, const pa_handle* handles, pa_mode mode,

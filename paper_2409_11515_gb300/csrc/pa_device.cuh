@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "pa_internal.h"
+
 namespace pa {
 
 // SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): output i of the generator
@@ -121,6 +123,89 @@ __device__ __forceinline__ double slice_dot(const int32_t* __restrict__ wp,
   return acc;
 }
 
+// ---- compensated (double-double) products --------------------------------
+// Error-free transformations: TwoProduct with one FMA (p + e = a b exactly)
+// and TwoSum (Knuth; s + e = a + b exactly).  The additions are written with
+// __dadd_rn / __dsub_rn so the compiler cannot contract them into FMAs.
+__device__ __forceinline__ void two_prod(double a, double b, double& p, double& e) {
+  p = __dmul_rn(a, b);
+  e = fma(a, b, -p);
+}
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+  const double x = __dadd_rn(a, b);
+  const double z = __dsub_rn(x, a);
+  e = __dadd_rn(__dsub_rn(a, __dsub_rn(x, z)), __dsub_rn(b, z));
+  s = x;
+}
+// One step of the Dot2 scheme (Ogita, Rump & Oishi 2005): add a*b to the
+// running sum s with its error collected in c.
+__device__ __forceinline__ void dot2_step(double a, double b, double& s, double& c) {
+  double p, pe, t, te;
+  two_prod(a, b, p, pe);
+  two_sum(s, p, t, te);
+  s = t;
+  c = __dadd_rn(c, __dadd_rn(te, pe));
+}
+
+// Compensated row product of lane `lane` of slice s: returns hi, lo with
+// hi = fl(hi + lo) (the unevaluated double-double sum), entries in storage order.
+__device__ __forceinline__ void slice_dot_dd(const int32_t* __restrict__ wp,
+                                             const int32_t* __restrict__ col,
+                                             const double* __restrict__ val, int s, int lane,
+                                             const double* x, double& hi, double& lo) {
+  const int w0 = __ldg(wp + s), w = __ldg(wp + s + 1) - w0;
+  const int64_t base = 32ll * w0 + lane;
+  double sum = 0.0, c = 0.0;
+  int k = 0;
+  for (; k + 4 <= w; k += 4) {  // loads of four entries issued before the chain
+    const int64_t e = base + 32ll * k;
+    const int j0 = __ldg(col + e), j1 = __ldg(col + e + 32), j2 = __ldg(col + e + 64),
+              j3 = __ldg(col + e + 96);
+    const double a0 = __ldg(val + e), a1 = __ldg(val + e + 32), a2 = __ldg(val + e + 64),
+                 a3 = __ldg(val + e + 96);
+    const double x0 = x[j0], x1 = x[j1], x2 = x[j2], x3 = x[j3];
+    dot2_step(a0, x0, sum, c);
+    dot2_step(a1, x1, sum, c);
+    dot2_step(a2, x2, sum, c);
+    dot2_step(a3, x3, sum, c);
+  }
+  for (; k < w; ++k) {
+    const int64_t e = base + 32ll * k;
+    dot2_step(__ldg(val + e), x[__ldg(col + e)], sum, c);
+  }
+  two_sum(sum, c, hi, lo);
+}
+
+// Compensated row product with a double-double vector (xh + xl): for each
+// entry the hi term, then the lo term; rounded to one double.
+__device__ __forceinline__ double slice_dot_dd2(const int32_t* __restrict__ wp,
+                                                const int32_t* __restrict__ col,
+                                                const double* __restrict__ val, int s,
+                                                int lane, const double* xh, const double* xl) {
+  const int w0 = __ldg(wp + s), w = __ldg(wp + s + 1) - w0;
+  const int64_t base = 32ll * w0 + lane;
+  double sum = 0.0, c = 0.0;
+  int k = 0;
+  for (; k + 2 <= w; k += 2) {  // loads of two entries issued before the chain
+    const int64_t e = base + 32ll * k;
+    const int32_t j0 = __ldg(col + e), j1 = __ldg(col + e + 32);
+    const double a0 = __ldg(val + e), a1 = __ldg(val + e + 32);
+    const double h0 = xh[j0], l0 = xl[j0], h1 = xh[j1], l1 = xl[j1];
+    dot2_step(a0, h0, sum, c);
+    dot2_step(a0, l0, sum, c);
+    dot2_step(a1, h1, sum, c);
+    dot2_step(a1, l1, sum, c);
+  }
+  for (; k < w; ++k) {
+    const int64_t e = base + 32ll * k;
+    const double a = __ldg(val + e);
+    const int32_t j = __ldg(col + e);
+    dot2_step(a, xh[j], sum, c);
+    dot2_step(a, xl[j], sum, c);
+  }
+  return __dadd_rn(sum, c);
+}
+
 // Block sum of NV per-thread values, result in thread 0 only.  Every thread
 // stores its values in `scratch` (NV * blockDim.x doubles); warp 0 adds them
 // in a fixed order (lane l sums threads l, l+32, ... sequentially, then a
@@ -140,6 +225,82 @@ __device__ __forceinline__ void block_sum_to0(double (&v)[NV], double* scratch) 
       v[i] = warp_sum(a);
     }
   }
+}
+
+// ----------------------------------------------------------- grid sync --
+// (used by the persistent kernels; RunState comes from pa_internal.h)
+
+// Grid-wide barrier with a time limit.  Returns false when the wait gave up
+// (this CTA's or another's), after which the caller must leave the kernel.
+__device__ __forceinline__ bool grid_barrier(RunState* st, unsigned& target, unsigned G,
+                                             long long timeout_ns, bool skip_arrival,
+                                             int site, int& ok_slot) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    target += G;
+    int ok = 1;
+    if (!skip_arrival) {
+      __threadfence();
+      atomicAdd(&st->barrier, 1u);
+    }
+    const long long t0 = globaltimer_ns();
+    int spins = 0;
+    while (true) {
+      const unsigned c = ld_acquire_u32(&st->barrier);
+      if ((int)(c - target) >= 0) break;
+      if (ld_relaxed_u32(&st->abort) != 0u) { ok = 0; break; }
+      if (++spins > 64) {
+        if (globaltimer_ns() - t0 > timeout_ns) {
+          if (atomicExch(&st->abort, 1u) == 0u) st->timeout_site = site;
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok_slot = ok;
+  }
+  __syncthreads();
+  return ok_slot != 0;
+}
+
+// Wait until every CTA in [lo, hi] has published iterate t (its ready flag
+// reaches t), with the same time limit and abort flag as grid_barrier.  Only
+// the CTAs whose x rows this CTA's products read take part, so this replaces
+// a grid-wide barrier between the update of x and the next product.
+__device__ __forceinline__ bool wait_ready(RunState* st, const unsigned* ready, int lo, int hi,
+                                           unsigned t, long long timeout_ns, int site,
+                                           int& ok_slot) {
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const long long t0 = globaltimer_ns();
+    int spins = 0;
+    for (int j = lo; j <= hi && ok; ++j) {
+      while (true) {
+        const unsigned c = ld_acquire_u32(ready + j);
+        if ((int)(c - t) >= 0) break;
+        if (ld_relaxed_u32(&st->abort) != 0u) { ok = 0; break; }
+        if (++spins > 64) {
+          if (globaltimer_ns() - t0 > timeout_ns) {
+            if (atomicExch(&st->abort, 1u) == 0u) st->timeout_site = site;
+            ok = 0;
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+    }
+    __threadfence();
+    ok_slot = ok;
+  }
+  __syncthreads();
+  return ok_slot != 0;
+}
+
+__device__ __forceinline__ void publish_ready(unsigned* flag, unsigned t) {
+  __threadfence();
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(flag), "r"(t) : "memory");
 }
 
 }  // namespace pa

@@ -66,9 +66,35 @@ struct IterParams {
   int n_trace;
   RunState* st;
   int iters;
+  int t0;         // iterations already done (bias corrections continue at t0 + 1)
   int mode;       // PA_SIGMA_MAX / PA_SIGMA_MIN
   int ablation;   // PA_ABLATE_* bits
   double beta1, beta2, eps;
+  long long timeout_ns;
+  int skip_arrival;
+};
+
+// The mixed-precision sigma_max iteration (FP32 products and Adam state on
+// the power-of-two-equilibrated matrix, FP64 norms).
+struct IterParams32 {
+  int32_t n_rows, n_cols;
+  const int32_t* a_wp; const int32_t* a_col; const float* a_val;  // P A_hat Q^T (sliced)
+  const int32_t* t_wp; const int32_t* t_col; const float* t_val;  // Q A_hat^T P^T
+  const float* dr;   // [n_rows] D_r at the row positions of P A Q^T
+  const float* dc;   // [n_cols] D_c at the x positions
+  const int32_t* part_a; const int32_t* part_t; const int32_t* dep;
+  float* X0; float* X1; float* X2;  // iterate buffers
+  float* W;                          // D_c x of the latest iterate
+  float* m; float* v; float* y; float* dx;
+  double* partials;
+  unsigned* ready;
+  unsigned long long* cta_ns;
+  const double2* bias;
+  double* L_trace;
+  RunState* st;
+  int iters;
+  int ablation;
+  double beta1, beta2;
   long long timeout_ns;
   int skip_arrival;
 };
@@ -136,7 +162,7 @@ cudaError_t launch_sell_spmv(const Sell& m, const double* x, double* y, cudaStre
 int sigma_blocks(int32_t n_slices, int32_t n_cols);
 cudaError_t launch_sigma(const Sell& m, int32_t n_cols, const double* X0, const double* X1,
                          const double* X2, int use_minb, RunState* st, double* blockpart,
-                         cudaStream_t s, int64_t* launches);
+                         bool dd, cudaStream_t s, int64_t* launches);
 
 // dep[2b], dep[2b+1] = first and last CTA owning an x position that a
 // non-zero of CTA b's slices of the (permuted) matrix reads.
@@ -144,9 +170,34 @@ cudaError_t launch_dependencies(const int32_t* wp, const int32_t* col, const dou
                                 const int32_t* part_a, const int32_t* part_t, int G,
                                 int32_t* dep, cudaStream_t s, int64_t* launches);
 
-// Persistent cooperative Projected Adam run (Algorithm 1) over a grid of G CTAs.
-int persistent_max_blocks(int loss, int* blocks_per_sm);
-cudaError_t launch_persistent(const IterParams& p, int loss, int G, cudaStream_t s,
+int persistent32_max_blocks(int* blocks_per_sm);
+cudaError_t launch_persistent32(const IterParams32& p, int G, cudaStream_t s, int64_t* launches);
+
+// Power-of-two equilibration (the paper's row then column 2-norm scaling,
+// each factor rounded to the nearest power of two), computed with the same
+// operation order as the CPU oracle: d_row from CSR(A), d_col from the
+// transpose (entries in row order) of D_row^-1 A.
+cudaError_t launch_equilibrate(int32_t n_rows, int32_t n_cols, const int32_t* rp,
+                               const double* va, const int32_t* rpt, const int32_t* cit,
+                               const double* vat, double* d_row, double* d_col, cudaStream_t s,
+                               int64_t* launches);
+// out[p] = (float) d[perm[p]] for p < n (permuted factors), and flags in
+// *range_flag (bit 1) any factor outside the FP32 normal range.
+cudaError_t launch_permute_factors(int32_t n, const int32_t* perm, const double* d, float* out,
+                                   int* range_flag, cudaStream_t s, int64_t* launches);
+// FP32 values of the sliced equilibrated matrix: val32[e] = (float)(val[e] /
+// drow[row position] / dcol[column position]) for every slice entry of m.
+cudaError_t launch_sell_scale32(const Sell& m, const float* d_rowpos, const float* d_colpos,
+                                float* val32, cudaStream_t s, int64_t* launches);
+cudaError_t launch_convert(int64_t n, const float* in, double* out, cudaStream_t s,
+                           int64_t* launches);
+cudaError_t launch_convert(int64_t n, const double* in, float* out, cudaStream_t s,
+                           int64_t* launches);
+
+// Persistent cooperative Projected Adam run (Algorithm 1) over a grid of G
+// CTAs; dd selects compensated (double-double) products.
+int persistent_max_blocks(int loss, bool dd, int* blocks_per_sm);
+cudaError_t launch_persistent(const IterParams& p, int loss, bool dd, int G, cudaStream_t s,
                               int64_t* launches);
 
 }  // namespace pa

@@ -57,79 +57,6 @@ struct Shared {
   long long tmark;
 };
 
-// Grid-wide barrier with a time limit.  Returns false when the wait gave up
-// (this CTA's or another's), after which the caller must leave the kernel.
-__device__ __forceinline__ bool grid_barrier(RunState* st, unsigned& target, unsigned G,
-                                             long long timeout_ns, bool skip_arrival,
-                                             int site, Shared& sh) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    target += G;
-    int ok = 1;
-    if (!skip_arrival) {
-      __threadfence();
-      atomicAdd(&st->barrier, 1u);
-    }
-    const long long t0 = globaltimer_ns();
-    int spins = 0;
-    while (true) {
-      const unsigned c = ld_acquire_u32(&st->barrier);
-      if ((int)(c - target) >= 0) break;
-      if (ld_relaxed_u32(&st->abort) != 0u) { ok = 0; break; }
-      if (++spins > 64) {
-        if (globaltimer_ns() - t0 > timeout_ns) {
-          if (atomicExch(&st->abort, 1u) == 0u) st->timeout_site = site;
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    sh.ok = ok;
-  }
-  __syncthreads();
-  return sh.ok != 0;
-}
-
-// Wait until every CTA in [lo, hi] has published iterate t (its ready flag
-// reaches t), with the same time limit and abort flag as grid_barrier.  Only
-// the CTAs whose x rows this CTA's products read take part, so this replaces
-// a grid-wide barrier between the update of x and the next product.
-__device__ __forceinline__ bool wait_ready(RunState* st, const unsigned* ready, int lo, int hi,
-                                           unsigned t, long long timeout_ns, int site,
-                                           Shared& sh) {
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    const long long t0 = globaltimer_ns();
-    int spins = 0;
-    for (int j = lo; j <= hi && ok; ++j) {
-      while (true) {
-        const unsigned c = ld_acquire_u32(ready + j);
-        if ((int)(c - t) >= 0) break;
-        if (ld_relaxed_u32(&st->abort) != 0u) { ok = 0; break; }
-        if (++spins > 64) {
-          if (globaltimer_ns() - t0 > timeout_ns) {
-            if (atomicExch(&st->abort, 1u) == 0u) st->timeout_site = site;
-            ok = 0;
-            break;
-          }
-          __nanosleep(32);
-        }
-      }
-    }
-    __threadfence();
-    sh.ok = ok;
-  }
-  __syncthreads();
-  return sh.ok != 0;
-}
-
-__device__ __forceinline__ void publish_ready(unsigned* flag, unsigned t) {
-  __threadfence();
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(flag), "r"(t) : "memory");
-}
-
 __device__ __forceinline__ double* pick(const IterParams& p, int k) {
   return k == 0 ? p.X0 : (k == 1 ? p.X1 : p.X2);
 }
@@ -140,7 +67,7 @@ __device__ __forceinline__ double loss_value(int mode, int loss, double s, doubl
   return mode == PA_SIGMA_MAX ? lx - lax : lax - lx;
 }
 
-template <int LOSS>
+template <int LOSS, bool DD>
 __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const IterParams p) {
   __shared__ Shared sh;
   constexpr int NW = kBlock / 32;
@@ -183,7 +110,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
 
   for (int t = 1;; ++t) {
     // x_{t-1} of the neighbours must be written before the gathers below
-    if (t > 1 && !wait_ready(st, p.ready, dlo, dhi, (unsigned)(t - 1), p.timeout_ns, site++, sh)) {
+    if (t > 1 && !wait_ready(st, p.ready, dlo, dhi, (unsigned)(t - 1), p.timeout_ns, site++, sh.ok)) {
       status = PA_ERR_TIMEOUT;
       break;
     }
@@ -193,8 +120,15 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
     {
       double v[2] = {0.0, qloc};
       for (int s = sa0 + warp; s < sa1; s += NW) {
-        const double yr = slice_dot(p.a_wp, p.a_col, p.a_val, s, lane, x);
         const int r = 32 * s + lane;
+        double yr;
+        if (DD) {
+          double lo;
+          slice_dot_dd(p.a_wp, p.a_col, p.a_val, s, lane, x, yr, lo);
+          if (r < p.n_rows) p.ylo[r] = lo;
+        } else {
+          yr = slice_dot(p.a_wp, p.a_col, p.a_val, s, lane, x);
+        }
         if (r < p.n_rows) {
           p.y[r] = yr;
           v[0] = fma(yr, yr, v[0]);
@@ -208,7 +142,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
       }
     }
     const bool skip = (p.skip_arrival == t) && (b == 0);
-    if (!grid_barrier(st, target, G, p.timeout_ns, skip, site++, sh)) { status = PA_ERR_TIMEOUT; break; }
+    if (!grid_barrier(st, target, G, p.timeout_ns, skip, site++, sh.ok)) { status = PA_ERR_TIMEOUT; break; }
     if (tid < 32) {
       const double s_ = ordered_sum(part, G, kPartSlots, 0);
       const double q = ordered_sum(part, G, kPartSlots, 1);
@@ -260,13 +194,14 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
       const double ca = sh.ca, cb = sh.cb;
       // lr m_hat / (sqrt(v_hat) + eps) = K1 m / (sqrt(v) + K2) with
       // K1 = lr sqrt(1-b2^t) / (1-b1^t) and K2 = eps sqrt(1-b2^t)
-      const double2 bc = p.bias[t - 1];
+      const double2 bc = p.bias[p.t0 + t - 1];
       const double b1 = p.beta1, b2 = p.beta2;
       // (1 - beta2) g^2 = w2 g'^2 with g' = (1 - beta1) g
       const double w2 = (1.0 - b2) / ((1.0 - b1) * (1.0 - b1));
       double v[2] = {0.0, 0.0};
       for (int s = st0 + warp; s < st1; s += NW) {
-        const double z = slice_dot(p.t_wp, p.t_col, p.t_val, s, lane, p.y);
+        const double z = DD ? slice_dot_dd2(p.t_wp, p.t_col, p.t_val, s, lane, p.y, p.ylo)
+                            : slice_dot(p.t_wp, p.t_col, p.t_val, s, lane, p.y);
         const int j = 32 * s + lane;
         if (j < n) {
           const double xj = x[j];
@@ -288,7 +223,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
         sh.busy_b += (unsigned long long)(globaltimer_ns() - sh.tmark);
       }
     }
-    if (!grid_barrier(st, target, G, p.timeout_ns, false, site++, sh)) { status = PA_ERR_TIMEOUT; break; }
+    if (!grid_barrier(st, target, G, p.timeout_ns, false, site++, sh.ok)) { status = PA_ERR_TIMEOUT; break; }
     if (tid < 32) {
       const double p1 = ordered_sum(part, G, kPartSlots, 2);
       const double p2 = ordered_sum(part, G, kPartSlots, 3);
@@ -360,25 +295,29 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
 
 }  // namespace
 
-int persistent_max_blocks(int loss, int* blocks_per_sm) {
+static void* persistent_fn(int loss, bool dd) {
+  if (loss == PA_LOSS_QUADRATIC)
+    return dd ? (void*)k_persistent<PA_LOSS_QUADRATIC, true>
+              : (void*)k_persistent<PA_LOSS_QUADRATIC, false>;
+  return dd ? (void*)k_persistent<PA_LOSS_LOGRATIO, true>
+            : (void*)k_persistent<PA_LOSS_LOGRATIO, false>;
+}
+
+int persistent_max_blocks(int loss, bool dd, int* blocks_per_sm) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaError_t e;
-  if (loss == PA_LOSS_QUADRATIC)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persistent<PA_LOSS_QUADRATIC>, kBlock, 0);
-  else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persistent<PA_LOSS_LOGRATIO>, kBlock, 0);
+  const cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, persistent_fn(loss, dd), kBlock, 0);
   if (e != cudaSuccess) return -1;
   if (blocks_per_sm) *blocks_per_sm = per;
   return per * sms;
 }
 
-cudaError_t launch_persistent(const IterParams& p, int loss, int G, cudaStream_t s,
+cudaError_t launch_persistent(const IterParams& p, int loss, bool dd, int G, cudaStream_t s,
                               int64_t* launches) {
   void* args[] = {(void*)&p};
-  void* fn = loss == PA_LOSS_QUADRATIC ? (void*)k_persistent<PA_LOSS_QUADRATIC>
-                                       : (void*)k_persistent<PA_LOSS_LOGRATIO>;
+  void* fn = persistent_fn(loss, dd);
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kBlock), args, 0, s);
   ++*launches;
   return e;

@@ -267,6 +267,85 @@ __global__ void __launch_bounds__(kT) k_dependencies(const int32_t* __restrict__
   }
 }
 
+// -------------------------------------------------------- equilibration --
+// Nearest power of two to r > 0: r = f 2^e with f in [0.5, 1); 2^e when
+// f >= sqrt(1/2), else 2^(e-1).  Zero, negative or non-finite r give 1.
+__device__ __forceinline__ double nearest_pow2(double r) {
+  if (!(r > 0.0) || !isfinite(r)) return 1.0;
+  int e;
+  const double f = frexp(r, &e);
+  return f >= 0.70710678118654752440 ? ldexp(1.0, e) : ldexp(1.0, e - 1);
+}
+
+// Row 2-norms: squares summed in storage order without FMA (the oracle's order).
+__global__ void k_row_norm_pow2(int32_t n, const int32_t* __restrict__ rp,
+                                const double* __restrict__ va, double* d) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+    double s = 0.0;
+    for (int32_t k = rp[r]; k < rp[r + 1]; ++k) s = __dadd_rn(s, __dmul_rn(va[k], va[k]));
+    d[r] = nearest_pow2(sqrt(s));
+  }
+}
+
+// Column 2-norms of D_row^-1 A over the rows of A^T (contributions in
+// increasing row order, as the oracle's scatter adds them).
+__global__ void k_col_norm_pow2(int32_t n_cols, const int32_t* __restrict__ rpt,
+                                const int32_t* __restrict__ cit, const double* __restrict__ vat,
+                                const double* __restrict__ d_row, double* d_col) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_cols; j += stride) {
+    double s = 0.0;
+    for (int32_t k = rpt[j]; k < rpt[j + 1]; ++k) {
+      const double a = __ddiv_rn(vat[k], d_row[cit[k]]);
+      s = __dadd_rn(s, __dmul_rn(a, a));
+    }
+    d_col[j] = nearest_pow2(sqrt(s));
+  }
+}
+
+__global__ void k_permute_factors(int32_t n, const int32_t* __restrict__ perm,
+                                  const double* __restrict__ d, float* out, int* flag) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
+    const double v = d[perm[q]];
+    if (!(v >= 0x1.0p-126 && v <= 0x1.0p+126)) atomicOr(flag, 1);
+    out[q] = (float)v;
+  }
+}
+
+// One thread per (slice, lane) of m: scale the lane's entries by its row
+// factor and each entry's column factor, round to FP32.
+__global__ void k_sell_scale32(int32_t n_rows, int32_t ns, const int32_t* __restrict__ wp,
+                               const int32_t* __restrict__ col, const double* __restrict__ val,
+                               const float* __restrict__ drow, const float* __restrict__ dcol,
+                               float* val32) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 32ll * ns; t += stride) {
+    const int64_t s = t >> 5;
+    const int lane = (int)(t & 31);
+    const int64_t p = 32 * s + lane;
+    const int w0 = wp[s], w = wp[s + 1] - w0;
+    const double dr = p < n_rows ? (double)drow[p] : 1.0;
+    for (int k = 0; k < w; ++k) {
+      const int64_t e = 32ll * (w0 + k) + lane;
+      val32[e] = (float)(val[e] / dr / (double)dcol[col[e]]);
+    }
+  }
+}
+
+__global__ void k_f32_to_f64(int64_t n, const float* __restrict__ in, double* out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    out[i] = (double)in[i];
+}
+
+__global__ void k_f64_to_f32(int64_t n, const double* __restrict__ in, float* out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    out[i] = (float)in[i];
+}
+
 // ------------------------------------------------------ sliced ELL build --
 __global__ void k_row_lengths(int32_t n, const int32_t* __restrict__ rp, int32_t* lens) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -419,6 +498,7 @@ __device__ __forceinline__ const double* select_x(const double* X0, const double
   return k == 0 ? X0 : (k == 1 ? X1 : X2);
 }
 
+template <bool DD>
 __global__ void __launch_bounds__(kT) k_sigma_part(int32_t n_rows, int32_t ns, int32_t n_cols,
                                                    const int32_t* __restrict__ wp,
                                                    const int32_t* __restrict__ col,
@@ -433,7 +513,9 @@ __global__ void __launch_bounds__(kT) k_sigma_part(int32_t n_rows, int32_t ns, i
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < ns;
        s += warps) {
-    const double a = slice_dot(wp, col, val, (int)s, lane, x);
+    double a, lo;
+    if (DD) slice_dot_dd(wp, col, val, (int)s, lane, x, a, lo);
+    else a = slice_dot(wp, col, val, (int)s, lane, x);
     if (32 * s + lane < n_rows) v[0] = fma(a, a, v[0]);
   }
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -505,6 +587,45 @@ cudaError_t launch_partition(const int32_t* wp, int32_t n_slices, int G, int row
 }
 
 int32_t sell_slices(int32_t n_rows) { return (n_rows + 31) / 32; }
+
+cudaError_t launch_equilibrate(int32_t n_rows, int32_t n_cols, const int32_t* rp,
+                               const double* va, const int32_t* rpt, const int32_t* cit,
+                               const double* vat, double* d_row, double* d_col, cudaStream_t s,
+                               int64_t* launches) {
+  k_row_norm_pow2<<<grid_for(n_rows), kT, 0, s>>>(n_rows, rp, va, d_row);
+  k_col_norm_pow2<<<grid_for(n_cols), kT, 0, s>>>(n_cols, rpt, cit, vat, d_row, d_col);
+  *launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute_factors(int32_t n, const int32_t* perm, const double* d, float* out,
+                                   int* range_flag, cudaStream_t s, int64_t* launches) {
+  k_permute_factors<<<grid_for(n), kT, 0, s>>>(n, perm, d, out, range_flag);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sell_scale32(const Sell& m, const float* d_rowpos, const float* d_colpos,
+                                float* val32, cudaStream_t s, int64_t* launches) {
+  k_sell_scale32<<<grid_for(32ll * m.n_slices), kT, 0, s>>>(m.n_rows, m.n_slices, m.wp, m.col,
+                                                             m.val, d_rowpos, d_colpos, val32);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(int64_t n, const float* in, double* out, cudaStream_t s,
+                           int64_t* launches) {
+  k_f32_to_f64<<<grid_for(n), kT, 0, s>>>(n, in, out);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(int64_t n, const double* in, float* out, cudaStream_t s,
+                           int64_t* launches) {
+  k_f64_to_f32<<<grid_for(n), kT, 0, s>>>(n, in, out);
+  ++*launches;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_dependencies(const int32_t* wp, const int32_t* col, const double* val,
                                 const int32_t* part_a, const int32_t* part_t, int G,
@@ -603,10 +724,14 @@ int sigma_blocks(int32_t n_slices, int32_t n_cols) {
 
 cudaError_t launch_sigma(const Sell& m, int32_t n_cols, const double* X0, const double* X1,
                          const double* X2, int use_minb, RunState* st, double* blockpart,
-                         cudaStream_t s, int64_t* launches) {
+                         bool dd, cudaStream_t s, int64_t* launches) {
   const int nb = sigma_blocks(m.n_slices, n_cols);
-  k_sigma_part<<<nb, kT, 0, s>>>(m.n_rows, m.n_slices, n_cols, m.wp, m.col, m.val, X0, X1, X2,
-                                 use_minb, st, blockpart);
+  if (dd)
+    k_sigma_part<true><<<nb, kT, 0, s>>>(m.n_rows, m.n_slices, n_cols, m.wp, m.col, m.val, X0,
+                                         X1, X2, use_minb, st, blockpart);
+  else
+    k_sigma_part<false><<<nb, kT, 0, s>>>(m.n_rows, m.n_slices, n_cols, m.wp, m.col, m.val, X0,
+                                          X1, X2, use_minb, st, blockpart);
   k_sigma_final<<<1, 32, 0, s>>>(blockpart, nb, st);
   *launches += 2;
   return cudaGetLastError();
