@@ -151,6 +151,12 @@ pa_status pa_estimate_batched(int n_mat, const pa_handle* handles, pa_mode mode,
                               const int* iters, double lr, double beta1, double beta2, double eps,
                               uint64_t seed, double* out, pa_status* item_status);
 
+/* 1 when the calling thread's latest pa_estimate_batched ran as one CUDA
+ * graph (start vectors, resets, the persistent launches and the sigma
+ * kernels captured and replayed), 0 when the driver refused the capture and
+ * the same sequence ran as ordinary launches. */
+int pa_last_batch_graph(void);
+
 /* x_min of the latest run of `which` (PA_SIGMA_MAX or PA_SIGMA_MIN) into the
  * host array x_min_host[n_cols] (Algorithm 1's output). */
 pa_status pa_get_vector(pa_handle h, pa_mode which, double* x_min_host);

@@ -872,12 +872,299 @@ extern "C" pa_status pa_get_equilibration(pa_handle h, double* d_row, double* d_
   return PA_OK;
 }
 
+// ------------------------------------------------------------ batched --
+
+namespace {
+
+// Device memory of one batched call, allocated through the first handle and
+// released at the end of the call.
+struct BatchScratch {
+  pa_ctx* h;
+  std::vector<void*> ptrs;
+  template <class T>
+  pa_status get(T** out, size_t count, const char* what) {
+    pa_status st = alloc_n(h, out, count, what);
+    if (st == PA_OK) ptrs.push_back((void*)*out);
+    return st;
+  }
+  ~BatchScratch() {
+    for (void* p : ptrs) dev_free(h, p);
+  }
+};
+
+// CTAs per item: at least one each, the rest proportional to the work.
+std::vector<int> share_ctas(const std::vector<double>& work, int G) {
+  const int n = (int)work.size();
+  std::vector<int> c(n, 1);
+  double tot = 0;
+  for (double w : work) tot += w;
+  int left = G - n;
+  if (left <= 0 || tot <= 0) return c;
+  std::vector<std::pair<double, int>> rem;
+  int used = 0;
+  for (int i = 0; i < n; ++i) {
+    const double want = left * work[i] / tot;
+    const int f = (int)floor(want);
+    c[i] += f;
+    used += f;
+    rem.push_back({want - f, i});
+  }
+  std::sort(rem.begin(), rem.end(), [](auto& a, auto& b) { return a.first > b.first || (a.first == b.first && a.second < b.second); });
+  for (int k = 0; k < left - used && k < n; ++k) c[rem[k].second] += 1;
+  return c;
+}
+
+}  // namespace
+
+// One wave of items [i0, i0 + m), restarts [r0, r0 + k_used) as K columns.
+static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_used, int K,
+                              int k_restarts, pa_mode mode, const int* iters, double lr, double b1,
+                              double b2, double eps, uint64_t seed, double* out,
+                              pa_status* item_status, bool* captured) {
+  pa_ctx* h0 = hs[0];
+  cudaStream_t s = h0->stream;  // replaced below by a capturable stream joined to it
+  BatchScratch sc{h0, {}};
+  const int Gmax = batched_max_blocks(K);
+  if (Gmax < m) return fail(PA_ERR_LAUNCH, "batched kernel: %d items exceed %d co-resident CTAs", m, Gmax);
+  // ---- CTA groups, sized by padded entries plus a per-row weight
+  std::vector<double> work(m);
+  for (int i = 0; i < m; ++i) {
+    const pa_ctx* hi = hs[i0 + i];
+    work[i] = (double)hi->a_entries + (double)hi->t_entries + 40.0 * std::max(hi->n_rows, hi->n_cols);
+  }
+  const std::vector<int> ncta = share_ctas(work, Gmax);
+  int G = 0;
+  for (int c : ncta) G += c;
+  std::vector<BatchItem> items(m);
+  std::vector<int32_t> cta_item(G);
+  std::vector<int32_t> blk_item, blk_row0, item_blk0(m + 1);
+  pa_status st;
+  cudaError_t e = cudaSuccess;
+  int cta = 0;
+  for (int i = 0; i < m; ++i) {
+    pa_ctx* hi = hs[i0 + i];
+    BatchItem& it = items[i];
+    const size_t nx = (size_t)hi->n_cols * K, ny = (size_t)hi->n_rows * K;
+    it.n_rows = hi->n_rows;
+    it.n_cols = hi->n_cols;
+    it.a_wp = hi->sa.wp; it.a_col = hi->sa.col; it.a_val = hi->sa.val;
+    it.t_wp = hi->sq.wp; it.t_col = hi->sq.col; it.t_val = hi->sq.val;
+    it.pos_c = hi->sq.pos;
+    it.n_slices_a = hi->sa.n_slices;
+    it.cta0 = cta;
+    it.ncta = ncta[i];
+    for (int c = 0; c < ncta[i]; ++c) cta_item[cta + c] = i;
+    cta += ncta[i];
+    int32_t *pa_ = nullptr, *pt_ = nullptr;
+    if ((st = sc.get(&pa_, (size_t)ncta[i] + 1, "batch partition")) ||
+        (st = sc.get(&pt_, (size_t)ncta[i] + 1, "batch partition")) ||
+        (st = sc.get(&it.partials, (size_t)ncta[i] * 4 * K, "batch partials")) ||
+        (st = sc.get(&it.barrier, 1, "batch barrier")) ||
+        (st = sc.get(&it.X0, nx, "batch x")) || (st = sc.get(&it.X1, nx, "batch x")) ||
+        (st = sc.get(&it.XMIN, nx, "batch x_min")) || (st = sc.get(&it.M, nx, "batch m")) ||
+        (st = sc.get(&it.V, nx, "batch v")) || (st = sc.get(&it.DX, nx, "batch dx")) ||
+        (st = sc.get(&it.Y, std::max<size_t>(ny, 1), "batch y")) ||
+        (st = sc.get(&it.result, (size_t)4 * K, "batch result")) ||
+        (st = sc.get(&it.status, 1, "batch status")))
+      return st;
+    if ((e = launch_partition(hi->sa.wp, hi->sa.n_slices, ncta[i], 2, pa_, s, &h0->launches)) ||
+        (e = launch_partition(hi->sq.wp, hi->sq.n_slices, ncta[i], 30, pt_, s, &h0->launches)))
+      return cuda_fail(e, "partitioning a batch item");
+    it.part_a = pa_;
+    it.part_t = pt_;
+    // blocks of 256 rows over max(n_rows, n_cols) for the start and sigma kernels
+    item_blk0[i] = (int32_t)blk_item.size();
+    const int rows = std::max(hi->n_rows, hi->n_cols);
+    for (int r = 0; r < rows; r += 256) {
+      blk_item.push_back(i);
+      blk_row0.push_back(r);
+    }
+  }
+  item_blk0[m] = (int32_t)blk_item.size();
+  const int nb = (int)blk_item.size();
+  BatchItem* items_d = nullptr;
+  int32_t *cta_item_d = nullptr, *blk_item_d = nullptr, *blk_row0_d = nullptr, *item_blk0_d = nullptr;
+  double *blockpart = nullptr, *sig = nullptr;
+  RunState* rs_d = nullptr;
+  if ((st = sc.get(&items_d, (size_t)m, "batch items")) ||
+      (st = sc.get(&cta_item_d, (size_t)G, "batch table")) ||
+      (st = sc.get(&blk_item_d, (size_t)nb, "batch table")) ||
+      (st = sc.get(&blk_row0_d, (size_t)nb, "batch table")) ||
+      (st = sc.get(&item_blk0_d, (size_t)m + 1, "batch table")) ||
+      (st = sc.get(&blockpart, (size_t)nb * 2 * K + (size_t)m * K + 64, "batch block partials")) ||
+      (st = sc.get(&sig, (size_t)2 * m * K, "batch sigma")) ||
+      (st = sc.get(&rs_d, 1, "batch run state")))
+    return st;
+  const int T = std::max(iters[0], iters[1]);
+  std::vector<double2> tab((size_t)std::max(T, 1));
+  for (int t = 1; t <= T; ++t) {
+    const double r2 = sqrt(1.0 - pow(b2, (double)t));
+    tab[t - 1] = make_double2(lr * r2 / (1.0 - pow(b1, (double)t)), eps * r2);
+  }
+  double2* bias_d = nullptr;
+  if ((st = sc.get(&bias_d, tab.size(), "batch bias table"))) return st;
+  // tables to the device (pageable host memory: synchronous copies, before capture)
+  if ((e = cudaMemcpyAsync(items_d, items.data(), sizeof(BatchItem) * m, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(cta_item_d, cta_item.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(blk_item_d, blk_item.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(blk_row0_d, blk_row0.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(item_blk0_d, item_blk0.data(), sizeof(int32_t) * (m + 1), cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(bias_d, tab.data(), sizeof(double2) * tab.size(), cudaMemcpyHostToDevice, s)) ||
+      (e = cudaStreamSynchronize(s)))
+    return cuda_fail(e, "uploading the batch tables");
+
+  BatchParams bp{};
+  bp.items = items_d;
+  bp.cta_item = cta_item_d;
+  bp.bias = bias_d;
+  bp.st = rs_d;
+  bp.loss = h0->opt.loss;
+  bp.ablation = h0->opt.ablation;
+  bp.beta1 = b1;
+  bp.beta2 = b2;
+  bp.timeout_ns = h0->opt.barrier_timeout_ns;
+
+  // The whole call as one sequence: start vectors, state reset, the
+  // persistent launch, sigma -- for sigma_max, then sigma_min.
+  auto enqueue = [&](bool count) -> cudaError_t {
+    int64_t dummy = 0;
+    int64_t* L = count ? &h0->launches : &dummy;
+    cudaError_t err = cudaSuccess;
+    for (int md : {PA_SIGMA_MAX, PA_SIGMA_MIN}) {
+      if (!(mode & md)) continue;
+      // item i, restart r: SplitMix64 output i * k_restarts + r of `seed`
+      err = launch_batch_start(items_d, m, K, k_used, k_restarts, i0, r0, seed, blk_item_d,
+                               blk_row0_d, nb, 256, blockpart, item_blk0_d, s, L);
+      if (err) return err;
+      if ((err = cudaMemsetAsync(rs_d, 0, sizeof(RunState), s))) return err;
+      for (int i = 0; i < m; ++i) {
+        const size_t nx = (size_t)items[i].n_cols * K;
+        if ((err = cudaMemsetAsync(items[i].M, 0, sizeof(double) * nx, s)) ||
+            (err = cudaMemsetAsync(items[i].V, 0, sizeof(double) * nx, s)) ||
+            (err = cudaMemsetAsync(items[i].barrier, 0, sizeof(unsigned), s)) ||
+            (err = cudaMemsetAsync(items[i].status, 0, sizeof(int), s)))
+          return err;
+      }
+      BatchParams q = bp;
+      q.mode = md;
+      q.iters = md == PA_SIGMA_MAX ? iters[0] : iters[1];
+      if ((err = launch_batched(q, K, G, s, L))) return err;
+      if ((err = launch_batch_sigma(items_d, m, K, blk_item_d, blk_row0_d, nb, 256, blockpart,
+                                    item_blk0_d, sig + (md == PA_SIGMA_MAX ? 0 : (size_t)m * K), s, L)))
+        return err;
+    }
+    return cudaSuccess;
+  };
+  // Capture the sequence into a CUDA graph on a library-owned stream that
+  // joins the handle's stream (the legacy default stream cannot be
+  // captured); if capture or instantiation is refused, run the same sequence
+  // on that stream directly.
+  const cudaStream_t user = s;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev = nullptr;
+  if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) ||
+      (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) ||
+      (e = cudaEventRecord(ev, user)) || (e = cudaStreamWaitEvent(cs, ev, 0))) {
+    if (cs) cudaStreamDestroy(cs);
+    if (ev) cudaEventDestroy(ev);
+    return cuda_fail(e, "preparing the batch stream");
+  }
+  s = cs;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  *captured = false;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    const cudaError_t ce = enqueue(false);
+    const cudaError_t ee = cudaStreamEndCapture(s, &graph);
+    if (ce == cudaSuccess && ee == cudaSuccess && graph &&
+        cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess)
+      *captured = true;
+    cudaGetLastError();  // a refused capture leaves a sticky-free error here
+  }
+  if (*captured) {
+    e = cudaGraphLaunch(exec, s);
+    h0->launches += (int64_t)((mode & PA_SIGMA_MAX ? 1 : 0) + (mode & PA_SIGMA_MIN ? 1 : 0)) * 6;
+  } else {
+    e = enqueue(true);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  cudaEventRecord(ev, s);
+  cudaStreamWaitEvent(user, ev, 0);
+  cudaStreamSynchronize(s);
+  cudaEventDestroy(ev);
+  cudaStreamDestroy(cs);
+  s = user;
+  if (e != cudaSuccess) return cuda_fail(e, "running the batched launch");
+  // ---- results
+  std::vector<double> sg((size_t)2 * m * K);
+  RunState rs{};
+  if ((e = cudaMemcpyAsync(sg.data(), sig, sizeof(double) * sg.size(), cudaMemcpyDeviceToHost, s)) ||
+      (e = cudaMemcpyAsync(&rs, rs_d, sizeof(RunState), cudaMemcpyDeviceToHost, s)) ||
+      (e = cudaStreamSynchronize(s)))
+    return cuda_fail(e, "reading the batched results");
+  std::vector<int> ist(m, PA_OK);
+  for (int i = 0; i < m; ++i) {
+    int v = 0;
+    if ((e = cudaMemcpy(&v, items[i].status, sizeof(int), cudaMemcpyDeviceToHost)))
+      return cuda_fail(e, "reading the batched status");
+    ist[i] = v;
+  }
+  if (rs.abort) return fail(PA_ERR_TIMEOUT, "a batched group barrier wait ran out of time");
+  for (int i = 0; i < m; ++i) {
+    for (int c = 0; c < k_used; ++c) {
+      const int r = r0 + c;
+      double* o = out + ((size_t)(i0 + i) * k_restarts + r) * 3;
+      const double smax = (mode & PA_SIGMA_MAX) ? sg[(size_t)i * K + c] : NAN;
+      const double smin = (mode & PA_SIGMA_MIN) ? sg[(size_t)m * K + (size_t)i * K + c] : NAN;
+      o[0] = smax;
+      o[1] = smin;
+      o[2] = (mode == PA_BOTH) ? (smin > 0 ? smax / smin : INFINITY) : NAN;
+      if (item_status) item_status[(size_t)(i0 + i) * k_restarts + r] = (pa_status)ist[i];
+    }
+  }
+  return PA_OK;
+}
+
+static thread_local int g_last_batch_graph = 0;
+extern "C" int pa_last_batch_graph(void) { return g_last_batch_graph; }
+
 extern "C" pa_status pa_estimate_batched(int n_mat, const pa_handle* handles, pa_mode mode,
                                          int k_restarts, const int* iters, double lr, double beta1,
                                          double beta2, double eps, uint64_t seed, double* out,
                                          pa_status* item_status) {
   g_err.clear();
-  (void)n_mat; (void)handles; (void)mode; (void)k_restarts; (void)iters; (void)lr;
-  (void)beta1; (void)beta2; (void)eps; (void)seed; (void)out; (void)item_status;
-  return fail(PA_ERR_UNSUPPORTED, "batched estimates are not available in this build");
+  if (n_mat <= 0 || !handles || !iters || !out || k_restarts <= 0)
+    return fail(PA_ERR_INVALID_ARG, "invalid batched arguments");
+  if (mode != PA_SIGMA_MAX && mode != PA_SIGMA_MIN && mode != PA_BOTH)
+    return fail(PA_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
+  pa_status st;
+  if ((st = check_hyper(std::min(iters[0], iters[1]), lr, beta1, beta2, eps))) return st;
+  for (int i = 0; i < n_mat; ++i) {
+    const pa_ctx* hi = handles[i];
+    if (!hi) return fail(PA_ERR_INVALID_ARG, "handle %d is NULL", i);
+    if (hi->stream != handles[0]->stream)
+      return fail(PA_ERR_INVALID_ARG, "all handles of a batch must share one stream");
+    if (hi->opt.precision != PA_FP64)
+      return fail(PA_ERR_UNSUPPORTED, "batched estimates run in FP64 only (handle %d)", i);
+    if ((mode & PA_SIGMA_MIN) && hi->n_rows < hi->n_cols)
+      return fail(PA_ERR_NOT_SQUARE, "sigma_min needs n_rows >= n_cols (handle %d)", i);
+  }
+  bool captured = false;
+  for (int r0 = 0; r0 < k_restarts; r0 += 8) {
+    const int k_used = std::min(8, k_restarts - r0);
+    const int K = k_used <= 1 ? 1 : (k_used <= 2 ? 2 : (k_used <= 4 ? 4 : 8));
+    const int Gmax = batched_max_blocks(K);
+    if (Gmax <= 0) return fail(PA_ERR_LAUNCH, "the batched kernel does not fit on this GPU");
+    const int wave = std::max(1, Gmax / 2);
+    for (int i0 = 0; i0 < n_mat; i0 += wave) {
+      const int m = std::min(wave, n_mat - i0);
+      if ((st = batched_wave(handles, i0, m, r0, k_used, K, k_restarts, mode, iters, lr, beta1,
+                             beta2, eps, seed, out, item_status, &captured)))
+        return st;
+      g_last_batch_graph = captured ? 1 : 0;
+    }
+  }
+  return PA_OK;
 }

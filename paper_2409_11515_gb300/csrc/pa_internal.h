@@ -99,6 +99,52 @@ struct IterParams32 {
   int skip_arrival;
 };
 
+// One matrix of a batched launch: its sliced copies, its group of CTAs and
+// its n x K (row-major) blocks of vectors.
+struct BatchItem {
+  int32_t n_rows, n_cols;
+  const int32_t* a_wp; const int32_t* a_col; const double* a_val;
+  const int32_t* t_wp; const int32_t* t_col; const double* t_val;
+  int cta0, ncta;                       // CTAs [cta0, cta0 + ncta) of the grid
+  const int32_t* part_a; const int32_t* part_t;  // [ncta + 1] slice ranges
+  double* partials;                     // [ncta][4][K]
+  unsigned* barrier;                    // the group's arrival counter
+  double *X0, *X1, *XMIN, *M, *V, *DX, *Y;
+  double* result;                       // [K][4]: L_min, t_min, L_last, iterations
+  int* status;                          // [1]
+  const int32_t* pos_c;                 // source column -> x position (Q)
+  int32_t n_slices_a;                   // slices of P A Q^T
+};
+
+struct BatchParams {
+  const BatchItem* items;
+  const int32_t* cta_item;   // [G] item of each CTA
+  const double2* bias;       // [iters] as in IterParams
+  RunState* st;              // shared abort flag
+  int iters, mode, loss, ablation;
+  double beta1, beta2;
+  long long timeout_ns;
+};
+
+int batched_threads();
+int batched_max_blocks(int k);
+cudaError_t launch_batched(const BatchParams& p, int k, int G, cudaStream_t s, int64_t* launches);
+
+// Start vectors of a batch: column c of item i is the SplitMix64 stream of
+// seed splitmix64_at(seed, (i0 + i) * k_stride + r0 + c), normalised per
+// column (columns >= k_used repeat column 0).  blk_item/blk_row0 describe
+// the blocks ([nb] each, rows [row0, row0 + rows)).
+cudaError_t launch_batch_start(const BatchItem* items_dev, int n_items, int K, int k_used,
+                               int k_stride, int i0, int r0, uint64_t seed, const int32_t* blk_item,
+                               const int32_t* blk_row0, int nb, int rows_per_block,
+                               double* blockpart, const int32_t* item_blk0, cudaStream_t s,
+                               int64_t* launches);
+// sigma per (item, column) of XMIN: out[(i * K + c)] for c < K.
+cudaError_t launch_batch_sigma(const BatchItem* items_dev, int n_items, int K,
+                               const int32_t* blk_item, const int32_t* blk_row0, int nb,
+                               int rows_per_block, double* blockpart, const int32_t* item_blk0,
+                               double* out, cudaStream_t s, int64_t* launches);
+
 // Record a message for pa_last_error() (printf-style) and return st.
 pa_status set_error(pa_status st, const char* fmt, ...);
 

@@ -38,7 +38,7 @@ STATUS_NAMES = {0: "PA_OK", 1: "PA_WARN_SINGULAR", -1: "PA_ERR_INVALID_ARG",
 EXPORTS = ("pa_options_default", "pa_create", "pa_estimate", "pa_run", "pa_estimate_batched",
            "pa_get_vector", "pa_spmv", "pa_spmv_t", "pa_get_transpose", "pa_get_equilibration",
            "pa_kernel_launches", "pa_destroy", "pa_last_error", "pa_set_allocator",
-           "pa_last_run_profile", "pa_sigma_noalloc")
+           "pa_last_run_profile", "pa_sigma_noalloc", "pa_last_batch_graph")
 
 
 class LibraryMissing(RuntimeError):
@@ -108,6 +108,8 @@ def _declare(L):
     L.pa_get_equilibration.argtypes = [vp, vp, vp]
     L.pa_last_run_profile.restype = C.c_int
     L.pa_last_run_profile.argtypes = [vp, C.POINTER(C.c_int), vp]
+    L.pa_last_batch_graph.restype = C.c_int
+    L.pa_last_batch_graph.argtypes = []
     L.pa_sigma_noalloc.restype = C.c_int
     L.pa_sigma_noalloc.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp]
     L.pa_kernel_launches.restype = i64
@@ -325,7 +327,8 @@ def estimate_batched(handles, mode=BOTH, k_restarts=8, iters=(2000, 2000), lr=1e
     st = _check(load().pa_estimate_batched(n, arr, mode, k_restarts, it, lr, beta1, beta2, eps,
                                            seed & (2**64 - 1), out.ctypes.data, stat.ctypes.data))
     return {"status": st, "sigma_max": out[:, :, 0], "sigma_min": out[:, :, 1],
-            "kappa": out[:, :, 2], "item_status": stat}
+            "kappa": out[:, :, 2], "item_status": stat,
+            "cuda_graph": bool(load().pa_last_batch_graph())}
 
 
 def sigma_noalloc(row_ptr, col, val, x, out, n_rows: int, n_cols: int, stream=None) -> int:

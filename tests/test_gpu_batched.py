@@ -1,0 +1,93 @@
+"""pa_estimate_batched: many matrices x k restarts in one persistent launch.
+
+Item (i, r) is Algorithm 1 on matrix i from the start vector of seed
+SplitMix64 output (i * k + r) of the call's seed; its sigma_max must match
+the oracle's run from the same start vector (sigma_max converges: 1e-9),
+and kappa must reach the closed form on the closed-form matrices (1e-6).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2409_11515_gb300 import build, pa, synth
+
+pytestmark = pytest.mark.gpu
+HYPER = dict(lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-12)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    pa.load()
+
+
+def _x0(n, seed, i, k, r):
+    return oracle.start_vector(n, oracle.splitmix64_at(seed, i * k + r))
+
+
+@pytest.mark.parametrize("k", [1, 3, 8, 10])
+def test_batched_sigma_max_matches_oracle(k):
+    mats = [synth.hydro_operator(9, seed=1), synth.laplacian_2d(7), synth.hydro_operator(13, 11, seed=2),
+            synth.random_sparse(500, 5, seed=3, diag_boost=2.0)]
+    hs = [pa.create(A) for A in mats]
+    try:
+        T = 1500
+        r = pa.estimate_batched(hs, pa.SIGMA_MAX, k, (T, T), seed=9, **HYPER)
+    finally:
+        for h in hs:
+            h.destroy()
+    assert np.all(r["item_status"] == 0)
+    assert r["cuda_graph"]
+    for i, A in enumerate(mats):
+        for rr in range(k):
+            ro = oracle.projected_adam(A, oracle.SIGMA_MAX, T, x_init=_x0(A.n_cols, 9, i, k, rr),
+                                       **HYPER)
+            assert abs(r["sigma_max"][i, rr] / ro.sigma - 1) <= 1e-9, (i, rr)
+    assert np.all(np.isnan(r["sigma_min"]))
+
+
+def test_batched_kappa_closed_forms_and_single_path():
+    mats = [synth.laplacian_1d(8), synth.laplacian_2d(4), synth.diag_csr([3.0, -0.5, 2.0, 1.5])]
+    kappas = [1 / math.tan(math.pi / 18) ** 2, 1 / math.tan(math.pi / 10) ** 2, 6.0]
+    hs = [pa.create(A) for A in mats]
+    try:
+        r = pa.estimate_batched(hs, pa.BOTH, 4, (3000, 3000), seed=2, **HYPER)
+        # the batched item equals the single-vector run from the same start vector
+        x0 = _x0(mats[1].n_cols, 2, 1, 4, 3)
+        single = hs[1].run(pa.SIGMA_MAX, 3000, x0, **HYPER)
+    finally:
+        for h in hs:
+            h.destroy()
+    for i, kap in enumerate(kappas):
+        assert np.all(np.abs(r["kappa"][i] / kap - 1) <= 1e-6), (i, r["kappa"][i], kap)
+    assert abs(r["sigma_max"][1, 3] / single["sigma"] - 1) <= 1e-12
+
+
+def test_batched_uneven_sizes_deterministic():
+    mats = [synth.hydro_operator(n, seed=n) for n in (5, 23, 41, 7, 31)]
+    hs = [pa.create(A) for A in mats]
+    try:
+        r1 = pa.estimate_batched(hs, pa.BOTH, 2, (400, 400), seed=5, **HYPER)
+        r2 = pa.estimate_batched(hs, pa.BOTH, 2, (400, 400), seed=5, **HYPER)
+    finally:
+        for h in hs:
+            h.destroy()
+    assert np.array_equal(r1["sigma_max"], r2["sigma_max"])
+    assert np.array_equal(r1["sigma_min"], r2["sigma_min"])
+    assert np.all(r1["sigma_min"] <= r1["sigma_max"])
+    for i, A in enumerate(mats):  # sigma_max after 400 iterations: within 1e-6 of the oracle
+        ro = oracle.projected_adam(A, oracle.SIGMA_MAX, 400, x_init=_x0(A.n_cols, 5, i, 2, 0), **HYPER)
+        assert abs(r1["sigma_max"][i, 0] / ro.sigma - 1) <= 1e-6
+
+
+def test_batched_errors():
+    with pa.create(synth.random_sparse(30, 3, seed=1, n_cols=40)) as h:
+        with pytest.raises(pa.PAError) as ei:
+            pa.estimate_batched([h], pa.SIGMA_MIN, 2, (10, 10))
+        assert ei.value.status == -3
+    with pa.create(synth.laplacian_1d(8), precision=pa.MIXED) as h:
+        with pytest.raises(pa.PAError) as ei:
+            pa.estimate_batched([h], pa.SIGMA_MAX, 2, (10, 10))
+        assert ei.value.status == -9
