@@ -79,12 +79,17 @@ typedef struct {
    * for its final sigma. */
   int precision;
   int equilibrate;  /* PA_EQ_STORAGE: keep D_r^-1 A D_c^-1 with pow2 D (implied by MIXED) */
-  int engine;       /* AUTO picks CLUSTER for small matrices, else GRID     */
+  int engine;       /* GRID: cooperative grid with timed software barriers;
+                       CLUSTER: one thread-block cluster (<= 16 CTAs) with
+                       the hardware cluster barrier (plain FP64 only);
+                       AUTO: CLUSTER when the grid would use <= 16 CTAs    */
   int ablation;     /* PA_ABLATE_* bits: drop the tangent projection and/or
                        the normalisation of Algorithm 1 (the paper's vanilla
                        Adam comparison); 0 = Algorithm 1 as printed        */
   int64_t barrier_timeout_ns; /* device wait limit per barrier; <= 0 -> 2 s */
-  int grid_blocks;  /* 0 = fill the GPU; > 0 caps the persistent grid      */
+  int grid_blocks;  /* CTAs of the persistent grid: 0 = chosen from the size
+                       (about four rows per thread, at most the GPU), > 0 =
+                       that many (at most the GPU and the slice count)     */
   int debug_skip_arrival; /* test hook: > 0 makes CTA 0 skip the barrier of
                              that iteration, so the others time out (0 = off) */
   int fp64_tail;    /* MIXED sigma_max: the last iterations, run in FP64 from

@@ -407,11 +407,11 @@ static int choose_grid(pa_ctx* h, int* maxG_out) {
   if (maxG_out) *maxG_out = maxG;
   if (maxG <= 0) return -1;
   const int64_t n = std::max(h->n_rows, h->n_cols);
+  const int64_t slices = std::max<int64_t>(1, std::min(h->sa.n_slices, h->sq.n_slices));
   int64_t want = (n + 2047) / 2048;  // about four rows per thread
-  if (want < 1) want = 1;
-  int G = (int)std::min<int64_t>(want, maxG);
-  if (h->opt.grid_blocks > 0) G = std::min(G, h->opt.grid_blocks);
-  return G;
+  if (h->opt.grid_blocks > 0) want = h->opt.grid_blocks;  // an explicit request
+  want = std::max<int64_t>(1, std::min(want, slices));
+  return (int)std::min<int64_t>(want, maxG);
 }
 
 static pa_status ensure_partitions(pa_ctx* h, int G) {
@@ -494,7 +494,7 @@ static pa_status status_error(const RunState* rs) {
 // from.  Then sigma of the tracked minimiser; the run state comes back in *out.
 static pa_status fp64_run(pa_ctx* h, pa_mode mode, int iters, int t0, bool fresh_state, bool dd,
                           double b1, double b2, double eps, int G, int maxG, double* L_trace_dev,
-                          double* x_trace_dev, int n_trace, RunState* out) {
+                          double* x_trace_dev, int n_trace, RunState* out, bool cluster = false) {
   const size_t n = (size_t)h->n_cols;
   cudaError_t e = cudaSuccess;
   if (fresh_state &&
@@ -530,7 +530,8 @@ static pa_status fp64_run(pa_ctx* h, pa_mode mode, int iters, int t0, bool fresh
   p.beta1 = b1; p.beta2 = b2; p.eps = eps;
   p.timeout_ns = h->opt.barrier_timeout_ns;
   p.skip_arrival = h->opt.debug_skip_arrival;
-  e = launch_persistent(p, h->opt.loss, dd, G, h->stream, &h->launches);
+  e = cluster ? launch_persistent_cluster(p, h->opt.loss, G, h->stream, &h->launches)
+              : launch_persistent(p, h->opt.loss, dd, G, h->stream, &h->launches);
   if (e == cudaErrorCooperativeLaunchTooLarge)
     return fail(PA_ERR_LAUNCH, "cooperative grid of %d CTAs does not fit (max %d)", G, maxG);
   if (e != cudaSuccess) return cuda_fail(e, "launching the persistent kernel");
@@ -647,15 +648,29 @@ static pa_status run_one(pa_ctx* h, pa_mode mode, int iters, double lr, double b
   if (mixed && mode == PA_SIGMA_MAX && x_trace_dev)
     return fail(PA_ERR_INVALID_ARG, "x traces are not available for the mixed-precision sigma_max");
   int maxG = 0;
-  const int G = choose_grid(h, &maxG);
+  int G = choose_grid(h, &maxG);
   if (G <= 0) return fail(PA_ERR_LAUNCH, "the persistent kernel does not fit on this GPU");
+  // the cluster engine: one thread-block cluster with hardware barriers, for
+  // plain FP64 runs of matrices that would use at most 16 CTAs anyway
+  bool cluster = false;
+  if (!mixed && h->opt.engine != PA_ENGINE_GRID && h->opt.debug_skip_arrival == 0 &&
+      (h->opt.engine == PA_ENGINE_CLUSTER || G <= 16)) {
+    const int cmax = persistent_cluster_max(h->opt.loss);
+    const int slices = std::max(1, std::min(h->sa.n_slices, h->sq.n_slices));
+    int Gc = std::min(std::min(cmax, 16), slices);
+    if (h->opt.grid_blocks > 0) Gc = std::min(Gc, h->opt.grid_blocks);
+    if (Gc >= 1) {
+      cluster = true;
+      G = Gc;
+    }
+  }
   pa_status st;
   if ((st = ensure_partitions(h, G)) || (st = ensure_bias(h, iters, lr, b1, b2, eps))) return st;
   if (mixed && mode == PA_SIGMA_MAX) {
     if ((st = mixed_max_run(h, iters, b1, b2, eps, G, maxG, L_trace_dev, out)) < 0) return st;
   } else {
     if ((st = fp64_run(h, mode, iters, 0, true, mixed, b1, b2, eps, G, maxG, L_trace_dev,
-                       x_trace_dev, n_trace, out)))
+                       x_trace_dev, n_trace, out, cluster)))
       return st;
     double* keep = mode == PA_SIGMA_MAX ? h->xmin_max : h->xmin_min;
     cudaError_t e = launch_unpermute(h->n_cols, 1, h->sq.pos, pick64h(h, out->minb), keep,

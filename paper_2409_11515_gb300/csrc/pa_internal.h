@@ -243,6 +243,11 @@ cudaError_t launch_convert(int64_t n, const double* in, float* out, cudaStream_t
 // Persistent cooperative Projected Adam run (Algorithm 1) over a grid of G
 // CTAs; dd selects compensated (double-double) products.
 int persistent_max_blocks(int loss, bool dd, int* blocks_per_sm);
+// The cluster variant: one thread-block cluster of G CTAs, synchronised by
+// the hardware cluster barrier (plain FP64 products).
+int persistent_cluster_max(int loss);
+cudaError_t launch_persistent_cluster(const IterParams& p, int loss, int G, cudaStream_t s,
+                                      int64_t* launches);
 cudaError_t launch_persistent(const IterParams& p, int loss, bool dd, int G, cudaStream_t s,
                               int64_t* launches);
 

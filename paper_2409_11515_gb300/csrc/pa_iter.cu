@@ -34,6 +34,8 @@
 // the kernel with PA_ERR_TIMEOUT instead of a hang.
 #include <math.h>
 
+#include <cooperative_groups.h>
+
 #include "pa_device.cuh"
 #include "pa_internal.h"
 
@@ -67,7 +69,10 @@ __device__ __forceinline__ double loss_value(int mode, int loss, double s, doubl
   return mode == PA_SIGMA_MAX ? lx - lax : lax - lx;
 }
 
-template <int LOSS, bool DD>
+// CL: the grid is one thread-block cluster (up to 16 CTAs) and every
+// grid-wide synchronisation is the hardware cluster barrier (release/acquire
+// at cluster scope), for matrices too small to fill the GPU.
+template <int LOSS, bool DD, bool CL>
 __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const IterParams p) {
   __shared__ Shared sh;
   constexpr int NW = kBlock / 32;
@@ -110,7 +115,10 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
 
   for (int t = 1;; ++t) {
     // x_{t-1} of the neighbours must be written before the gathers below
-    if (t > 1 && !wait_ready(st, p.ready, dlo, dhi, (unsigned)(t - 1), p.timeout_ns, site++, sh.ok)) {
+    if (CL) {
+      if (t > 1) cooperative_groups::this_cluster().sync();
+    } else if (t > 1 &&
+               !wait_ready(st, p.ready, dlo, dhi, (unsigned)(t - 1), p.timeout_ns, site++, sh.ok)) {
       status = PA_ERR_TIMEOUT;
       break;
     }
@@ -142,7 +150,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
       }
     }
     const bool skip = (p.skip_arrival == t) && (b == 0);
-    if (!grid_barrier(st, target, G, p.timeout_ns, skip, site++, sh.ok)) { status = PA_ERR_TIMEOUT; break; }
+    if (CL) cooperative_groups::this_cluster().sync();
+    else if (!grid_barrier(st, target, G, p.timeout_ns, skip, site++, sh.ok)) { status = PA_ERR_TIMEOUT; break; }
     if (tid < 32) {
       const double s_ = ordered_sum(part, G, kPartSlots, 0);
       const double q = ordered_sum(part, G, kPartSlots, 1);
@@ -223,7 +232,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
         sh.busy_b += (unsigned long long)(globaltimer_ns() - sh.tmark);
       }
     }
-    if (!grid_barrier(st, target, G, p.timeout_ns, false, site++, sh.ok)) { status = PA_ERR_TIMEOUT; break; }
+    if (CL) cooperative_groups::this_cluster().sync();
+    else if (!grid_barrier(st, target, G, p.timeout_ns, false, site++, sh.ok)) { status = PA_ERR_TIMEOUT; break; }
     if (tid < 32) {
       const double p1 = ordered_sum(part, G, kPartSlots, 2);
       const double p2 = ordered_sum(part, G, kPartSlots, 3);
@@ -295,12 +305,15 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
 
 }  // namespace
 
-static void* persistent_fn(int loss, bool dd) {
+static void* persistent_fn(int loss, bool dd, bool cl = false) {
+  if (cl)
+    return loss == PA_LOSS_QUADRATIC ? (void*)k_persistent<PA_LOSS_QUADRATIC, false, true>
+                                     : (void*)k_persistent<PA_LOSS_LOGRATIO, false, true>;
   if (loss == PA_LOSS_QUADRATIC)
-    return dd ? (void*)k_persistent<PA_LOSS_QUADRATIC, true>
-              : (void*)k_persistent<PA_LOSS_QUADRATIC, false>;
-  return dd ? (void*)k_persistent<PA_LOSS_LOGRATIO, true>
-            : (void*)k_persistent<PA_LOSS_LOGRATIO, false>;
+    return dd ? (void*)k_persistent<PA_LOSS_QUADRATIC, true, false>
+              : (void*)k_persistent<PA_LOSS_QUADRATIC, false, false>;
+  return dd ? (void*)k_persistent<PA_LOSS_LOGRATIO, true, false>
+            : (void*)k_persistent<PA_LOSS_LOGRATIO, false, false>;
 }
 
 int persistent_max_blocks(int loss, bool dd, int* blocks_per_sm) {
@@ -321,6 +334,52 @@ cudaError_t launch_persistent(const IterParams& p, int loss, bool dd, int G, cud
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kBlock), args, 0, s);
   ++*launches;
   return e;
+}
+
+// Largest cluster (<= 16 CTAs) of the cluster variant that the GPU can hold.
+int persistent_cluster_max(int loss) {
+  void* fn = persistent_fn(loss, false, true);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return 8;
+  }
+  for (int c = 16; c >= 1; c /= 2) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c);
+    cfg.blockDim = dim3(kBlock);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = c;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) == cudaSuccess && n >= 1) return c;
+    cudaGetLastError();
+  }
+  return 1;
+}
+
+cudaError_t launch_persistent_cluster(const IterParams& p, int loss, int G, cudaStream_t s,
+                                      int64_t* launches) {
+  void* fn = persistent_fn(loss, false, true);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(G);
+  cfg.blockDim = dim3(kBlock);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = G;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  void* args[] = {(void*)&p};
+  ++*launches;
+  return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 }  // namespace pa

@@ -94,20 +94,22 @@ def _iterate_parity(A, mode, loss=pa.LOSS_LOGRATIO, T=100, seed=7, **opt):
     return rg, ro, err_x, err_L
 
 
+@pytest.mark.parametrize("engine", [pa.ENGINE_GRID, pa.ENGINE_CLUSTER])
 @pytest.mark.parametrize("name", ["hydro21", "hydro13_8incl", "lap2d_12", "random_sparse",
                                   "rect_tall"])
-def test_first_100_iterates_sigma_max(name):
+def test_first_100_iterates_sigma_max(name, engine):
     A = CASES[name]()
-    rg, ro, err_x, err_L = _iterate_parity(A, pa.SIGMA_MAX)
+    rg, ro, err_x, err_L = _iterate_parity(A, pa.SIGMA_MAX, engine=engine)
     assert np.max(err_x) <= 1e-10, (np.argmax(err_x), np.max(err_x))
     assert np.max(err_L) <= 1e-10
     assert rg["t_min"] == ro.t_min
     assert abs(rg["sigma"] / ro.sigma - 1) <= 1e-10
 
 
+@pytest.mark.parametrize("engine", [pa.ENGINE_GRID, pa.ENGINE_CLUSTER])
 @pytest.mark.parametrize("name", ["hydro21", "hydro13_8incl", "lap2d_12", "random_sparse",
                                   "rect_tall"])
-def test_first_100_iterates_sigma_min(name, tmp_path):
+def test_first_100_iterates_sigma_min(name, engine, tmp_path):
     """sigma_min iterates amplify round-off: the oracle disagrees with its own
     FMA-contracted build by up to 1e-2 within 100 iterations on the hydro
     operators.  The bar is therefore 1e-10 for every t at which the oracle's
@@ -118,7 +120,7 @@ def test_first_100_iterates_sigma_min(name, tmp_path):
     x0 = oracle.start_vector(A.n_cols, 7)
     ref, runs = oracle.rounding_ensemble(A, oracle.SIGMA_MIN, T, x0, tmp_path, **HYPER)
     spread = np.max([np.linalg.norm(r.x_trace - ref.x_trace, axis=1) for r in runs], axis=0)
-    with pa.create(A) as h:
+    with pa.create(A, engine=engine) as h:
         rg = h.run(pa.SIGMA_MIN, T, x0, trace_L=True, n_trace=T, **HYPER)
     err = np.linalg.norm(rg["x_trace"] - ref.x_trace, axis=1)
     quiet = spread <= 1e-12
