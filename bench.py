@@ -115,13 +115,21 @@ def _barrier(ws):
 
 
 def _max_over_ranks(x, ws):
+    """The slowest rank's time: every rank gets the maximum of x."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_value(units_per_rank, seconds, ws):
+    """Whole-job throughput of ws independent replicas: all ranks' units over
+    the slowest rank's time."""
+    return ws * units_per_rank / seconds
 
 
 def flops_per_iteration(n_rows, n_cols, nnz):
@@ -235,7 +243,7 @@ def run_ours(args):
                              eta_lo=WORKLOAD["eta_lo"], eta_hi=WORKLOAD["eta_hi"],
                              seed=WORKLOAD["seed"])
     stream = torch.cuda.Stream()
-    h = pa.create(A, stream=stream)
+    h = pa.create(A, stream=stream, autotune=args.autotune)
     it_per_step = ITERS_MAX + ITERS_MIN
 
     def step(handle):
@@ -262,7 +270,7 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     ms = _max_over_ranks(ms, ws)
     launches = h.launches() - launches0
-    value = ws * it_per_step * args.steps / (ms / 1e3)
+    value = whole_job_value(it_per_step * args.steps, ms / 1e3, ws)
     # ---- roofline of the persistent kernel: per-launch time on its own stream
     kms = []
     r_fp64 = None
@@ -320,7 +328,7 @@ def run_ours(args):
     _barrier(ws)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        with pa.create(A, stream=stream) as he:
+        with pa.create(A, stream=stream, autotune=args.autotune) as he:
             he.estimate(pa.SIGMA_MAX, ITERS_MAX, seed=START_SEED, **HYPER)
             re = he.estimate(pa.SIGMA_MIN, ITERS_MIN, seed=START_SEED, **HYPER)
     torch.cuda.synchronize()
@@ -334,7 +342,9 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded hydro-mechanical operator generator)",
-            "config": dict(_config(A), parallelism=f"replicas{ws}" if ws > 1 else "single_gpu"),
+            "config": dict(_config(A), parallelism=f"replicas{ws}" if ws > 1 else "single_gpu",
+                           partition=(f"measured-cost tuner, {args.autotune} rounds in warm-up"
+                                      if args.autotune > 0 else "fixed cost model")),
             "kappa_estimates_per_s": ws * args.steps / (ms / 1e3),
             "result": {"sigma_max": r["sigma_max"], "sigma_min": r["sigma_min"],
                        "kappa": r["kappa"], "status": r["status"]},
@@ -352,7 +362,7 @@ def run_ours(args):
             "variants_same_workload": variants,
             "clocks": clocks,
             "gpu_launches": launches,
-            "e2e": {"value": ws * it_per_step * e2e_steps / e2e_s, "unit": UNIT,
+            "e2e": {"value": whole_job_value(it_per_step * e2e_steps, e2e_s, ws), "unit": UNIT,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         }
         if ws == 1 and not args.no_cpu_baseline:
@@ -369,6 +379,8 @@ def run_batched_workload(args):
     each, FP64: vector-iterations per second of pa_estimate_batched (one
     persistent launch per sigma mode, one CUDA graph) against the
     single-vector path looping over the same (matrix, restart) items."""
+    if _dist()[0] > 1:
+        raise SystemExit("the batched workload runs on one GPU (launch it without torchrun)")
     import torch
     from paper_2409_11515_gb300 import build, pa, synth
     build.build()
@@ -437,6 +449,9 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--autotune", type=int, default=3,
+                    help="partition-tuner rounds on the FP64 handle (0 = fixed cost model); "
+                         "they run in the warm-up steps")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")

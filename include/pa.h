@@ -95,6 +95,12 @@ typedef struct {
   int fp64_tail;    /* MIXED sigma_max: the last iterations, run in FP64 from
                        the FP32 state (x, m, v) near convergence; < 0 (default)
                        = iters / 10, 0 = none */
+  int autotune;     /* > 0: after each of the first `autotune` runs of the
+                       grid engine, re-split the slices among the CTAs at
+                       equal measured busy time (per-CTA timers of that run).
+                       The split sets the order of the reductions, so tuned
+                       runs are reproducible only for the same split; 0
+                       (default) keeps the fixed cost model. */
 } pa_options;
 
 /* Fill *opt with the defaults above (LOGRATIO, FP64, no equilibration, AUTO

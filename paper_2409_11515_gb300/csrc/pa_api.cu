@@ -99,6 +99,7 @@ struct pa_ctx {
   unsigned* ready = nullptr;
   unsigned long long* cta_ns = nullptr;  // [2G] per-CTA busy time of the last run
   int last_G = 0;
+  int tuned_rounds = 0;                  // partition re-splits done for h->G
   double2* bias = nullptr;
   int bias_cap = 0;
   bool have_max = false, have_min = false;
@@ -292,6 +293,7 @@ extern "C" pa_status pa_create(pa_handle* out, int32_t n_rows, int32_t n_cols, i
     return fail(PA_ERR_INVALID_ARG, "unknown equilibration mode %d", o.equilibrate);
   if (o.precision == PA_MIXED && o.loss != PA_LOSS_LOGRATIO)
     return fail(PA_ERR_UNSUPPORTED, "mixed precision supports the log-ratio loss only");
+  if (o.autotune < 0) return fail(PA_ERR_INVALID_ARG, "autotune must be >= 0 (got %d)", o.autotune);
   if (o.precision == PA_MIXED) o.equilibrate = PA_EQ_STORAGE;
 
   pa_ctx* h = new pa_ctx();
@@ -444,6 +446,69 @@ static pa_status ensure_partitions(pa_ctx* h, int G) {
                                h->stream, &h->launches)))
     return cuda_fail(e, "finding neighbour dependencies");
   h->G = G;
+  h->tuned_rounds = 0;
+  return PA_OK;
+}
+
+// Re-split one partition at equal measured cost.  CTA b spent busy[b] on
+// slices [part[b], part[b+1]); its time is spread over those slices in
+// proportion to the cost model u(s) = 32 (w(s) + row_weight), and the new
+// boundaries cut the cumulative estimate into G equal parts.
+static void resplit(std::vector<int32_t>& part, const std::vector<int32_t>& wp,
+                    const std::vector<double>& busy, int row_weight) {
+  const int G = (int)part.size() - 1;
+  const int ns = (int)wp.size() - 1;
+  std::vector<double> cost(ns);
+  for (int b = 0; b < G; ++b) {
+    double U = 0;
+    for (int s = part[b]; s < part[b + 1]; ++s) U += 32.0 * (wp[s + 1] - wp[s] + row_weight);
+    const double tau = U > 0 ? busy[b] / U : 0.0;
+    for (int s = part[b]; s < part[b + 1]; ++s) cost[s] = tau * 32.0 * (wp[s + 1] - wp[s] + row_weight);
+  }
+  double tot = 0;
+  for (double c : cost) tot += c;
+  if (!(tot > 0)) return;
+  std::vector<int32_t> np(G + 1);
+  np[0] = 0;
+  np[G] = ns;
+  double acc = 0;
+  int s = 0;
+  for (int b = 1; b < G; ++b) {
+    const double target = tot * b / G;
+    while (s < ns && acc + cost[s] < target) acc += cost[s++];
+    np[b] = std::max(np[b - 1], s);
+  }
+  part = np;
+}
+
+// One round of the partition tuner, from the per-CTA timers of the last run.
+static pa_status tune_partitions(pa_ctx* h) {
+  const int G = h->G;
+  std::vector<unsigned long long> t((size_t)2 * G);
+  std::vector<int32_t> pa_((size_t)G + 1), pt_((size_t)G + 1);
+  std::vector<int32_t> wpa((size_t)h->sa.n_slices + 1), wpt((size_t)h->sq.n_slices + 1);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(t.data(), h->cta_ns, sizeof(unsigned long long) * t.size(), cudaMemcpyDeviceToHost, h->stream)) ||
+      (e = cudaMemcpyAsync(pa_.data(), h->part_a, sizeof(int32_t) * pa_.size(), cudaMemcpyDeviceToHost, h->stream)) ||
+      (e = cudaMemcpyAsync(pt_.data(), h->part_t, sizeof(int32_t) * pt_.size(), cudaMemcpyDeviceToHost, h->stream)) ||
+      (e = cudaMemcpyAsync(wpa.data(), h->sa.wp, sizeof(int32_t) * wpa.size(), cudaMemcpyDeviceToHost, h->stream)) ||
+      (e = cudaMemcpyAsync(wpt.data(), h->sq.wp, sizeof(int32_t) * wpt.size(), cudaMemcpyDeviceToHost, h->stream)) ||
+      (e = cudaStreamSynchronize(h->stream)))
+    return cuda_fail(e, "reading the run profile for the tuner");
+  std::vector<double> ba(G), bb(G);
+  for (int b = 0; b < G; ++b) {
+    ba[b] = (double)t[2 * b];
+    bb[b] = (double)t[2 * b + 1];
+  }
+  resplit(pa_, wpa, ba, 2);
+  resplit(pt_, wpt, bb, 30);
+  if ((e = cudaMemcpyAsync(h->part_a, pa_.data(), sizeof(int32_t) * pa_.size(), cudaMemcpyHostToDevice, h->stream)) ||
+      (e = cudaMemcpyAsync(h->part_t, pt_.data(), sizeof(int32_t) * pt_.size(), cudaMemcpyHostToDevice, h->stream)) ||
+      (e = launch_dependencies(h->sa.wp, h->sa.col, h->sa.val, h->part_a, h->part_t, G, h->dep,
+                               h->stream, &h->launches)) ||
+      (e = cudaStreamSynchronize(h->stream)))
+    return cuda_fail(e, "applying the tuned partition");
+  ++h->tuned_rounds;
   return PA_OK;
 }
 
@@ -680,6 +745,11 @@ static pa_status run_one(pa_ctx* h, pa_mode mode, int iters, double lr, double b
   }
   if (mode == PA_SIGMA_MAX) { h->sigma_max = out->sigma; h->have_max = true; }
   else { h->sigma_min = out->sigma; h->have_min = true; }
+  // the partition tuner learns from plain FP64 grid-engine runs long enough
+  // to time (the FP32 and compensated kernels have other cost profiles)
+  if (!cluster && !mixed && h->opt.autotune > 0 && h->tuned_rounds < h->opt.autotune && iters >= 20 &&
+      (st = tune_partitions(h)))
+    return st;
   return (pa_status)out->status;
 }
 

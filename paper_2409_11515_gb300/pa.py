@@ -55,7 +55,7 @@ class Options(C.Structure):
     _fields_ = [("loss", C.c_int), ("precision", C.c_int), ("equilibrate", C.c_int),
                 ("engine", C.c_int), ("ablation", C.c_int), ("barrier_timeout_ns", C.c_int64),
                 ("grid_blocks", C.c_int), ("debug_skip_arrival", C.c_int),
-                ("fp64_tail", C.c_int)]
+                ("fp64_tail", C.c_int), ("autotune", C.c_int)]
 
 
 _ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)

@@ -51,14 +51,15 @@ def test_options_layout_matches_c(tmp_path, lib):
         "int main(void){printf(\"%zu %zu %zu %zu\\n\", sizeof(pa_options),"
         " offsetof(pa_options, barrier_timeout_ns), offsetof(pa_options, grid_blocks),"
         " offsetof(pa_options, debug_skip_arrival));"
-        "printf(\" %zu\\n\", offsetof(pa_options, fp64_tail));return 0;}\n")
+        "printf(\" %zu %zu\\n\", offsetof(pa_options, fp64_tail),"
+        " offsetof(pa_options, autotune));return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", str(ROOT / "include"), str(src), "-o", str(exe)], check=True)
     got = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True,
                                        check=True).stdout.split()))
     O = pa.Options
     assert got == [C.sizeof(O), O.barrier_timeout_ns.offset, O.grid_blocks.offset,
-                   O.debug_skip_arrival.offset, O.fp64_tail.offset]
+                   O.debug_skip_arrival.offset, O.fp64_tail.offset, O.autotune.offset]
 
 
 def test_defaults_and_errors_without_gpu(lib):

@@ -353,3 +353,32 @@ def test_torch_allocator_hook():
         assert abs(r["sigma_max"] / ro["sigma_max"] - 1) < 1e-10
     finally:
         pa.load().pa_set_allocator(pa._ALLOC(0), pa._FREE(0), None)
+
+
+def test_autotuned_partition_keeps_parity():
+    """The measured-cost partition tuner moves slice boundaries between runs;
+    every run, tuned or not, stays within the iterate bars, and once tuning
+    has stopped the runs are reproducible again."""
+    A = synth.hydro_operator(61, n_incl=4, eta_lo=1e18, eta_hi=1e24, seed=2)
+    T = 100
+    x0 = oracle.start_vector(A.n_cols, 3)
+    ro = oracle.projected_adam(A, pa.SIGMA_MAX, T, x_init=x0, n_trace=T, trace_L=True, **HYPER)
+    last = []
+    with pa.create(A, engine=pa.ENGINE_GRID, grid_blocks=48, autotune=3) as h:
+        for k in range(6):
+            rg = h.run(pa.SIGMA_MAX, T, x0, trace_L=True, n_trace=T, **HYPER)
+            err_x = np.linalg.norm(rg["x_trace"] - ro.x_trace, axis=1)
+            err_L = np.abs(rg["L_trace"] - ro.L_trace) / np.maximum(1.0, np.abs(ro.L_trace))
+            assert np.max(err_x) <= 1e-10, (k, np.max(err_x))
+            assert np.max(err_L) <= 1e-10, k
+            assert rg["t_min"] == ro.t_min
+            last.append(rg["x_last"])
+        G, busy = h.last_run_profile()
+    assert G == 48 and np.all(busy > 0)
+    assert np.array_equal(last[4], last[5])
+
+
+def test_autotune_rejects_negative():
+    A = synth.laplacian_2d(6)
+    with pytest.raises(pa.PAError):
+        pa.create(A, autotune=-1)
