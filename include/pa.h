@@ -59,7 +59,7 @@ typedef enum {
 enum { PA_HOST = 0, PA_DEVICE = 1 };                   /* pointer kinds        */
 enum { PA_LOSS_LOGRATIO = 0, PA_LOSS_QUADRATIC = 1 };  /* loss forms           */
 enum { PA_FP64 = 0, PA_MIXED = 1 };                    /* precision modes      */
-enum { PA_EQ_NONE = 0, PA_EQ_STORAGE = 1 };            /* equilibration        */
+enum { PA_EQ_NONE = 0, PA_EQ_STORAGE = 1, PA_EQ_TARGET = 2 }; /* equilibration */
 enum { PA_ENGINE_AUTO = 0, PA_ENGINE_GRID = 1, PA_ENGINE_CLUSTER = 2 };
 enum { PA_ABLATE_NO_TANGENT = 1, PA_ABLATE_NO_NORMALISE = 2 };
 
@@ -78,7 +78,14 @@ typedef struct {
    * uses compensated (double-double, Dot2) products for A x and A^T y and
    * for its final sigma. */
   int precision;
-  int equilibrate;  /* PA_EQ_STORAGE: keep D_r^-1 A D_c^-1 with pow2 D (implied by MIXED) */
+  /* Equilibration with the paper's row and column 2-norm scaling (rows
+   * first, then the columns of D_r^-1 A), each factor rounded to the nearest
+   * power of two so the scaling is exact.  STORAGE (implied by MIXED): the
+   * handle keeps D_r^-1 A D_c^-1 for its FP32 copies but every result still
+   * refers to A.  TARGET: the handle's matrix IS A_hat = D_r^-1 A D_c^-1;
+   * sigmas, kappa, products and the transpose all refer to A_hat (the
+   * paper's kappa of the scaled system). */
+  int equilibrate;
   int engine;       /* GRID: cooperative grid with timed software barriers;
                        CLUSTER: one thread-block cluster (<= 16 CTAs) with
                        the hardware cluster barrier (plain FP64 only);
@@ -182,8 +189,36 @@ pa_status pa_spmv_t(pa_handle h, const double* y, double* z, int ptr_kind);
  * col_t[nnz], val_t[nnz]; each may be NULL). */
 pa_status pa_get_transpose(pa_handle h, int32_t* row_ptr_t, int32_t* col_t, double* val_t);
 
+/* The paper's error analysis (section "Error estimates and conditioning",
+ * Theorems 1-4) for an approximate solution x_hat of A x = b, A being the
+ * handle's matrix (A_hat under PA_EQ_TARGET).
+ *   x_hat: n_cols float64; b: n_rows float64; host (ptr_kind = PA_HOST) or
+ *   device (PA_DEVICE) pointers, read only.
+ *   kappa, norm_a: kappa_2(A) and ||A||_2; a value <= 0 takes the handle's
+ *   latest estimates (sigma_max / sigma_min and sigma_max).
+ *   u: unit roundoff for Theorem 4 (<= 0: 2^-53, FP64).
+ *   out: host array of 10 float64:
+ *     [0] ||r||, r = A x_hat - b accumulated in Dot2 (compensated: each row's
+ *         products in CSR order, then -b_i); [1] ||b||; [2] ||x_hat||;
+ *     [3], [4] Theorem 1: ||x_hat - x|| / ||x|| lies in
+ *         [(||r||/||b||) / kappa, kappa ||r||/||b||];
+ *     [5], [6] Theorem 2: ||x_hat - x|| / ||x_hat|| lies in
+ *         [||r|| / (||A|| ||x_hat||), eps = kappa ||r|| / (||A|| ||x_hat||)];
+ *     [7] Theorem 3: ||x_hat - x|| / ||x|| <= eps / (1 - eps) (+inf if eps >= 1);
+ *     [8] Theorem 4: the rounding error bound 2 u kappa / (1 - kappa u)
+ *         (+inf if kappa u >= 1); [9] 1 if kappa u >= 1 (numerically singular
+ *         at precision u), else 0.
+ *   Divisions follow IEEE rules (b = 0 gives inf/NaN in [3], [4]).
+ * Bit-reproducible for a given matrix and inputs.  Synchronises the handle's
+ * stream.  Errors: PA_ERR_INVALID_ARG (NULL pointers, no estimates to default
+ * to), PA_ERR_OOM, PA_ERR_CUDA. */
+pa_status pa_error_bounds(pa_handle h, const double* x_hat, const double* b, int ptr_kind,
+                          double kappa, double norm_a, double u, double* out);
+
 /* The power-of-two equilibration factors D_r (n_rows) and D_c (n_cols) of the
- * handle (host outputs); PA_ERR_INVALID_ARG when the handle has none. */
+ * handle (host outputs): those of A_hat = D_r^-1 A D_c^-1 under PA_EQ_TARGET,
+ * else those of the STORAGE copies; PA_ERR_INVALID_ARG when the handle has
+ * none. */
 pa_status pa_get_equilibration(pa_handle h, double* d_row, double* d_col);
 
 /* Diagnostics of the latest persistent run of the handle: *grid = number of

@@ -150,6 +150,8 @@ def _declare(L):
     L.po_loss_grad.argtypes = [i32, i32, p, p, p, C.c_int, C.c_int, p, p]
     L.po_equilibrate_pow2.restype = None
     L.po_equilibrate_pow2.argtypes = [i32, i32, p, p, p, p, p, p]
+    L.po_error_bounds.restype = None
+    L.po_error_bounds.argtypes = [i32, i32, p, p, p, p, p, d, d, d, p]
 
 
 def _ptr(a):
@@ -218,6 +220,22 @@ def equilibrate_pow2(A):
     vh = np.empty(va.size, dtype=np.float64)
     _L().po_equilibrate_pow2(m, n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(dr), _ptr(dc), _ptr(vh))
     return dr, dc, vh
+
+
+ERROR_BOUND_KEYS = ("residual_norm", "b_norm", "x_hat_norm", "thm1_lower", "thm1_upper",
+                    "thm2_lower", "thm2_upper", "thm3_upper", "thm4_rounding", "singular")
+
+
+def error_bounds(A, x_hat, b, kappa: float, norm_a: float, u: float = 2.0 ** -53) -> dict:
+    """Residual (Dot2) of x_hat for A x = b and the bounds of the paper's
+    Theorems 1-4 (po_error_bounds)."""
+    rp, ci, va, m, n = _csr(A)
+    x_hat = np.ascontiguousarray(x_hat, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    out = np.empty(10)
+    _L().po_error_bounds(m, n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(x_hat), _ptr(b), kappa, norm_a,
+                         u, _ptr(out))
+    return dict(zip(ERROR_BOUND_KEYS, out.tolist()))
 
 
 class AdamResult(dict):

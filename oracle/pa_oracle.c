@@ -25,6 +25,8 @@
  *   po_equilibrate_pow2   row then column 2-norm scaling (the paper's "Row and
  *                         Column Scaling" subsection), each factor rounded to the
  *                         nearest power of two.
+ *   po_error_bounds       the residual of an approximate solution (Dot2) and
+ *                         the error bounds of the paper's Theorems 1-4.
  *
  * Readings where the paper is silent (all stated again in the design notes):
  *   - sigma_min: minimise L(x) = log||Ax|| - log||x|| on the sphere with the
@@ -378,4 +380,56 @@ void po_equilibrate_pow2(int32_t n_rows, int32_t n_cols, const int32_t* row_ptr,
     for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k)
       val_hat[k] = val[k] / d_row[i] / d_col[col[k]];
   free(cs);
+}
+
+/* The paper's error analysis ("Error estimates and conditioning"): the
+ * residual of an approximate solution x_hat of A x = b and the bounds of its
+ * Theorems 1-4, given kappa = kappa_2(A) and norm_a = ||A||_2.
+ *
+ * r_i = sum_k a_ik x_hat_k - b_i, accumulated in Dot2 (the row's products in
+ * CSR order, then -b_i as one more term, then s + c), so a residual near the
+ * rounding level of A x_hat is not lost to cancellation.
+ *
+ * out[0] ||r||          out[1] ||b||          out[2] ||x_hat||
+ * out[3] Theorem 1 lower bound of ||x_hat - x|| / ||x||:  (||r|| / ||b||) / kappa
+ * out[4] Theorem 1 upper bound:                            kappa ||r|| / ||b||
+ * out[5] Theorem 2 lower bound of ||x_hat - x|| / ||x_hat||: ||r|| / (||A|| ||x_hat||)
+ * out[6] Theorem 2 upper bound eps:               kappa ||r|| / (||A|| ||x_hat||)
+ * out[7] Theorem 3 bound of ||x_hat - x|| / ||x||: eps / (1 - eps), +inf if eps >= 1
+ * out[8] Theorem 4 rounding bound 2 u kappa / (1 - kappa u), +inf if kappa u >= 1
+ * out[9] 1 when kappa u >= 1 (numerically singular at precision u), else 0 */
+void po_error_bounds(int32_t n_rows, int32_t n_cols, const int32_t* row_ptr, const int32_t* col,
+                     const double* val, const double* x_hat, const double* b, double kappa,
+                     double norm_a, double u, double* out) {
+  double rr = 0.0, bb = 0.0, xx = 0.0;
+  for (int32_t i = 0; i < n_rows; ++i) {
+    double s = 0.0, c = 0.0, t, te;
+    for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+      double p, pe;
+      two_prod(val[k], x_hat[col[k]], &p, &pe);
+      two_sum(s, p, &t, &te);
+      s = t;
+      c = c + (te + pe);
+    }
+    two_sum(s, -b[i], &t, &te);
+    s = t;
+    c = c + te;
+    double r = s + c;
+    rr = rr + r * r;
+    bb = bb + b[i] * b[i];
+  }
+  for (int32_t j = 0; j < n_cols; ++j) xx = xx + x_hat[j] * x_hat[j];
+  double nr = sqrt(rr), nb = sqrt(bb), nx = sqrt(xx);
+  out[0] = nr;
+  out[1] = nb;
+  out[2] = nx;
+  out[3] = (nr / nb) / kappa;
+  out[4] = kappa * (nr / nb);
+  out[5] = nr / (norm_a * nx);
+  double eps = kappa * (nr / (norm_a * nx));
+  out[6] = eps;
+  out[7] = eps < 1.0 ? eps / (1.0 - eps) : INFINITY;
+  double ku = kappa * u;
+  out[8] = ku < 1.0 ? 2.0 * u * kappa / (1.0 - ku) : INFINITY;
+  out[9] = ku >= 1.0 ? 1.0 : 0.0;
 }

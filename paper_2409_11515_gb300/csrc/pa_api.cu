@@ -92,6 +92,7 @@ struct pa_ctx {
   double *X0 = nullptr, *X1 = nullptr, *X2 = nullptr, *Xinit = nullptr;
   double *m = nullptr, *v = nullptr, *y = nullptr, *ylo = nullptr, *dx = nullptr;
   double *partials = nullptr, *blockpart = nullptr;
+  double *eb_part = nullptr, *eb_out = nullptr;  // pa_error_bounds scratch
   double *xmin_max = nullptr, *xmin_min = nullptr;
   RunState* st = nullptr;
   int G = 0;
@@ -108,6 +109,7 @@ struct pa_ctx {
   // power-of-two equilibration (source order, FP64) and the FP32 copies the
   // mixed-precision sigma_max kernel iterates over
   double *d_row = nullptr, *d_col = nullptr;
+  double *tgt_row = nullptr, *tgt_col = nullptr;  // PA_EQ_TARGET: A_hat = D_r^-1 A D_c^-1
   float *drp32 = nullptr, *dcp32 = nullptr, *a_val32 = nullptr, *t_val32 = nullptr;
   float *X0f = nullptr, *X1f = nullptr, *X2f = nullptr, *Wf = nullptr;
   float *mf = nullptr, *vf = nullptr, *yf = nullptr, *dxf = nullptr;
@@ -209,8 +211,8 @@ static pa_status build_sell(pa_ctx* h) {
       (st = alloc_n(h, &h->sq.pos, (size_t)h->n_cols, "column permutation")))
     return st;
   cudaError_t e;
-  if ((e = launch_row_lengths(h->n_rows, h->rp, lens_a, h->stream, &h->launches)) ||
-      (e = launch_row_lengths(h->n_cols, h->rpt, lens_t, h->stream, &h->launches)) ||
+  if ((e = launch_row_lengths(h->n_rows, h->rp, h->va, lens_a, h->stream, &h->launches)) ||
+      (e = launch_row_lengths(h->n_cols, h->rpt, h->vat, lens_t, h->stream, &h->launches)) ||
       (e = launch_window_sort(h->n_rows, lens_a, h->sa.perm, h->sa.pos, h->stream, &h->launches)) ||
       (e = launch_window_sort(h->n_cols, lens_t, h->sq.perm, h->sq.pos, h->stream, &h->launches)))
     return cuda_fail(e, "sorting rows by length");
@@ -289,12 +291,17 @@ extern "C" pa_status pa_create(pa_handle* out, int32_t n_rows, int32_t n_cols, i
     return fail(PA_ERR_INVALID_ARG, "unknown loss %d", o.loss);
   if (o.precision != PA_FP64 && o.precision != PA_MIXED)
     return fail(PA_ERR_INVALID_ARG, "unknown precision mode %d", o.precision);
-  if (o.equilibrate != PA_EQ_NONE && o.equilibrate != PA_EQ_STORAGE)
+  if (o.equilibrate != PA_EQ_NONE && o.equilibrate != PA_EQ_STORAGE &&
+      o.equilibrate != PA_EQ_TARGET)
     return fail(PA_ERR_INVALID_ARG, "unknown equilibration mode %d", o.equilibrate);
   if (o.precision == PA_MIXED && o.loss != PA_LOSS_LOGRATIO)
     return fail(PA_ERR_UNSUPPORTED, "mixed precision supports the log-ratio loss only");
   if (o.autotune < 0) return fail(PA_ERR_INVALID_ARG, "autotune must be >= 0 (got %d)", o.autotune);
+  // TARGET replaces A by A_hat once at creation; the handle then treats A_hat
+  // like any input (MIXED adds its own STORAGE copies of it)
+  const bool target = o.equilibrate == PA_EQ_TARGET;
   if (o.precision == PA_MIXED) o.equilibrate = PA_EQ_STORAGE;
+  else if (target) o.equilibrate = PA_EQ_NONE;
 
   pa_ctx* h = new pa_ctx();
   h->stream = (cudaStream_t)cuda_stream;
@@ -362,6 +369,16 @@ extern "C" pa_status pa_create(pa_handle* out, int32_t n_rows, int32_t n_cols, i
   dev_free(h, src);
   dev_free(h, rowid);
   dev_free(h, bsums);
+  if (target) {
+    if ((st = alloc_n(h, &h->tgt_row, (size_t)n_rows, "row scaling")) ||
+        (st = alloc_n(h, &h->tgt_col, (size_t)n_cols, "column scaling")))
+      return bail(st);
+    if ((e = launch_equilibrate(n_rows, n_cols, h->rp, h->va, h->rpt, h->cit, h->vat, h->tgt_row,
+                                h->tgt_col, h->stream, &h->launches)) ||
+        (e = launch_scale_csr(n_rows, n_cols, h->rp, h->ci, h->va, h->rpt, h->cit, h->vat,
+                              h->tgt_row, h->tgt_col, h->stream, &h->launches)))
+      return bail(cuda_fail(e, "equilibrating the target matrix"));
+  }
   if ((st = build_sell(h))) return bail(st);
   if (o.equilibrate == PA_EQ_STORAGE &&
       (st = build_equilibration(h, o.precision == PA_MIXED)))
@@ -943,15 +960,58 @@ extern "C" pa_status pa_last_run_profile(pa_handle h, int* grid, double* busy_ns
   return PA_OK;
 }
 
+extern "C" pa_status pa_error_bounds(pa_handle h, const double* x_hat, const double* b,
+                                     int ptr_kind, double kappa, double norm_a, double u,
+                                     double* out) {
+  g_err.clear();
+  if (!h || !x_hat || !b || !out) return fail(PA_ERR_INVALID_ARG, "NULL handle or pointer");
+  if (ptr_kind != PA_HOST && ptr_kind != PA_DEVICE)
+    return fail(PA_ERR_INVALID_ARG, "ptr_kind must be PA_HOST or PA_DEVICE");
+  if (!(kappa > 0.0)) {
+    if (!h->have_max || !h->have_min)
+      return fail(PA_ERR_INVALID_ARG, "kappa not given and the handle has no sigma_max and sigma_min estimates");
+    kappa = h->sigma_max / h->sigma_min;
+  }
+  if (!(norm_a > 0.0)) {
+    if (!h->have_max) return fail(PA_ERR_INVALID_ARG, "||A|| not given and the handle has no sigma_max estimate");
+    norm_a = h->sigma_max;
+  }
+  if (!(u > 0.0)) u = 0x1.0p-53;
+  pa_status st;
+  if ((st = ensure_run_buffers(h))) return st;
+  if (!h->eb_part &&
+      ((st = alloc_n(h, &h->eb_part, (size_t)3 * kErrorBoundMaxBlocks, "error-bound partials")) ||
+       (st = alloc_n(h, &h->eb_out, 10, "error bounds"))))
+    return st;
+  cudaError_t e = cudaSuccess;
+  const double* xd = x_hat;
+  const double* bd = b;
+  if (ptr_kind == PA_HOST) {  // the run's scratch vectors y (n_rows) and dx (>= n_cols)
+    if ((e = cudaMemcpyAsync(h->dx, x_hat, sizeof(double) * h->n_cols, cudaMemcpyHostToDevice, h->stream)) ||
+        (e = cudaMemcpyAsync(h->y, b, sizeof(double) * h->n_rows, cudaMemcpyHostToDevice, h->stream)))
+      return cuda_fail(e, "copying x_hat and b");
+    xd = h->dx;
+    bd = h->y;
+  }
+  if ((e = launch_error_bounds(h->n_rows, h->n_cols, h->rp, h->ci, h->va, xd, bd, kappa, norm_a,
+                               u, h->eb_part, h->eb_out, h->stream, &h->launches)) ||
+      (e = cudaMemcpyAsync(out, h->eb_out, sizeof(double) * 10, cudaMemcpyDeviceToHost, h->stream)) ||
+      (e = cudaStreamSynchronize(h->stream)))
+    return cuda_fail(e, "evaluating the error bounds");
+  return PA_OK;
+}
+
 extern "C" pa_status pa_get_equilibration(pa_handle h, double* d_row, double* d_col) {
   g_err.clear();
   if (!h) return fail(PA_ERR_INVALID_ARG, "NULL handle");
-  if (!h->d_row) return fail(PA_ERR_INVALID_ARG, "the handle holds no equilibration");
+  const double* dr = h->tgt_row ? h->tgt_row : h->d_row;
+  const double* dc = h->tgt_row ? h->tgt_col : h->d_col;
+  if (!dr) return fail(PA_ERR_INVALID_ARG, "the handle holds no equilibration");
   cudaError_t e = cudaSuccess;
   if (d_row)
-    e = cudaMemcpyAsync(d_row, h->d_row, sizeof(double) * h->n_rows, cudaMemcpyDeviceToHost, h->stream);
+    e = cudaMemcpyAsync(d_row, dr, sizeof(double) * h->n_rows, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess && d_col)
-    e = cudaMemcpyAsync(d_col, h->d_col, sizeof(double) * h->n_cols, cudaMemcpyDeviceToHost, h->stream);
+    e = cudaMemcpyAsync(d_col, dc, sizeof(double) * h->n_cols, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "reading the equilibration");
   return PA_OK;

@@ -176,8 +176,9 @@ cudaError_t launch_partition(const int32_t* wp, int32_t n_slices, int G, int row
 // are scratch of n_rows and n_slices + 1 entries, `blocksums` of
 // scan_blocks(n_slices + 1).
 int32_t sell_slices(int32_t n_rows);
-cudaError_t launch_row_lengths(int32_t n_rows, const int32_t* rp, int32_t* lens, cudaStream_t s,
-                               int64_t* launches);
+// Non-zero values per row (explicit zeros are not stored in the sliced copies).
+cudaError_t launch_row_lengths(int32_t n_rows, const int32_t* rp, const double* va,
+                               int32_t* lens, cudaStream_t s, int64_t* launches);
 cudaError_t launch_window_sort(int32_t n, const int32_t* lens, int32_t* perm, int32_t* pos,
                                cudaStream_t s, int64_t* launches);
 cudaError_t launch_sell_build(int32_t n_rows, const int32_t* rp, const int32_t* ci,
@@ -227,6 +228,21 @@ cudaError_t launch_equilibrate(int32_t n_rows, int32_t n_cols, const int32_t* rp
                                const double* va, const int32_t* rpt, const int32_t* cit,
                                const double* vat, double* d_row, double* d_col, cudaStream_t s,
                                int64_t* launches);
+// Residual norms of an approximate solution and the bounds of Theorems 1-4
+// into out[10] (device); part holds 3 * error_bound_blocks(max(n_rows,
+// n_cols)) doubles.
+constexpr int kErrorBoundMaxBlocks = 1216;
+int error_bound_blocks(int64_t n);
+cudaError_t launch_error_bounds(int32_t n_rows, int32_t n_cols, const int32_t* rp,
+                                const int32_t* ci, const double* va, const double* x_hat,
+                                const double* b, double kappa, double norm_a, double u,
+                                double* part, double* out, cudaStream_t s, int64_t* launches);
+// A := D_row^-1 A D_col^-1 in place, in the CSR of A and in that of A^T
+// (power-of-two factors: exact).
+cudaError_t launch_scale_csr(int32_t n_rows, int32_t n_cols, const int32_t* rp,
+                             const int32_t* ci, double* va, const int32_t* rpt,
+                             const int32_t* cit, double* vat, const double* d_row,
+                             const double* d_col, cudaStream_t s, int64_t* launches);
 // out[p] = (float) d[perm[p]] for p < n (permuted factors), and flags in
 // *range_flag (bit 1) any factor outside the FP32 normal range.
 cudaError_t launch_permute_factors(int32_t n, const int32_t* perm, const double* d, float* out,

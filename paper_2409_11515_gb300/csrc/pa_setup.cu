@@ -304,6 +304,24 @@ __global__ void k_col_norm_pow2(int32_t n_cols, const int32_t* __restrict__ rpt,
   }
 }
 
+// In-place A_hat = D_row^-1 A D_col^-1 over a CSR whose rows are the rows of A
+// (row_is_a = true: entry (r, ci[k])) or the columns of A (its transpose:
+// entry (ci[k], r)).  Each value is divided by its row-of-A factor, then by
+// its column-of-A factor; both are powers of two, so the result is exact.
+__global__ void k_scale_csr(int32_t n, const int32_t* __restrict__ rp,
+                            const int32_t* __restrict__ ci, double* va,
+                            const double* __restrict__ d_row, const double* __restrict__ d_col,
+                            bool row_is_a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+    for (int32_t k = rp[r]; k < rp[r + 1]; ++k) {
+      const double dr = row_is_a ? d_row[r] : d_row[ci[k]];
+      const double dc = row_is_a ? d_col[ci[k]] : d_col[r];
+      va[k] = __ddiv_rn(__ddiv_rn(va[k], dr), dc);
+    }
+  }
+}
+
 __global__ void k_permute_factors(int32_t n, const int32_t* __restrict__ perm,
                                   const double* __restrict__ d, float* out, int* flag) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -347,10 +365,17 @@ __global__ void k_f64_to_f32(int64_t n, const double* __restrict__ in, float* ou
 }
 
 // ------------------------------------------------------ sliced ELL build --
-__global__ void k_row_lengths(int32_t n, const int32_t* __restrict__ rp, int32_t* lens) {
+// Stored non-zeros per row: explicit zeros are left out of the sliced copies
+// (they add nothing to a product of finite vectors), so every unpadded entry
+// of a slice is a real non-zero and the neighbour dependencies are exact.
+__global__ void k_row_lengths(int32_t n, const int32_t* __restrict__ rp,
+                              const double* __restrict__ va, int32_t* lens) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride)
-    lens[r] = rp[r + 1] - rp[r];
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+    int32_t c = 0;
+    for (int32_t k = rp[r]; k < rp[r + 1]; ++k) c += va[k] != 0.0;
+    lens[r] = c;
+  }
 }
 
 // One block per window of kWindow rows: bitonic sort of the keys
@@ -399,8 +424,9 @@ __global__ void k_slice_widths(int32_t n, int32_t ns, const int32_t* __restrict_
     widths[s] = (s < ns) ? lens[perm[32 * s]] : 0;
 }
 
-// One thread per (slice, lane): copy the row's entries column-major into the
-// slice and pad with (column 0, value 0.0) up to the slice width.
+// One thread per (slice, lane): copy the row's non-zero entries (in CSR
+// order) column-major into the slice and pad with (column 0, value 0.0) up
+// to the slice width.
 __global__ void k_sell_fill(int32_t n, int32_t ns, const int32_t* __restrict__ rp,
                             const int32_t* __restrict__ ci, const double* __restrict__ va,
                             const int32_t* __restrict__ perm, const int32_t* __restrict__ col_pos,
@@ -415,10 +441,11 @@ __global__ void k_sell_fill(int32_t n, int32_t ns, const int32_t* __restrict__ r
     int k = 0;
     if (p < n) {
       const int32_t r = perm[p];
-      const int32_t k0 = rp[r], len = rp[r + 1] - k0;
-      for (; k < len; ++k) {
-        col[out + 32ll * k] = col_pos[ci[k0 + k]];
-        val[out + 32ll * k] = va[k0 + k];
+      for (int32_t q = rp[r]; q < rp[r + 1]; ++q) {
+        if (va[q] == 0.0) continue;
+        col[out + 32ll * k] = col_pos[ci[q]];
+        val[out + 32ll * k] = va[q];
+        ++k;
       }
     }
     for (; k < w; ++k) {
@@ -598,6 +625,16 @@ cudaError_t launch_equilibrate(int32_t n_rows, int32_t n_cols, const int32_t* rp
   return cudaGetLastError();
 }
 
+cudaError_t launch_scale_csr(int32_t n_rows, int32_t n_cols, const int32_t* rp,
+                             const int32_t* ci, double* va, const int32_t* rpt,
+                             const int32_t* cit, double* vat, const double* d_row,
+                             const double* d_col, cudaStream_t s, int64_t* launches) {
+  k_scale_csr<<<grid_for(n_rows), kT, 0, s>>>(n_rows, rp, ci, va, d_row, d_col, true);
+  k_scale_csr<<<grid_for(n_cols), kT, 0, s>>>(n_cols, rpt, cit, vat, d_row, d_col, false);
+  *launches += 2;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_permute_factors(int32_t n, const int32_t* perm, const double* d, float* out,
                                    int* range_flag, cudaStream_t s, int64_t* launches) {
   k_permute_factors<<<grid_for(n), kT, 0, s>>>(n, perm, d, out, range_flag);
@@ -635,9 +672,9 @@ cudaError_t launch_dependencies(const int32_t* wp, const int32_t* col, const dou
   return cudaGetLastError();
 }
 
-cudaError_t launch_row_lengths(int32_t n_rows, const int32_t* rp, int32_t* lens, cudaStream_t s,
-                               int64_t* launches) {
-  k_row_lengths<<<grid_for(n_rows), kT, 0, s>>>(n_rows, rp, lens);
+cudaError_t launch_row_lengths(int32_t n_rows, const int32_t* rp, const double* va,
+                               int32_t* lens, cudaStream_t s, int64_t* launches) {
+  k_row_lengths<<<grid_for(n_rows), kT, 0, s>>>(n_rows, rp, va, lens);
   ++*launches;
   return cudaGetLastError();
 }

@@ -25,7 +25,7 @@ SIGMA_MAX, SIGMA_MIN, BOTH = 1, 2, 3
 HOST, DEVICE = 0, 1
 LOSS_LOGRATIO, LOSS_QUADRATIC = 0, 1
 FP64, MIXED = 0, 1
-EQ_NONE, EQ_STORAGE = 0, 1
+EQ_NONE, EQ_STORAGE, EQ_TARGET = 0, 1, 2
 ENGINE_AUTO, ENGINE_GRID, ENGINE_CLUSTER = 0, 1, 2
 ABLATE_NO_TANGENT, ABLATE_NO_NORMALISE = 1, 2
 
@@ -38,7 +38,10 @@ STATUS_NAMES = {0: "PA_OK", 1: "PA_WARN_SINGULAR", -1: "PA_ERR_INVALID_ARG",
 EXPORTS = ("pa_options_default", "pa_create", "pa_estimate", "pa_run", "pa_estimate_batched",
            "pa_get_vector", "pa_spmv", "pa_spmv_t", "pa_get_transpose", "pa_get_equilibration",
            "pa_kernel_launches", "pa_destroy", "pa_last_error", "pa_set_allocator",
-           "pa_last_run_profile", "pa_sigma_noalloc", "pa_last_batch_graph")
+           "pa_last_run_profile", "pa_sigma_noalloc", "pa_last_batch_graph", "pa_error_bounds")
+
+ERROR_BOUND_KEYS = ("residual_norm", "b_norm", "x_hat_norm", "thm1_lower", "thm1_upper",
+                    "thm2_lower", "thm2_upper", "thm3_upper", "thm4_rounding", "singular")
 
 
 class LibraryMissing(RuntimeError):
@@ -106,6 +109,8 @@ def _declare(L):
     L.pa_get_transpose.argtypes = [vp, vp, vp, vp]
     L.pa_get_equilibration.restype = C.c_int
     L.pa_get_equilibration.argtypes = [vp, vp, vp]
+    L.pa_error_bounds.restype = C.c_int
+    L.pa_error_bounds.argtypes = [vp, vp, vp, C.c_int, d, d, d, vp]
     L.pa_last_run_profile.restype = C.c_int
     L.pa_last_run_profile.argtypes = [vp, C.POINTER(C.c_int), vp]
     L.pa_last_batch_graph.restype = C.c_int
@@ -288,6 +293,19 @@ class Handle:
         t = np.zeros((max(g.value, 1), 2))
         _check(load().pa_last_run_profile(self._h, C.byref(g), t.ctypes.data))
         return g.value, t[:g.value]
+
+    def error_bounds(self, x_hat, b, kappa: float = 0.0, norm_a: float = 0.0,
+                     u: float = 0.0) -> dict:
+        """pa_error_bounds: residual of x_hat for A x = b and the bounds of the
+        paper's Theorems 1-4 (kappa / norm_a <= 0: the handle's estimates)."""
+        f64 = _dtypes()["f64"]
+        xp, kx, keep_x = _ptr_and_kind(x_hat, f64)
+        bp, kb, keep_b = _ptr_and_kind(b, f64)
+        if kx != kb:
+            raise ValueError("x_hat and b must both be host arrays or both device tensors")
+        out = np.empty(10)
+        _check(load().pa_error_bounds(self._h, xp, bp, kx, kappa, norm_a, u, out.ctypes.data))
+        return dict(zip(ERROR_BOUND_KEYS, out.tolist()))
 
     def get_equilibration(self):
         dr, dc = np.empty(self.n_rows), np.empty(self.n_cols)

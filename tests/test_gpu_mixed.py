@@ -91,3 +91,60 @@ def test_mixed_rejects_quadratic_loss():
     with pytest.raises(pa.PAError) as ei:
         pa.create(synth.laplacian_1d(8), precision=pa.MIXED, loss=pa.LOSS_QUADRATIC)
     assert ei.value.status == -9
+
+
+# ------------------------------------------------ PA_EQ_TARGET (kappa of A_hat) ---
+
+def _scaled(A):
+    dr, dc, vh = oracle.equilibrate_pow2(A)
+    return dr, dc, synth.CSR(A.row_ptr, A.col, vh, A.n_rows, A.n_cols)
+
+
+def test_target_equilibration_holds_the_scaled_matrix():
+    """The handle's matrix is A_hat = D_r^-1 A D_c^-1: factors, transpose values and
+    products bit-exact / within the product bar of the oracle's A_hat."""
+    A = synth.hydro_operator(21, seed=1)
+    dr, dc, S = _scaled(A)
+    with pa.create(A, equilibrate=pa.EQ_TARGET) as h:
+        gr, gc = h.get_equilibration()
+        rpt, cit, vat = h.get_transpose()
+        x = oracle.start_vector(A.n_cols, 2)
+        y = h.spmv(x)
+    assert np.array_equal(gr, dr) and np.array_equal(gc, dc)
+    order = np.argsort(S.col, kind="stable")
+    assert np.array_equal(vat, S.val[order])
+    yo = oracle.spmv(S, x)
+    absy = oracle.spmv(synth.CSR(S.row_ptr, S.col, np.abs(S.val), S.n_rows, S.n_cols), np.abs(x))
+    k = np.diff(S.row_ptr).max()
+    assert np.all(np.abs(y - yo) <= 4 * k * 2.0 ** -53 * absy + 1e-300)
+
+
+@pytest.mark.parametrize("precision", [pa.FP64, pa.MIXED])
+def test_target_sigma_max_matches_dense_svd(precision):
+    A = synth.hydro_operator(13, seed=1)
+    _, _, S = _scaled(A)
+    sv = np.linalg.svd(synth.csr_to_dense(S), compute_uv=False)
+    with pa.create(A, equilibrate=pa.EQ_TARGET, precision=precision) as h:
+        r = h.estimate(pa.SIGMA_MAX, 2000, seed=1, **HYPER)
+    assert r["status"] == 0
+    # FP64: Algorithm 1's own accuracy after 2000 iterations (the oracle's is
+    # 1.5e-10 here); MIXED: the bar of its FP64-oracle comparison
+    tol = 1e-8 if precision == pa.FP64 else 1e-6
+    assert abs(r["sigma_max"] / sv[0] - 1) <= tol, (r["sigma_max"], sv[0])
+
+
+def test_target_iterates_match_oracle_on_scaled_matrix():
+    A = synth.hydro_operator(21, seed=1)
+    _, _, S = _scaled(A)
+    T = 100
+    x0 = oracle.start_vector(A.n_cols, 7)
+    ro = oracle.projected_adam(S, pa.SIGMA_MAX, T, x_init=x0, n_trace=T, trace_L=True, **HYPER)
+    with pa.create(A, equilibrate=pa.EQ_TARGET) as h:
+        rg = h.run(pa.SIGMA_MAX, T, x0, trace_L=True, n_trace=T, **HYPER)
+    assert np.max(np.linalg.norm(rg["x_trace"] - ro.x_trace, axis=1)) <= 1e-10
+    assert np.max(np.abs(rg["L_trace"] - ro.L_trace) / np.maximum(1, np.abs(ro.L_trace))) <= 1e-10
+
+
+def test_unknown_equilibration_rejected():
+    with pytest.raises(pa.PAError):
+        pa.create(synth.laplacian_2d(5), equilibrate=7)

@@ -44,7 +44,24 @@ def _abs_products(A, x):
     return oracle.spmv(synth.CSR(A.row_ptr, A.col, np.abs(A.val), A.n_rows, A.n_cols), np.abs(x))
 
 
+def _explicit_zeros():
+    """A banded matrix plus explicit zeros: a fifth of its entries zeroed and
+    one far-away zero per row (every stored zero must stay harmless, whatever
+    the buffers it gathers from hold)."""
+    A = synth.random_sparse(3000, 7, seed=11, diag_boost=4.0)
+    rng = np.random.default_rng(12)
+    rows = np.repeat(np.arange(A.n_rows), np.diff(A.row_ptr))
+    val = A.val.copy()
+    off = rows != A.col
+    val[off & (rng.random(A.nnz) < 0.2)] = 0.0
+    far = (np.arange(A.n_rows) + A.n_rows // 2) % A.n_cols
+    return synth.from_coo(np.concatenate([rows, np.arange(A.n_rows)]),
+                          np.concatenate([A.col, far]),
+                          np.concatenate([val, np.zeros(A.n_rows)]), A.n_rows, A.n_cols)
+
+
 CASES = {
+    "explicit_zeros": _explicit_zeros,
     "hydro21": lambda: synth.hydro_operator(21, seed=1),
     "hydro13_8incl": lambda: synth.hydro_operator(13, 17, n_incl=8, seed=5),
     "lap2d_12": lambda: synth.laplacian_2d(12),
@@ -96,7 +113,7 @@ def _iterate_parity(A, mode, loss=pa.LOSS_LOGRATIO, T=100, seed=7, **opt):
 
 @pytest.mark.parametrize("engine", [pa.ENGINE_GRID, pa.ENGINE_CLUSTER])
 @pytest.mark.parametrize("name", ["hydro21", "hydro13_8incl", "lap2d_12", "random_sparse",
-                                  "rect_tall"])
+                                  "rect_tall", "explicit_zeros"])
 def test_first_100_iterates_sigma_max(name, engine):
     A = CASES[name]()
     rg, ro, err_x, err_L = _iterate_parity(A, pa.SIGMA_MAX, engine=engine)

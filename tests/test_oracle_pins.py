@@ -365,6 +365,98 @@ def test_equilibration_pow2_exact():
     assert np.all(ratio >= 2 ** -0.5 - 1e-12) and np.all(ratio <= 2 ** 0.5 + 1e-12)
 
 
+def test_equilibrated_hydro_sigma_max_matches_dense_svd():
+    """The paper's scaled system A_hat = D_r^-1 A D_c^-1 (kappa ~ 2.5e4 here,
+    against ~1e20 unscaled): Algorithm 1's sigma_max agrees with the dense SVD.
+    sigma_min of the direct route only bounds the truth from above (Rayleigh)."""
+    A = synth.hydro_operator(13, seed=1)
+    dr, dc, vh = oracle.equilibrate_pow2(A)
+    S = synth.CSR(A.row_ptr, A.col, vh, A.n_rows, A.n_cols)
+    sv = np.linalg.svd(synth.csr_to_dense(S), compute_uv=False)
+    x0 = oracle.start_vector(A.n_cols, 1)
+    r = oracle.projected_adam(S, oracle.SIGMA_MAX, 2000, x_init=x0, lr=LR, beta1=B1,
+                              beta2=B2, eps=EPS)
+    assert abs(r.sigma / sv[0] - 1) <= 1e-8
+    rm = oracle.projected_adam(S, oracle.SIGMA_MIN, 500, x_init=x0, lr=LR, beta1=B1,
+                               beta2=B2, eps=EPS)
+    assert sv[-1] * (1 - 1e-12) <= rm.sigma <= sv[0]
+
+
+# ------------------------------------ error bounds (Theorems 1-4) ---
+
+def test_error_bounds_exact_residual_on_integers():
+    """Integer A and x: b = A x is exact, so moving two entries of b by
+    2^-20 gives ||r|| = 2^-20 sqrt(2) exactly."""
+    M = _int_matrix(30, 30, seed=21) + 40.0 * np.eye(30)
+    A = synth.dense_csr(M)
+    x = np.random.default_rng(3).integers(-5, 6, size=30).astype(np.float64)
+    b = M @ x
+    assert np.array_equal(b, oracle.spmv(A, x))
+    b[[4, 17]] += 2.0 ** -20
+    e = oracle.error_bounds(A, x, b, kappa=2.0, norm_a=50.0)
+    assert e["residual_norm"] == np.sqrt(2.0) * 2.0 ** -20
+    assert e["b_norm"] == pytest.approx(np.linalg.norm(b), rel=1e-15)
+    assert e["x_hat_norm"] == pytest.approx(np.linalg.norm(x), rel=1e-15)
+
+
+def test_error_bounds_residual_survives_cancellation():
+    """Row (1e16, 1, -1e16) . (1, 1, 1) - 0 = 1: plain FP64 accumulation
+    returns 0, the compensated residual returns the exact 1."""
+    A = synth.from_coo([0, 0, 0], [0, 1, 2], [1e16, 1.0, -1e16], 1, 3)
+    x = np.ones(3)
+    assert oracle.spmv(A, x)[0] == 0.0
+    e = oracle.error_bounds(A, x, np.zeros(1), kappa=1.0, norm_a=1.0)
+    assert e["residual_norm"] == 1.0
+
+
+@pytest.mark.parametrize("kappa_true", [1e2, 1e5])
+def test_error_bounds_enclose_the_true_error(kappa_true):
+    """Dense systems with a prescribed kappa: the true error of a perturbed
+    solution lies inside every bound of Theorems 1-3 (brute force)."""
+    rng = np.random.default_rng(int(kappa_true))
+    n = 40
+    U, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    M = U @ np.diag(np.geomspace(1.0, 1.0 / kappa_true, n)) @ V.T
+    A = synth.dense_csr(M)
+    sv = np.linalg.svd(M, compute_uv=False)
+    kappa, norm_a = sv[0] / sv[-1], sv[0]
+    for trial in range(5):
+        x = rng.standard_normal(n)
+        b = M @ x
+        x_true = np.linalg.solve(M, b)
+        x_hat = x_true + 1e-6 * rng.standard_normal(n) * (10.0 ** trial)
+        e = oracle.error_bounds(A, x_hat, b, kappa=kappa, norm_a=norm_a)
+        err_x = np.linalg.norm(x_hat - x_true) / np.linalg.norm(x_true)
+        err_xh = np.linalg.norm(x_hat - x_true) / np.linalg.norm(x_hat)
+        assert e["thm1_lower"] <= err_x * (1 + 1e-9) and err_x <= e["thm1_upper"] * (1 + 1e-9)
+        assert e["thm2_lower"] <= err_xh * (1 + 1e-9) and err_xh <= e["thm2_upper"] * (1 + 1e-9)
+        if e["thm2_upper"] < 1:
+            assert err_x <= e["thm3_upper"] * (1 + 1e-9)
+        # Theorem 2's pair is tighter than Theorem 1's upper bound only up to
+        # ||b|| <= ||A|| ||x||: both uppers share the factor kappa ||r||
+        assert e["thm1_upper"] / e["thm1_lower"] == pytest.approx(kappa ** 2, rel=1e-12)
+        assert e["thm2_upper"] / e["thm2_lower"] == pytest.approx(kappa, rel=1e-12)
+
+
+def test_error_bounds_theorem4_and_singularity():
+    A = synth.laplacian_1d(5)
+    x = np.ones(5)
+    b = oracle.spmv(A, x)
+    u = 2.0 ** -53
+    e = oracle.error_bounds(A, x, b, kappa=1e10, norm_a=4.0)
+    assert e["thm4_rounding"] == pytest.approx(2 * u * 1e10 / (1 - 1e10 * u), rel=1e-15)
+    assert e["singular"] == 0.0
+    e = oracle.error_bounds(A, x, b, kappa=2.0 ** 53, norm_a=4.0)
+    assert e["thm4_rounding"] == math.inf and e["singular"] == 1.0
+    # single precision reading: u = 2^-24 makes kappa = 1e10 singular
+    e = oracle.error_bounds(A, x, b, kappa=1e10, norm_a=4.0, u=2.0 ** -24)
+    assert e["singular"] == 1.0
+    # eps >= 1: Theorem 3 gives no bound
+    e = oracle.error_bounds(A, x, b + 1.0, kappa=1e6, norm_a=4.0)
+    assert e["thm2_upper"] >= 1 and e["thm3_upper"] == math.inf
+
+
 # ---------------------------------------------- planted-mistake checks ---
 
 MUTANTS = {
@@ -378,6 +470,9 @@ MUTANTS = {
                       "for (int64_t i = 0; i < n; ++i) dx[i] = dx[i] - 0.0 * c * x[i];"),
     "sqrt_dropped": ("dx[i] = lr * mh / (sqrt(vh) + eps);", "dx[i] = lr * mh / (vh + eps);"),
     "score_before_update": ("if (L < L_min) {", "if (L <= L_min) {"),
+    "residual_sign": ("two_sum(s, -b[i], &t, &te);", "two_sum(s, b[i], &t, &te);"),
+    "residual_uncompensated": ("    double r = s + c;\n", "    double r = s;\n"),
+    "theorem2_normalised_by_b": ("out[5] = nr / (norm_a * nx);", "out[5] = nr / (norm_a * nb);"),
 }
 
 
@@ -409,6 +504,14 @@ def _pins_pass():
         checks.append(True)
     except AssertionError:
         checks.append(False)
+    for pin in (test_error_bounds_exact_residual_on_integers,
+                test_error_bounds_residual_survives_cancellation,
+                lambda: test_error_bounds_enclose_the_true_error(1e5)):
+        try:
+            pin()
+            checks.append(True)
+        except AssertionError:
+            checks.append(False)
     return all(checks)
 
 
