@@ -439,6 +439,214 @@ def run_batched_workload(args):
     return 0
 
 
+def _timed(stream, fn):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    r = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return r, e0.elapsed_time(e1) / 1e3
+
+
+def run_mixed1001(args):
+    """1001 x 1001 cells (6,012,006 rows, 8 inclusions, viscosity 1e18..1e24,
+    seed 4): one kappa_2 estimate (5000 sigma_max + 20000 sigma_min
+    iterations) in MIXED precision (pow2 storage equilibration; FP32 sigma_max
+    with an FP64 tail, Dot2-compensated FP64 sigma_min) against the same
+    estimate in plain FP64 on the same GPU; per-sigma relative differences."""
+    if _dist()[0] > 1:
+        raise SystemExit("this workload runs on one GPU (launch it without torchrun)")
+    import torch
+    from paper_2409_11515_gb300 import build, pa, synth
+    build.build()
+    pa.load()
+    torch.cuda.set_device(0)
+    A = synth.hydro_operator(1001, n_incl=8, eta_lo=1e18, eta_hi=1e24, seed=4)
+    stream = torch.cuda.Stream()
+    it_max, it_min = args.iters_max, args.iters_min
+    res = {}
+    for name, prec in (("fp64", pa.FP64), ("mixed", pa.MIXED)):
+        with pa.create(A, stream=stream, precision=prec,
+                       autotune=args.autotune if prec == pa.FP64 else 0) as h:
+            for _ in range(args.warmup):  # warm-up (and the partition tuner's rounds)
+                h.estimate(pa.SIGMA_MAX, 50, seed=START_SEED, **HYPER)
+                h.estimate(pa.SIGMA_MIN, 50, seed=START_SEED, **HYPER)
+            rM, tM = _timed(stream, lambda: h.estimate(pa.SIGMA_MAX, it_max, seed=START_SEED, **HYPER))
+            rm, tm = _timed(stream, lambda: h.estimate(pa.SIGMA_MIN, it_min, seed=START_SEED, **HYPER))
+        res[name] = {"sigma_max": rM["sigma_max"], "sigma_min": rm["sigma_min"],
+                     "kappa": rM["sigma_max"] / rm["sigma_min"],
+                     "sigma_max_iterations_per_s": it_max / tM,
+                     "sigma_min_iterations_per_s": it_min / tm,
+                     "estimate_s": tM + tm, "status": [rM["status"], rm["status"]]}
+    f, m = res["fp64"], res["mixed"]
+    line = {
+        "metric": "kappa2_estimates_per_s (mixed precision)", "value": 1.0 / m["estimate_s"],
+        "unit": "estimates/s", "n_gpus": 1, "steps": 1, "warmup": args.warmup,
+        "ms_per_step": 1e3 * m["estimate_s"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (seeded hydro-mechanical operator)",
+        "config": {"workload": "hydro-mechanical 1001x1001 cells, 6,012,006 rows, pow2 "
+                               "equilibration, mixed precision vs FP64",
+                   "n_rows": int(A.n_rows), "nnz": int(A.nnz),
+                   "iters_sigma_max": it_max, "iters_sigma_min": it_min},
+        "fp64_estimates_per_s": 1.0 / f["estimate_s"],
+        "rel_diff_vs_fp64": {"sigma_max": abs(m["sigma_max"] / f["sigma_max"] - 1),
+                             "sigma_min": abs(m["sigma_min"] / f["sigma_min"] - 1)},
+        "runs": res,
+        "note": "the comparator is this build's FP64 path (parity-tested against the CPU "
+                "oracle); a full-length oracle run at this size takes hours on one core",
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_stress2001(args):
+    """2001 x 1001 cells (12,018,006 rows, viscosity 1e16..1e24, k/eta_f
+    1e-22..1e-10, seed 5): 32 seeded restarts as FP64 SpMM blocks (k = 8 per
+    launch, four waves) against the plain FP64 single-vector path and the
+    mixed-precision single-vector path, each on a short timed run
+    (--iters-max/--iters-min, extrapolated to one estimate), plus one full
+    FP64 estimate for kappa_2."""
+    if _dist()[0] > 1:
+        raise SystemExit("this workload runs on one GPU (launch it without torchrun)")
+    import torch
+    from paper_2409_11515_gb300 import build, pa, synth
+    build.build()
+    pa.load()
+    torch.cuda.set_device(0)
+    A = synth.hydro_operator(2001, 1001, n_incl=8, eta_lo=1e16, eta_hi=1e24, keta_lo=1e-22,
+                             keta_hi=1e-10, seed=5)
+    stream = torch.cuda.Stream()
+    it = (args.iters_max, args.iters_min)
+    full_T = EST_ITERS[0] + EST_ITERS[1]
+    out = {}
+    with pa.create(A, stream=stream, autotune=args.autotune) as h:
+        for _ in range(args.warmup):
+            h.estimate(pa.SIGMA_MAX, 50, seed=START_SEED, **HYPER)
+        r1, t1 = _timed(stream, lambda: (h.estimate(pa.SIGMA_MAX, it[0], seed=START_SEED, **HYPER),
+                                         h.estimate(pa.SIGMA_MIN, it[1], seed=START_SEED, **HYPER)))
+        out["fp64_k1_vector_iterations_per_s"] = (it[0] + it[1]) / t1
+        pa.estimate_batched([h], pa.BOTH, 8, (5, 5), seed=START_SEED, **HYPER)  # warm-up
+        rb, tb = _timed(stream, lambda: pa.estimate_batched([h], pa.BOTH, 32, it,
+                                                            seed=START_SEED, **HYPER))
+        out["fp64_k32_vector_iterations_per_s"] = 32 * (it[0] + it[1]) / tb
+        rf, tf = _timed(stream, lambda: (h.estimate(pa.SIGMA_MAX, EST_ITERS[0], seed=START_SEED, **HYPER),
+                                         h.estimate(pa.SIGMA_MIN, EST_ITERS[1], seed=START_SEED, **HYPER)))
+    with pa.create(A, stream=stream, precision=pa.MIXED) as hm:
+        hm.estimate(pa.SIGMA_MAX, 50, seed=START_SEED, **HYPER)
+        rmx, tmx = _timed(stream, lambda: hm.estimate(pa.SIGMA_MAX, it[0], seed=START_SEED, **HYPER))
+        rmn, tmn = _timed(stream, lambda: hm.estimate(pa.SIGMA_MIN, it[1], seed=START_SEED, **HYPER))
+    out["mixed_k1_vector_iterations_per_s"] = (it[0] + it[1]) / (tmx + tmn)
+    kappa = rf[0]["sigma_max"] / rf[1]["sigma_min"]
+    est_k32 = 32 * (it[0] + it[1]) / tb / full_T
+    line = {
+        "metric": "kappa2_estimates_per_s (32 restarts, FP64 SpMM)", "value": est_k32,
+        "unit": "estimates/s", "n_gpus": 1, "steps": 1, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tb, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded hydro-mechanical operator)",
+        "config": {"workload": "hydro-mechanical 2001x1001 cells, 12,018,006 rows, viscosity "
+                               "contrast 1e8, 32 restarts", "n_rows": int(A.n_rows),
+                   "nnz": int(A.nnz), "iters_timed": list(it), "estimate_iters": list(EST_ITERS)},
+        "fp64_k1_estimates_per_s": out["fp64_k1_vector_iterations_per_s"] / full_T,
+        "throughput": out,
+        "kappa_fp64_full_estimate": kappa,
+        "sigma_fp64": [rf[0]["sigma_max"], rf[1]["sigma_min"]],
+        "mixed_short_run_sigmas": [rmx["sigma_max"], rmn["sigma_min"]],
+        "batched_sigma_max_spread": [float(rb["sigma_max"].min()), float(rb["sigma_max"].max())],
+        "note": "value and the k=1 figures extrapolate the timed iterations to the 5000 + 20000 "
+                "of one estimate; the mixed-precision path has no batched (SpMM) form",
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _lu_factors(A):
+    """P A Q = L U from SuperLU (scipy, host): the caller's direct solver."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    from paper_2409_11515_gb300 import synth
+    n = A.n_rows
+    lu = spl.splu(sp.csr_matrix((A.val, A.col, A.row_ptr), shape=(n, n)).tocsc(),
+                  permc_spec="COLAMD")
+    out = []
+    for T in (lu.L.tocsr(), lu.U.tocsr()):
+        T.sort_indices()
+        out.append(synth.CSR(T.indptr.astype(np.int32), T.indices.astype(np.int32),
+                             T.data.copy(), n, n))
+    return (out[0], out[1], np.argsort(lu.perm_r).astype(np.int32),
+            np.argsort(lu.perm_c).astype(np.int32))
+
+
+def run_lu64(args):
+    """The paper's full kappa_2 route on many small operators: 64 hydro
+    operators with sides drawn from 7..31 cells (seed 6), 8 restarts each;
+    sigma_max by Algorithm 1 (FP64 SpMM, 2000 iterations) and sigma_min by
+    Algorithm 1 on A^{-1} with Algorithm 2's gradient (given COLAMD LU
+    factors, 500 iterations), all items in one pa_estimate_batched call;
+    against the single-handle loop and the CPU oracle on the same items."""
+    if _dist()[0] > 1:
+        raise SystemExit("this workload runs on one GPU (launch it without torchrun)")
+    import torch
+    from paper_2409_11515_gb300 import build, pa, synth
+    build.build()
+    pa.load()
+    torch.cuda.set_device(0)
+    n_mat, k, it = 64, 8, (2000, 500)
+    mats = synth.hydro_batch(n_mat, 7, 31, seed=6)
+    t0 = time.perf_counter()
+    facs = [_lu_factors(A) for A in mats]
+    t_factor = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    hs = [pa.create(A, stream=stream) for A in mats]
+    for h, f in zip(hs, facs):
+        h.attach_lu(*f)
+    for _ in range(args.warmup):
+        pa.estimate_batched(hs, pa.BOTH_LU, k, (20, 20), seed=3, **HYPER)
+    rb, tb = _timed(stream, lambda: pa.estimate_batched(hs, pa.BOTH_LU, k, it, seed=3, **HYPER))
+    sample = list(range(0, n_mat, 8))
+
+    def single_loop():
+        for i in sample:
+            for r in range(2):
+                hs[i].estimate(pa.SIGMA_MAX, it[0], seed=r, **HYPER)
+                hs[i].estimate(pa.SIGMA_MIN_LU, it[1], seed=r, **HYPER)
+
+    _, ts = _timed(stream, single_loop)
+    for h in hs:
+        h.destroy()
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    for i in sample[:4]:
+        x0 = oracle.start_vector(mats[i].n_cols, 1)
+        oracle.projected_adam(mats[i], oracle.SIGMA_MAX, it[0], x_init=x0, **HYPER)
+        oracle.projected_adam_lu(*facs[i], it[1], x0, **HYPER)
+    t_cpu = time.perf_counter() - t0
+    rows = [A.n_rows for A in mats]
+    kap = rb["kappa"]
+    line = {
+        "metric": "kappa2_estimates_per_s (LU route, batched)", "value": n_mat * k / tb,
+        "unit": "estimates/s", "n_gpus": 1, "steps": 1, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tb, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded hydro-mechanical operators)",
+        "config": {"workload": "64 hydro operators, sides U[7,31] (seed 6), 8 restarts each; "
+                               "sigma_max 2000 iterations (SpMM), sigma_min 500 iterations on "
+                               "A^{-1} through COLAMD LU factors, one CTA per item",
+                   "rows_min_max": [min(rows), max(rows)], "k": k, "iters": list(it)},
+        "single_handle_estimates_per_s": 2 * len(sample) / ts,
+        "cpu_baseline": {"value": len(sample[:4]) / t_cpu, "unit": "estimates/s", "cores": 1,
+                         "kind": "oracle",
+                         "sample": "4 of the 64 operators, one restart each, same iterations "
+                                   "(serial C oracle, one host core)"},
+        "kappa_range": [float(np.nanmin(kap)), float(np.nanmax(kap))],
+        "item_status_nonzero": int(np.count_nonzero(rb["item_status"])),
+        "host_factorisation_s": t_factor,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _start_vector_host(n):
     import oracle
     return oracle.start_vector(n, START_SEED)
@@ -456,8 +664,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision leg")
-    ap.add_argument("--workload", choices=["hydro401", "batched"], default="hydro401",
-                    help="hydro401: the benchmark line; batched: 64 operators x 8 restarts")
+    ap.add_argument("--workload", choices=["hydro401", "batched", "mixed1001", "stress2001",
+                                           "lu64"],
+                    default="hydro401",
+                    help="hydro401: the benchmark line; batched: 64 operators x 8 restarts; "
+                         "mixed1001: 1001x1001 mixed vs FP64; stress2001: 2001x1001, 32 restarts; "
+                         "lu64: 64 small operators, kappa through the LU route")
     ap.add_argument("--iters-max", type=int, default=ITERS_MAX,
                     help="sigma_max iterations per estimate (short runs for profiling)")
     ap.add_argument("--iters-min", type=int, default=ITERS_MIN)
@@ -467,6 +679,12 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched_workload(args)
+    if args.workload == "mixed1001":
+        return run_mixed1001(args)
+    if args.workload == "stress2001":
+        return run_stress2001(args)
+    if args.workload == "lu64":
+        return run_lu64(args)
     return run_ours(args)
 
 

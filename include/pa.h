@@ -37,9 +37,13 @@ extern "C" {
 typedef struct pa_ctx* pa_handle; /* opaque; owned by the library */
 
 typedef enum {
-  PA_SIGMA_MAX = 1, /* maximise L: sigma_max = ||A||_2                   */
-  PA_SIGMA_MIN = 2, /* minimise ||Ax||/||x|| on the sphere: sigma_min   */
-  PA_BOTH = 3
+  PA_SIGMA_MAX = 1,    /* maximise L: sigma_max = ||A||_2                  */
+  PA_SIGMA_MIN = 2,    /* minimise ||Ax||/||x|| on the sphere: sigma_min  */
+  PA_BOTH = 3,
+  PA_SIGMA_MIN_LU = 4, /* sigma_min = 1 / ||A^{-1}||_2 by Algorithm 1 on
+                          A^{-1} with the gradient of Algorithm 2 (needs the
+                          factors of pa_attach_lu)                         */
+  PA_BOTH_LU = 5       /* PA_SIGMA_MAX + PA_SIGMA_MIN_LU                    */
 } pa_mode;
 
 typedef enum {
@@ -135,13 +139,38 @@ pa_status pa_create(pa_handle* out, int32_t n_rows, int32_t n_cols, int64_t nnz,
  * is ||A x_min|| / ||x_min|| for the tracked minimiser x_min.  The handle keeps
  * the latest sigma_max and sigma_min, so kappa = sigma_max / sigma_min once
  * both modes have run (NaN before).  Host outputs; each may be NULL.
+ * PA_SIGMA_MIN_LU / PA_BOTH_LU take sigma_min through the attached LU
+ * factors (Algorithm 2); the same start vector serves both modes.
  * Returns PA_OK, PA_WARN_SINGULAR or an error (PA_ERR_NONFINITE,
- * PA_ERR_TIMEOUT, PA_ERR_NOT_SQUARE for sigma_min with n_rows < n_cols). */
+ * PA_ERR_TIMEOUT, PA_ERR_NOT_SQUARE for sigma_min with n_rows < n_cols,
+ * PA_ERR_INVALID_ARG for an LU mode without factors). */
 pa_status pa_estimate(pa_handle h, pa_mode mode, int iters, double lr, double beta1,
                       double beta2, double eps, uint64_t seed, double* sigma_max,
                       double* sigma_min, double* kappa);
 
-/* Algorithm 1 for one mode (PA_SIGMA_MAX or PA_SIGMA_MIN) from a given
+/* Attach an LU factorisation P A Q = L U of the handle's (square) matrix for
+ * the paper's sigma_min route (Algorithm 2: r = A^{-1} x from L U r = x,
+ * s = A^{-T} r from U^T L^T s = r, gradient x/||x||^2 - s/||r||^2, inside
+ * Algorithm 1 on A^{-1}).  The library does not factorise: the factors come
+ * from the caller's direct solver.
+ *   L: lower triangular, U: upper triangular, n x n CSR (int32 row_ptr[n+1],
+ *   col[nnz], float64 val[nnz]; each row stores its non-zero diagonal; L
+ *   need not be unit).  p[i] = the row of A that is row i of P A, q[j] = the
+ *   column of A that is column j of A Q (int32[n]; NULL = identity).
+ *   Host pointers (ptr_kind = PA_HOST) or device pointers (PA_DEVICE); all
+ *   are copied, a second call replaces the factors.
+ * The host orders each triangular system by dependency level once here; the
+ * iteration runs as one CTA that walks the levels (cost per iteration grows
+ * with the number of levels, so fill-reducing orderings with short
+ * elimination trees run fastest).
+ * Errors: PA_ERR_NOT_SQUARE, PA_ERR_INVALID_ARG (NULL pointers, a factor that
+ * is not triangular, has an entry out of range or a zero or missing
+ * diagonal, p or q not a permutation), PA_ERR_OOM, PA_ERR_CUDA. */
+pa_status pa_attach_lu(pa_handle h, const int32_t* l_row_ptr, const int32_t* l_col,
+                       const double* l_val, const int32_t* u_row_ptr, const int32_t* u_col,
+                       const double* u_val, const int32_t* p, const int32_t* q, int ptr_kind);
+
+/* Algorithm 1 for one mode (PA_SIGMA_MAX, PA_SIGMA_MIN or PA_SIGMA_MIN_LU) from a given
  * start vector x_init (n_cols float64, host or device per x_kind, used as
  * is: Algorithm 1 does not normalise x_init).  Host outputs, each may be NULL:
  *   x_min[n_cols]   Algorithm 1's return value
@@ -149,7 +178,9 @@ pa_status pa_estimate(pa_handle h, pa_mode mode, int iters, double lr, double be
  *   info[4]         {L_min, t_min (0 = x_init), L(x_T), iterations run}
  *   L_trace[iters]  L(x_t) for t = 1..iters
  *   x_trace[n_trace * n_cols]  x_t for t = 1..n_trace (n_trace <= iters)
- *   sigma           ||A x_min|| / ||x_min||
+ *   sigma           ||A x_min|| / ||x_min||; for PA_SIGMA_MIN_LU the
+ *                   iterates live on A^{-1}: L(x) = log||x|| - log||A^{-1} x||
+ *                   and sigma = ||x_min|| / ||A^{-1} x_min|| = sigma_min(A)
  */
 pa_status pa_run(pa_handle h, pa_mode mode, int iters, double lr, double beta1, double beta2,
                  double eps, const double* x_init, int x_kind, double* x_min, double* x_last,
@@ -175,8 +206,9 @@ pa_status pa_estimate_batched(int n_mat, const pa_handle* handles, pa_mode mode,
  * the same sequence ran as ordinary launches. */
 int pa_last_batch_graph(void);
 
-/* x_min of the latest run of `which` (PA_SIGMA_MAX or PA_SIGMA_MIN) into the
- * host array x_min_host[n_cols] (Algorithm 1's output). */
+/* x_min of the latest run of `which` (PA_SIGMA_MAX, PA_SIGMA_MIN or
+ * PA_SIGMA_MIN_LU) into the host array x_min_host[n_cols] (Algorithm 1's
+ * output; for PA_SIGMA_MIN_LU the maximiser of ||A^{-1} x|| / ||x||). */
 pa_status pa_get_vector(pa_handle h, pa_mode which, double* x_min_host);
 
 /* y = A x (n_rows outputs) or z = A^T y over the explicit transpose (n_cols

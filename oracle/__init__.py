@@ -152,6 +152,14 @@ def _declare(L):
     L.po_equilibrate_pow2.argtypes = [i32, i32, p, p, p, p, p, p]
     L.po_error_bounds.restype = None
     L.po_error_bounds.argtypes = [i32, i32, p, p, p, p, p, d, d, d, p]
+    for name in ("po_lower_solve", "po_upper_solve", "po_upper_t_solve", "po_lower_t_solve"):
+        getattr(L, name).restype = None
+        getattr(L, name).argtypes = [i32, p, p, p, p, p]
+    L.po_lu_products.restype = None
+    L.po_lu_products.argtypes = [i32, p, p, p, p, p, p, p, p, p, p, p]
+    L.po_projected_adam_lu.restype = C.c_int
+    L.po_projected_adam_lu.argtypes = [i32, p, p, p, p, p, p, p, p, i64, d, d, d, d, p, p, p, p,
+                                       p, p, i64]
 
 
 def _ptr(a):
@@ -236,6 +244,52 @@ def error_bounds(A, x_hat, b, kappa: float, norm_a: float, u: float = 2.0 ** -53
     _L().po_error_bounds(m, n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(x_hat), _ptr(b), kappa, norm_a,
                          u, _ptr(out))
     return dict(zip(ERROR_BOUND_KEYS, out.tolist()))
+
+
+def triangular_solve(T, b, kind: str) -> np.ndarray:
+    """kind: 'lower' (T x = b), 'upper', 'upper_t' (T^T x = b, T upper) or
+    'lower_t' (T^T x = b, T lower); T in CSR with its diagonal stored."""
+    rp, ci, va, n, _ = _csr(T)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.empty(n)
+    getattr(_L(), f"po_{kind}_solve")(n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(b), _ptr(x))
+    return x
+
+
+def _perm(p, n):
+    return None if p is None else np.ascontiguousarray(p, dtype=np.int32)
+
+
+def lu_products(Lf, Uf, p, q, x):
+    """(r, s) = (A^{-1} x, A^{-T} A^{-1} x) for P A Q = L U (Algorithm 2's solves)."""
+    lrp, lci, lva, n, _ = _csr(Lf)
+    urp, uci, uva, _, _ = _csr(Uf)
+    p, q = _perm(p, n), _perm(q, n)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    r, s = np.empty(n), np.empty(n)
+    _L().po_lu_products(n, _ptr(lrp), _ptr(lci), _ptr(lva), _ptr(urp), _ptr(uci), _ptr(uva),
+                        _ptr(p), _ptr(q), _ptr(x), _ptr(r), _ptr(s))
+    return r, s
+
+
+def projected_adam_lu(Lf, Uf, p, q, iters: int, x_init, lr: float = 1e-2, beta1: float = 0.9,
+                      beta2: float = 0.999, eps: float = 1e-12, n_trace: int = 0,
+                      trace_L: bool = False):
+    """Algorithm 1 on A^{-1} with Algorithm 2's gradient; sigma_min = 1 / sigma."""
+    lrp, lci, lva, n, _ = _csr(Lf)
+    urp, uci, uva, _, _ = _csr(Uf)
+    p, q = _perm(p, n), _perm(q, n)
+    x_init = np.ascontiguousarray(x_init, dtype=np.float64)
+    x_min, x_last, out = np.empty(n), np.empty(n), np.empty(5)
+    L_trace = np.empty(iters) if trace_L else None
+    x_trace = np.empty((n_trace, n)) if n_trace else None
+    st = _L().po_projected_adam_lu(n, _ptr(lrp), _ptr(lci), _ptr(lva), _ptr(urp), _ptr(uci),
+                                   _ptr(uva), _ptr(p), _ptr(q), iters, lr, beta1, beta2, eps,
+                                   _ptr(x_init), _ptr(x_min), _ptr(x_last), _ptr(out),
+                                   _ptr(L_trace), _ptr(x_trace), n_trace)
+    return AdamResult(status=st, x_min=x_min, x_last=x_last, L_min=out[0], t_min=int(out[1]),
+                      L_last=out[2], iters_run=int(out[3]), sigma=out[4], sigma_min=1.0 / out[4],
+                      L_trace=L_trace, x_trace=x_trace)
 
 
 class AdamResult(dict):

@@ -27,6 +27,9 @@
  *                         nearest power of two.
  *   po_error_bounds       the residual of an approximate solution (Dot2) and
  *                         the error bounds of the paper's Theorems 1-4.
+ *   po_projected_adam_lu  Algorithm 1 on A^{-1} with the gradient of Algorithm 2
+ *                         (triangular solves with given L, U factors):
+ *                         sigma_min(A) = 1 / ||A^{-1}||_2.
  *
  * Readings where the paper is silent (all stated again in the design notes):
  *   - sigma_min: minimise L(x) = log||Ax|| - log||x|| on the sphere with the
@@ -432,4 +435,200 @@ void po_error_bounds(int32_t n_rows, int32_t n_cols, const int32_t* row_ptr, con
   double ku = kappa * u;
   out[8] = ku < 1.0 ? 2.0 * u * kappa / (1.0 - ku) : INFINITY;
   out[9] = ku >= 1.0 ? 1.0 : 0.0;
+}
+
+/* ------------------------------------------------ Algorithm 2 (LU route) --- */
+/*
+ * sigma_min(A) = 1 / ||A^{-1}||_2, with ||A^{-1}||_2 found by Algorithm 1 on
+ * the operator B = A^{-1}, whose gradient Algorithm 2 computes from one LU
+ * factorisation: r = A^{-1} x by L U r = x, s = A^{-T} r by U^T L^T s = r,
+ * grad L(x) = x / ||x||^2 - s / ||r||^2.
+ *
+ * Factors: P A Q = L U with L lower and U upper triangular (n x n CSR, each
+ * row holding its diagonal entry; L need not be unit), p[i] = the row of A
+ * that is row i of P A, q[j] = the column of A that is column j of A Q
+ * (NULL = identity).  Then A^{-1} = Q U^{-1} L^{-1} P and
+ * A^{-T} = P^T L^{-T} U^{-T} Q^T.
+ */
+
+/* L x = b by forward substitution: x_i = (b_i - sum_{j<i} l_ij x_j) / l_ii,
+ * the sum in CSR order. */
+void po_lower_solve(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
+                    const double* b, double* x) {
+  for (int32_t i = 0; i < n; ++i) {
+    double acc = 0.0, d = 0.0;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+      if (ci[k] < i) acc = acc + va[k] * x[ci[k]];
+      else if (ci[k] == i) d = va[k];
+    }
+    x[i] = (b[i] - acc) / d;
+  }
+}
+
+/* U x = b by back substitution: x_i = (b_i - sum_{j>i} u_ij x_j) / u_ii. */
+void po_upper_solve(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
+                    const double* b, double* x) {
+  for (int32_t i = n - 1; i >= 0; --i) {
+    double acc = 0.0, d = 0.0;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+      if (ci[k] > i) acc = acc + va[k] * x[ci[k]];
+      else if (ci[k] == i) d = va[k];
+    }
+    x[i] = (b[i] - acc) / d;
+  }
+}
+
+/* U^T x = b from the rows of U (column-oriented forward substitution: once
+ * x_i is known, row i of U scatters u_ij x_i into the pending sums of the
+ * later unknowns j). */
+void po_upper_t_solve(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
+                      const double* b, double* x) {
+  double* acc = (double*)calloc((size_t)n, sizeof(double));
+  for (int32_t i = 0; i < n; ++i) {
+    double d = 0.0;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k)
+      if (ci[k] == i) d = va[k];
+    x[i] = (b[i] - acc[i]) / d;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k)
+      if (ci[k] > i) acc[ci[k]] = acc[ci[k]] + va[k] * x[i];
+  }
+  free(acc);
+}
+
+/* L^T x = b from the rows of L (column-oriented back substitution). */
+void po_lower_t_solve(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
+                      const double* b, double* x) {
+  double* acc = (double*)calloc((size_t)n, sizeof(double));
+  for (int32_t i = n - 1; i >= 0; --i) {
+    double d = 0.0;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k)
+      if (ci[k] == i) d = va[k];
+    x[i] = (b[i] - acc[i]) / d;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k)
+      if (ci[k] < i) acc[ci[k]] = acc[ci[k]] + va[k] * x[i];
+  }
+  free(acc);
+}
+
+typedef struct {
+  int32_t n;
+  const int32_t *l_rp, *l_ci, *u_rp, *u_ci, *p, *q;
+  const double *l_va, *u_va;
+} po_lu;
+
+/* r = A^{-1} x = Q U^{-1} L^{-1} P x.  Returns u = Q^T r (||u|| = ||r||); r
+ * itself goes to r_out when it is not NULL. */
+static void po_lu_apply(const po_lu* f, const double* x, double* w, double* t, double* u,
+                        double* r_out) {
+  const int32_t n = f->n;
+  for (int32_t i = 0; i < n; ++i) w[i] = x[f->p ? f->p[i] : i];
+  po_lower_solve(n, f->l_rp, f->l_ci, f->l_va, w, t);
+  po_upper_solve(n, f->u_rp, f->u_ci, f->u_va, t, u);
+  if (r_out)
+    for (int32_t j = 0; j < n; ++j) r_out[f->q ? f->q[j] : j] = u[j];
+}
+
+/* s = A^{-T} r = P^T L^{-T} U^{-T} (Q^T r), from u = Q^T r. */
+static void po_lu_apply_t(const po_lu* f, const double* u, double* a, double* c, double* s) {
+  const int32_t n = f->n;
+  po_upper_t_solve(n, f->u_rp, f->u_ci, f->u_va, u, a);
+  po_lower_t_solve(n, f->l_rp, f->l_ci, f->l_va, a, c);
+  for (int32_t i = 0; i < n; ++i) s[f->p ? f->p[i] : i] = c[i];
+}
+
+/* r = A^{-1} x and s = A^{-T} A^{-1} x through the factors (test access). */
+void po_lu_products(int32_t n, const int32_t* l_rp, const int32_t* l_ci, const double* l_va,
+                    const int32_t* u_rp, const int32_t* u_ci, const double* u_va,
+                    const int32_t* p, const int32_t* q, const double* x, double* r, double* s) {
+  po_lu f = {n, l_rp, l_ci, u_rp, u_ci, p, q, l_va, u_va};
+  double* w = (double*)malloc(sizeof(double) * n);
+  double* t = (double*)malloc(sizeof(double) * n);
+  double* u = (double*)malloc(sizeof(double) * n);
+  po_lu_apply(&f, x, w, t, u, r);
+  if (s) po_lu_apply_t(&f, u, w, t, s);
+  free(w); free(t); free(u);
+}
+
+/* Algorithm 1 on B = A^{-1} with the gradient of Algorithm 2.  Arguments and
+ * outputs as po_projected_adam (mode sigma_max of B, log-ratio loss,
+ * L(x) = log||x|| - log||A^{-1} x||); out[4] = sigma_max(B) = ||B x_min|| /
+ * ||x_min||, so sigma_min(A) = 1 / out[4]. */
+int po_projected_adam_lu(int32_t n, const int32_t* l_rp, const int32_t* l_ci, const double* l_va,
+                         const int32_t* u_rp, const int32_t* u_ci, const double* u_va,
+                         const int32_t* p, const int32_t* q, int64_t iters, double lr,
+                         double beta1, double beta2, double eps, const double* x_init,
+                         double* x_min, double* x_last, double* out, double* L_trace,
+                         double* x_trace, int64_t n_trace) {
+  if (iters < 0 || n <= 0) return PO_BADARG;
+  po_lu f = {n, l_rp, l_ci, u_rp, u_ci, p, q, l_va, u_va};
+  double* x = (double*)malloc(sizeof(double) * n);
+  double* xm = (double*)malloc(sizeof(double) * n);
+  double* m = (double*)calloc(n, sizeof(double));
+  double* v = (double*)calloc(n, sizeof(double));
+  double* g = (double*)malloc(sizeof(double) * n);
+  double* dx = (double*)malloc(sizeof(double) * n);
+  double* u = (double*)malloc(sizeof(double) * n);
+  double* sv = (double*)malloc(sizeof(double) * n);
+  double* w1 = (double*)malloc(sizeof(double) * n);
+  double* w2 = (double*)malloc(sizeof(double) * n);
+  memcpy(x, x_init, sizeof(double) * n);
+  memcpy(xm, x_init, sizeof(double) * n);
+  double L_min = INFINITY, L_last = NAN;
+  int64_t t_min = 0, t_done = 0;
+  int status = PO_OK;
+  if (L_trace)
+    for (int64_t t = 0; t < iters; ++t) L_trace[t] = NAN;
+
+  for (int64_t t = 1; t <= iters + 1; ++t) {
+    /* r = A^{-1} x (Algorithm 2: solve L U r = x) and norm_r */
+    po_lu_apply(&f, x, w1, w2, u, NULL);
+    double rr = po_dot(n, u, u);
+    double q2 = po_dot(n, x, x);
+    if (!isfinite(rr) || !isfinite(q2) || rr == 0.0) { status = PO_NONFINITE; break; }
+    if (t > 1) {
+      double L = log(sqrt(q2)) - log(sqrt(rr));
+      L_last = L;
+      if (L_trace) L_trace[t - 2] = L;
+      if (L < L_min) {
+        L_min = L;
+        t_min = t - 1;
+        memcpy(xm, x, sizeof(double) * n);
+      }
+    }
+    if (t == iters + 1) break;
+    /* s = A^{-T} r (solve U^T L^T s = r); grad L = x / ||x||^2 - s / ||r||^2 */
+    po_lu_apply_t(&f, u, w1, w2, sv);
+    for (int32_t i = 0; i < n; ++i) g[i] = x[i] / q2 - sv[i] / rr;
+    double bc1 = 1.0 - pow(beta1, (double)t);
+    double bc2 = 1.0 - pow(beta2, (double)t);
+    for (int32_t i = 0; i < n; ++i) {
+      m[i] = beta1 * m[i] + (1.0 - beta1) * g[i];
+      v[i] = beta2 * v[i] + (1.0 - beta2) * (g[i] * g[i]);
+      double mh = m[i] / bc1;
+      double vh = v[i] / bc2;
+      dx[i] = lr * mh / (sqrt(vh) + eps);
+    }
+    double c = po_dot(n, x, dx);
+    for (int32_t i = 0; i < n; ++i) dx[i] = dx[i] - c * x[i];
+    for (int32_t i = 0; i < n; ++i) x[i] = x[i] - dx[i];
+    double nrm = sqrt(po_dot(n, x, x));
+    for (int32_t i = 0; i < n; ++i) x[i] = x[i] / nrm;
+    t_done = t;
+    if (x_trace && t <= n_trace) memcpy(x_trace + (t - 1) * n, x, sizeof(double) * n);
+  }
+
+  /* sigma_max(A^{-1}) at the tracked maximiser */
+  po_lu_apply(&f, xm, w1, w2, u, NULL);
+  double sig = sqrt(po_dot(n, u, u)) / sqrt(po_dot(n, xm, xm));
+  if (x_min) memcpy(x_min, xm, sizeof(double) * n);
+  if (x_last) memcpy(x_last, x, sizeof(double) * n);
+  if (out) {
+    out[0] = L_min;
+    out[1] = (double)t_min;
+    out[2] = L_last;
+    out[3] = (double)t_done;
+    out[4] = sig;
+  }
+  free(x); free(xm); free(m); free(v); free(g); free(dx); free(u); free(sv); free(w1); free(w2);
+  return status;
 }

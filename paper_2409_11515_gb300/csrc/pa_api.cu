@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "pa_device.cuh"
 #include "pa_internal.h"
 
 using namespace pa;
@@ -93,6 +94,14 @@ struct pa_ctx {
   double *m = nullptr, *v = nullptr, *y = nullptr, *ylo = nullptr, *dx = nullptr;
   double *partials = nullptr, *blockpart = nullptr;
   double *eb_part = nullptr, *eb_out = nullptr;  // pa_error_bounds scratch
+  // Algorithm 2: the attached factors in level-scheduled form
+  bool have_lu = false, have_min_lu = false, have_min_direct = false;
+  TriSys lu_sys[4] = {};          // L, U, U^T, L^T
+  int32_t* lu_p = nullptr;        // row permutation (null = identity)
+  std::vector<void*> lu_bufs;     // device arrays of the factors
+  double* xmin_lu = nullptr;      // x_min of the latest LU-route run (source order)
+  double *lu_w = nullptr, *lu_t = nullptr, *lu_u = nullptr, *lu_a = nullptr, *lu_c = nullptr;
+  LuParams* lu_params = nullptr;  // device copy of the latest run's parameters
   double *xmin_max = nullptr, *xmin_min = nullptr;
   RunState* st = nullptr;
   int G = 0;
@@ -761,7 +770,7 @@ static pa_status run_one(pa_ctx* h, pa_mode mode, int iters, double lr, double b
     if ((st = status_error(out))) return st;
   }
   if (mode == PA_SIGMA_MAX) { h->sigma_max = out->sigma; h->have_max = true; }
-  else { h->sigma_min = out->sigma; h->have_min = true; }
+  else { h->sigma_min = out->sigma; h->have_min = true; h->have_min_direct = true; }
   // the partition tuner learns from plain FP64 grid-engine runs long enough
   // to time (the FP32 and compensated kernels have other cost profiles)
   if (!cluster && !mixed && h->opt.autotune > 0 && h->tuned_rounds < h->opt.autotune && iters >= 20 &&
@@ -770,20 +779,254 @@ static pa_status run_one(pa_ctx* h, pa_mode mode, int iters, double lr, double b
   return (pa_status)out->status;
 }
 
+// ------------------------------------------------ Algorithm 2 (LU route) --
+
+static pa_status free_lu(pa_ctx* h) {
+  for (void* b : h->lu_bufs) dev_free(h, b);
+  h->lu_bufs.clear();
+  h->have_lu = false;
+  h->lu_p = nullptr;
+  return PA_OK;
+}
+
+template <typename T>
+static pa_status upload(pa_ctx* h, const std::vector<T>& v, T** out, const char* what) {
+  pa_status st = alloc_n(h, out, std::max<size_t>(v.size(), 1), what);
+  if (st) return st;
+  h->lu_bufs.push_back((void*)*out);
+  if (!v.empty()) {
+    cudaError_t e = cudaMemcpyAsync(*out, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice,
+                                    h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // v is pageable
+    if (e != cudaSuccess) return cuda_fail(e, what);
+  }
+  return PA_OK;
+}
+
+template <typename T>
+static pa_status to_host(pa_ctx* h, const T* src, size_t count, int kind, std::vector<T>* out) {
+  out->resize(count);
+  if (count == 0) return PA_OK;
+  if (kind == PA_HOST) {
+    std::copy(src, src + count, out->begin());
+    return PA_OK;
+  }
+  cudaError_t e = cudaMemcpyAsync(out->data(), src, sizeof(T) * count, cudaMemcpyDeviceToHost,
+                                  h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? PA_OK : cuda_fail(e, "reading the LU factors");
+}
+
+static pa_status upload_tri(pa_ctx* h, const TriHost& t, TriSys* out) {
+  int32_t *rp, *ci, *order, *lvl;
+  double *va, *diag;
+  pa_status st;
+  if ((st = upload(h, t.rp, &rp, "LU factor")) || (st = upload(h, t.ci, &ci, "LU factor")) ||
+      (st = upload(h, t.va, &va, "LU factor")) || (st = upload(h, t.diag, &diag, "LU factor")) ||
+      (st = upload(h, t.order, &order, "LU levels")) || (st = upload(h, t.lvl, &lvl, "LU levels")))
+    return st;
+  *out = TriSys{(int32_t)t.lvl.size() - 1, rp, ci, va, diag, order, lvl};
+  return PA_OK;
+}
+
+static bool is_permutation(const std::vector<int32_t>& p, int32_t n) {
+  std::vector<char> seen((size_t)n, 0);
+  for (int32_t v : p) {
+    if (v < 0 || v >= n || seen[v]) return false;
+    seen[v] = 1;
+  }
+  return true;
+}
+
+extern "C" pa_status pa_attach_lu(pa_handle h, const int32_t* l_row_ptr, const int32_t* l_col,
+                                  const double* l_val, const int32_t* u_row_ptr,
+                                  const int32_t* u_col, const double* u_val, const int32_t* p,
+                                  const int32_t* q, int ptr_kind) {
+  g_err.clear();
+  if (!h || !l_row_ptr || !u_row_ptr) return fail(PA_ERR_INVALID_ARG, "NULL handle or row_ptr");
+  if (h->n_rows != h->n_cols)
+    return fail(PA_ERR_NOT_SQUARE, "the LU route needs a square matrix (%d x %d)", h->n_rows, h->n_cols);
+  if (ptr_kind != PA_HOST && ptr_kind != PA_DEVICE)
+    return fail(PA_ERR_INVALID_ARG, "ptr_kind must be PA_HOST or PA_DEVICE");
+  const int32_t n = h->n_rows;
+  pa_status st;
+  std::vector<int32_t> lrp, urp, lci, uci, pp, qq;
+  std::vector<double> lva, uva;
+  if ((st = to_host(h, l_row_ptr, (size_t)n + 1, ptr_kind, &lrp)) ||
+      (st = to_host(h, u_row_ptr, (size_t)n + 1, ptr_kind, &urp)))
+    return st;
+  for (const auto* rp : {&lrp, &urp}) {
+    if ((*rp)[0] != 0) return fail(PA_ERR_INVALID_ARG, "factor row_ptr[0] != 0");
+    for (int32_t i = 0; i < n; ++i)
+      if ((*rp)[i + 1] < (*rp)[i]) return fail(PA_ERR_INVALID_ARG, "factor row_ptr decreases");
+  }
+  if ((lrp[n] > 0 && (!l_col || !l_val)) || (urp[n] > 0 && (!u_col || !u_val)))
+    return fail(PA_ERR_INVALID_ARG, "NULL factor arrays");
+  if ((st = to_host(h, l_col, (size_t)lrp[n], ptr_kind, &lci)) ||
+      (st = to_host(h, l_val, (size_t)lrp[n], ptr_kind, &lva)) ||
+      (st = to_host(h, u_col, (size_t)urp[n], ptr_kind, &uci)) ||
+      (st = to_host(h, u_val, (size_t)urp[n], ptr_kind, &uva)) ||
+      (p && (st = to_host(h, p, (size_t)n, ptr_kind, &pp))) ||
+      (q && (st = to_host(h, q, (size_t)n, ptr_kind, &qq))))
+    return st;
+  if ((p && !is_permutation(pp, n)) || (q && !is_permutation(qq, n)))
+    return fail(PA_ERR_INVALID_ARG, "p or q is not a permutation of 0..n-1");
+  // the four systems: L t = w, U u = t, U^T a = u (rows of U^T: increasing
+  // source row), L^T c = a (rows of L^T: decreasing source row, the order in
+  // which back substitution meets them)
+  std::vector<int32_t> utrp, utci, ltrp, ltci;
+  std::vector<double> utva, ltva;
+  csr_transpose_host(n, urp.data(), uci.data(), uva.data(), false, &utrp, &utci, &utva);
+  csr_transpose_host(n, lrp.data(), lci.data(), lva.data(), true, &ltrp, &ltci, &ltva);
+  TriHost tl, tu, tut, tlt;
+  std::string why;
+  if (!(why = tri_analyse(n, lrp.data(), lci.data(), lva.data(), true, &tl)).empty())
+    return fail(PA_ERR_INVALID_ARG, "L: %s", why.c_str());
+  if (!(why = tri_analyse(n, urp.data(), uci.data(), uva.data(), false, &tu)).empty())
+    return fail(PA_ERR_INVALID_ARG, "U: %s", why.c_str());
+  if (!(why = tri_analyse(n, utrp.data(), utci.data(), utva.data(), true, &tut)).empty())
+    return fail(PA_ERR_INVALID_ARG, "U^T: %s", why.c_str());
+  if (!(why = tri_analyse(n, ltrp.data(), ltci.data(), ltva.data(), false, &tlt)).empty())
+    return fail(PA_ERR_INVALID_ARG, "L^T: %s", why.c_str());
+  // q only relabels u: ||r|| = ||Q u|| = ||u|| and s needs Q^T r = u, so the
+  // iteration never applies it (it is checked above for the caller's sake)
+  free_lu(h);
+  if ((st = upload_tri(h, tl, &h->lu_sys[0])) || (st = upload_tri(h, tu, &h->lu_sys[1])) ||
+      (st = upload_tri(h, tut, &h->lu_sys[2])) || (st = upload_tri(h, tlt, &h->lu_sys[3])) ||
+      (p && (st = upload(h, pp, &h->lu_p, "LU permutation"))))
+    return (free_lu(h), st);
+  if (!h->xmin_lu &&
+      ((st = alloc_n(h, &h->xmin_lu, (size_t)n, "x_min")) ||
+       (st = alloc_n(h, &h->lu_w, (size_t)n, "LU vectors")) ||
+       (st = alloc_n(h, &h->lu_t, (size_t)n, "LU vectors")) ||
+       (st = alloc_n(h, &h->lu_u, (size_t)n, "LU vectors")) ||
+       (st = alloc_n(h, &h->lu_a, (size_t)n, "LU vectors")) ||
+       (st = alloc_n(h, &h->lu_c, (size_t)n, "LU vectors"))))
+    return (free_lu(h), st);
+  h->have_lu = true;
+  return PA_OK;
+}
+
+// Algorithm 1 on A^{-1} from x0 (device, source order, n entries); x_last
+// stays in h->dx's sibling buffer X0.  sigma_min(A) = 1 / ||A^{-1} x_min||.
+static pa_status lu_run(pa_ctx* h, const double* x0, int iters, double lr, double b1, double b2,
+                        double eps, double* L_trace_dev, double* x_trace_dev, int n_trace,
+                        RunState* out) {
+  if (!h->have_lu) return fail(PA_ERR_INVALID_ARG, "no LU factors attached (pa_attach_lu)");
+  pa_status st;
+  if ((st = ensure_bias(h, iters, lr, b1, b2, eps))) return st;
+  const size_t n = (size_t)h->n_cols;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(h->X0, x0, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream)) ||
+      (e = cudaMemcpyAsync(h->xmin_lu, x0, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream)) ||
+      (e = cudaMemsetAsync(h->m, 0, sizeof(double) * n, h->stream)) ||
+      (e = cudaMemsetAsync(h->v, 0, sizeof(double) * n, h->stream)) ||
+      (e = cudaMemsetAsync(h->st, 0, sizeof(RunState), h->stream)))
+    return cuda_fail(e, "preparing the LU-route run");
+  LuParams p{};
+  p.n = h->n_rows;
+  p.L = h->lu_sys[0];
+  p.U = h->lu_sys[1];
+  p.Ut = h->lu_sys[2];
+  p.Lt = h->lu_sys[3];
+  p.p = h->lu_p;
+  p.x = h->X0;
+  p.xmin = h->xmin_lu;
+  p.m = h->m;
+  p.v = h->v;
+  p.dx = h->dx;
+  p.w = h->lu_w;
+  p.t = h->lu_t;
+  p.u = h->lu_u;
+  p.a = h->lu_a;
+  p.c = h->lu_c;
+  p.bias = h->bias;
+  p.L_trace = L_trace_dev;
+  p.x_trace = x_trace_dev;
+  p.n_trace = n_trace;
+  p.st = h->st;
+  p.iters = iters;
+  p.t0 = 0;
+  p.beta1 = b1;
+  p.beta2 = b2;
+  p.smem_mode = lu_smem_bytes(p, 2) ? 2 : (lu_smem_bytes(p, 1) ? 1 : 0);
+  if (!h->lu_params && (st = alloc_n(h, &h->lu_params, 1, "LU run parameters"))) return st;
+  if ((e = cudaMemcpyAsync(h->lu_params, &p, sizeof(LuParams), cudaMemcpyHostToDevice, h->stream)) ||
+      (e = cudaStreamSynchronize(h->stream)) ||  // p lives on this stack frame
+      (e = launch_lu_iter(h->lu_params, 1, lu_smem_bytes(p, p.smem_mode), h->stream, &h->launches)) ||
+      (e = cudaMemcpyAsync(out, h->st, sizeof(RunState), cudaMemcpyDeviceToHost, h->stream)) ||
+      (e = cudaStreamSynchronize(h->stream)))
+    return cuda_fail(e, "running the LU route");
+  if ((st = status_error(out))) return st;
+  const double sig_inv = out->sigma;  // ||A^{-1} x_min|| / ||x_min||
+  out->sigma = 1.0 / sig_inv;
+  h->sigma_min = out->sigma;
+  h->have_min = true;
+  h->have_min_lu = true;
+  return (pa_status)out->status;
+}
+
+// pa_run for PA_SIGMA_MIN_LU: everything in source order, no permutations.
+static pa_status run_lu_traced(pa_ctx* h, int iters, double lr, double b1, double b2, double eps,
+                               const double* x_init, int x_kind, double* x_min, double* x_last,
+                               double* info, double* L_trace, double* x_trace, int n_trace,
+                               double* sigma) {
+  const size_t n = (size_t)h->n_cols;
+  cudaError_t e = cudaMemcpyAsync(h->Xinit, x_init, sizeof(double) * n,
+                                  x_kind == PA_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                  h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "copying x_init");
+  pa_status st;
+  double *Ld = nullptr, *Xd = nullptr;
+  if (L_trace && iters > 0 && (st = alloc_n(h, &Ld, (size_t)iters, "L trace"))) return st;
+  if (x_trace && n_trace > 0 && (st = alloc_n(h, &Xd, (size_t)n_trace * n, "x trace"))) {
+    if (Ld) dev_free(h, Ld);
+    return st;
+  }
+  RunState rs{};
+  pa_status rst = lu_run(h, h->Xinit, iters, lr, b1, b2, eps, Ld, Xd, x_trace ? n_trace : 0, &rs);
+  if (rst >= 0) {
+    if (x_min) e = cudaMemcpyAsync(x_min, h->xmin_lu, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && x_last)
+      e = cudaMemcpyAsync(x_last, h->X0, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && Ld)
+      e = cudaMemcpyAsync(L_trace, Ld, sizeof(double) * iters, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && Xd)
+      e = cudaMemcpyAsync(x_trace, Xd, sizeof(double) * n_trace * n, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) rst = cuda_fail(e, "reading results");
+    if (rst >= 0) {
+      if (info) {
+        info[0] = rs.L_min;
+        info[1] = rs.t_min;
+        info[2] = rs.L_last;
+        info[3] = rs.iters_run;
+      }
+      if (sigma) *sigma = rs.sigma;
+    }
+  }
+  if (Ld) dev_free(h, Ld);
+  if (Xd) dev_free(h, Xd);
+  return rst;
+}
+
 extern "C" pa_status pa_run(pa_handle h, pa_mode mode, int iters, double lr, double beta1,
                             double beta2, double eps, const double* x_init, int x_kind,
                             double* x_min, double* x_last, double* info, double* L_trace,
                             double* x_trace, int n_trace, double* sigma) {
   g_err.clear();
   if (!h) return fail(PA_ERR_INVALID_ARG, "NULL handle");
-  if (mode != PA_SIGMA_MAX && mode != PA_SIGMA_MIN)
-    return fail(PA_ERR_INVALID_ARG, "pa_run takes PA_SIGMA_MAX or PA_SIGMA_MIN");
+  if (mode != PA_SIGMA_MAX && mode != PA_SIGMA_MIN && mode != PA_SIGMA_MIN_LU)
+    return fail(PA_ERR_INVALID_ARG, "pa_run takes PA_SIGMA_MAX, PA_SIGMA_MIN or PA_SIGMA_MIN_LU");
   if (!x_init) return fail(PA_ERR_INVALID_ARG, "x_init is NULL");
   if (x_kind != PA_HOST && x_kind != PA_DEVICE) return fail(PA_ERR_INVALID_ARG, "bad x_kind");
   if (n_trace < 0 || n_trace > iters) return fail(PA_ERR_INVALID_ARG, "n_trace must lie in [0, iters]");
   pa_status st;
   if ((st = check_hyper(iters, lr, beta1, beta2, eps)) || (st = ensure_run_buffers(h))) return st;
   const size_t n = (size_t)h->n_cols;
+  if (mode == PA_SIGMA_MIN_LU) return run_lu_traced(h, iters, lr, beta1, beta2, eps, x_init, x_kind,
+                                                    x_min, x_last, info, L_trace, x_trace, n_trace,
+                                                    sigma);
   // x_init arrives in source order; the kernels work in the column order Q
   cudaError_t e = cudaMemcpyAsync(h->dx, x_init, sizeof(double) * n,
                                   x_kind == PA_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
@@ -845,8 +1088,11 @@ extern "C" pa_status pa_estimate(pa_handle h, pa_mode mode, int iters, double lr
                                  double* sigma_min, double* kappa) {
   g_err.clear();
   if (!h) return fail(PA_ERR_INVALID_ARG, "NULL handle");
-  if (mode != PA_SIGMA_MAX && mode != PA_SIGMA_MIN && mode != PA_BOTH)
+  if (mode != PA_SIGMA_MAX && mode != PA_SIGMA_MIN && mode != PA_BOTH &&
+      mode != PA_SIGMA_MIN_LU && mode != PA_BOTH_LU)
     return fail(PA_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
+  if ((mode & PA_SIGMA_MIN_LU) && !h->have_lu)
+    return fail(PA_ERR_INVALID_ARG, "no LU factors attached (pa_attach_lu)");
   pa_status st;
   if ((st = check_hyper(iters, lr, beta1, beta2, eps)) || (st = ensure_run_buffers(h))) return st;
   if ((mode & PA_SIGMA_MIN) && h->n_rows < h->n_cols)
@@ -856,9 +1102,15 @@ extern "C" pa_status pa_estimate(pa_handle h, pa_mode mode, int iters, double lr
   if (e != cudaSuccess) return cuda_fail(e, "building the start vector");
   pa_status worst = PA_OK;
   RunState rs{};
-  for (int md : {PA_SIGMA_MAX, PA_SIGMA_MIN}) {
+  for (int md : {PA_SIGMA_MAX, PA_SIGMA_MIN, PA_SIGMA_MIN_LU}) {
     if (!(mode & md)) continue;
-    st = run_one(h, (pa_mode)md, iters, lr, beta1, beta2, eps, nullptr, nullptr, 0, &rs);
+    if (md == PA_SIGMA_MIN_LU) {  // the same start vector, in source order
+      if ((e = launch_unpermute(h->n_cols, 1, h->sq.pos, h->Xinit, h->dx, h->stream, &h->launches)))
+        return cuda_fail(e, "building the start vector");
+      st = lu_run(h, h->dx, iters, lr, beta1, beta2, eps, nullptr, nullptr, 0, &rs);
+    } else {
+      st = run_one(h, (pa_mode)md, iters, lr, beta1, beta2, eps, nullptr, nullptr, 0, &rs);
+    }
     if (st < 0) return st;
     if (st > worst) worst = st;
   }
@@ -876,10 +1128,13 @@ extern "C" pa_status pa_estimate(pa_handle h, pa_mode mode, int iters, double lr
 extern "C" pa_status pa_get_vector(pa_handle h, pa_mode which, double* x_min_host) {
   g_err.clear();
   if (!h || !x_min_host) return fail(PA_ERR_INVALID_ARG, "NULL argument");
-  if (which != PA_SIGMA_MAX && which != PA_SIGMA_MIN) return fail(PA_ERR_INVALID_ARG, "bad mode");
-  if ((which == PA_SIGMA_MAX && !h->have_max) || (which == PA_SIGMA_MIN && !h->have_min))
+  if (which != PA_SIGMA_MAX && which != PA_SIGMA_MIN && which != PA_SIGMA_MIN_LU)
+    return fail(PA_ERR_INVALID_ARG, "bad mode");
+  if ((which == PA_SIGMA_MAX && !h->have_max) || (which == PA_SIGMA_MIN && !h->have_min_direct) ||
+      (which == PA_SIGMA_MIN_LU && !h->have_min_lu))
     return fail(PA_ERR_INVALID_ARG, "no run of that mode yet");
-  double* src = which == PA_SIGMA_MAX ? h->xmin_max : h->xmin_min;
+  double* src = which == PA_SIGMA_MAX ? h->xmin_max
+                                      : (which == PA_SIGMA_MIN ? h->xmin_min : h->xmin_lu);
   cudaError_t e = cudaMemcpyAsync(x_min_host, src, sizeof(double) * h->n_cols,
                                   cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -1275,6 +1530,95 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
 static thread_local int g_last_batch_graph = 0;
 extern "C" int pa_last_batch_graph(void) { return g_last_batch_graph; }
 
+// sigma_min of every (matrix, restart) item through the matrices' attached LU
+// factors (Algorithm 2): one CTA per item runs k_lu_iter on its own vectors,
+// from the start vector of the same seed the SpMM engine gives that item (in
+// source order).  Fills out[item][1] (and [2] when sigma_max ran).
+static pa_status batched_lu(const pa_handle* hs, int n_mat, int k_restarts, int iters, double lr,
+                            double b1, double b2, double eps, uint64_t seed, bool have_max,
+                            double* out, pa_status* item_status) {
+  pa_ctx* h0 = hs[0];
+  const cudaStream_t s = h0->stream;
+  BatchScratch sc{h0, {}};
+  const int n_items = n_mat * k_restarts;
+  pa_status st;
+  cudaError_t e;
+  // bias corrections, shared by the items
+  std::vector<double2> tab((size_t)std::max(iters, 1));
+  for (int t = 1; t <= iters; ++t) {
+    const double r2 = sqrt(1.0 - pow(b2, (double)t));
+    tab[t - 1] = make_double2(lr * r2 / (1.0 - pow(b1, (double)t)), eps * r2);
+  }
+  double2* bias = nullptr;
+  RunState* states = nullptr;
+  LuParams* items_dev = nullptr;
+  int32_t nmax = 0;
+  for (int i = 0; i < n_mat; ++i) nmax = std::max(nmax, hs[i]->n_rows);
+  double* blockpart = nullptr;
+  if ((st = sc.get(&bias, tab.size(), "bias table")) ||
+      (st = sc.get(&states, (size_t)n_items, "run states")) ||
+      (st = sc.get(&items_dev, (size_t)n_items, "LU items")) ||
+      (st = sc.get(&blockpart, (size_t)start_vector_blocks(nmax) + 1, "start vector partials")))
+    return st;
+  if ((e = cudaMemcpyAsync(bias, tab.data(), sizeof(double2) * tab.size(), cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemsetAsync(states, 0, sizeof(RunState) * n_items, s)))
+    return cuda_fail(e, "preparing the LU items");
+  std::vector<LuParams> items((size_t)n_items);
+  size_t smem = 0;
+  for (int i = 0; i < n_mat; ++i) {
+    pa_ctx* hi = hs[i];
+    const size_t n = (size_t)hi->n_rows;
+    for (int r = 0; r < k_restarts; ++r) {
+      const int it = i * k_restarts + r;
+      double* buf = nullptr;
+      if ((st = sc.get(&buf, 10 * n, "LU item vectors"))) return st;
+      LuParams& p = items[it];
+      p.n = hi->n_rows;
+      p.L = hi->lu_sys[0];
+      p.U = hi->lu_sys[1];
+      p.Ut = hi->lu_sys[2];
+      p.Lt = hi->lu_sys[3];
+      p.p = hi->lu_p;
+      p.x = buf;
+      p.xmin = buf + n;
+      p.m = buf + 2 * n;
+      p.v = buf + 3 * n;
+      p.dx = buf + 4 * n;
+      p.w = buf + 5 * n;
+      p.t = buf + 6 * n;
+      p.u = buf + 7 * n;
+      p.a = buf + 8 * n;
+      p.c = buf + 9 * n;
+      p.bias = bias;
+      p.st = states + it;
+      p.iters = iters;
+      p.beta1 = b1;
+      p.beta2 = b2;
+      p.smem_mode = lu_smem_bytes(p, 2) ? 2 : (lu_smem_bytes(p, 1) ? 1 : 0);
+      smem = std::max(smem, lu_smem_bytes(p, p.smem_mode));
+      // item (i, r): SplitMix64 output i * k_restarts + r of `seed`, source order
+      const uint64_t s_ir = splitmix64_at(seed, (uint64_t)it);
+      if ((e = launch_start_vector(hi->n_rows, s_ir, nullptr, p.x, blockpart, s, &h0->launches)) ||
+          (e = cudaMemcpyAsync(p.xmin, p.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s)) ||
+          (e = cudaMemsetAsync(p.m, 0, sizeof(double) * 2 * n, s)))
+        return cuda_fail(e, "preparing the LU items");
+    }
+  }
+  std::vector<RunState> rs((size_t)n_items);
+  if ((e = cudaMemcpyAsync(items_dev, items.data(), sizeof(LuParams) * n_items, cudaMemcpyHostToDevice, s)) ||
+      (e = launch_lu_iter(items_dev, n_items, smem, s, &h0->launches)) ||
+      (e = cudaMemcpyAsync(rs.data(), states, sizeof(RunState) * n_items, cudaMemcpyDeviceToHost, s)) ||
+      (e = cudaStreamSynchronize(s)))
+    return cuda_fail(e, "running the batched LU route");
+  for (int it = 0; it < n_items; ++it) {
+    double* o = out + (size_t)it * 3;
+    o[1] = rs[it].status == PA_OK ? 1.0 / rs[it].sigma : NAN;
+    o[2] = have_max ? o[0] / o[1] : NAN;
+    if (item_status && rs[it].status != PA_OK) item_status[it] = (pa_status)rs[it].status;
+  }
+  return PA_OK;
+}
+
 extern "C" pa_status pa_estimate_batched(int n_mat, const pa_handle* handles, pa_mode mode,
                                          int k_restarts, const int* iters, double lr, double beta1,
                                          double beta2, double eps, uint64_t seed, double* out,
@@ -1282,10 +1626,16 @@ extern "C" pa_status pa_estimate_batched(int n_mat, const pa_handle* handles, pa
   g_err.clear();
   if (n_mat <= 0 || !handles || !iters || !out || k_restarts <= 0)
     return fail(PA_ERR_INVALID_ARG, "invalid batched arguments");
-  if (mode != PA_SIGMA_MAX && mode != PA_SIGMA_MIN && mode != PA_BOTH)
+  if (mode != PA_SIGMA_MAX && mode != PA_SIGMA_MIN && mode != PA_BOTH &&
+      mode != PA_SIGMA_MIN_LU && mode != PA_BOTH_LU)
     return fail(PA_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
   pa_status st;
   if ((st = check_hyper(std::min(iters[0], iters[1]), lr, beta1, beta2, eps))) return st;
+  const bool lu = (mode & PA_SIGMA_MIN_LU) != 0;
+  for (int i = 0; lu && i < n_mat; ++i)
+    if (!handles[i] || !handles[i]->have_lu)
+      return fail(PA_ERR_INVALID_ARG, "handle %d has no LU factors attached", i);
+  const pa_mode spmm_mode = (pa_mode)(mode & PA_BOTH);
   for (int i = 0; i < n_mat; ++i) {
     const pa_ctx* hi = handles[i];
     if (!hi) return fail(PA_ERR_INVALID_ARG, "handle %d is NULL", i);
@@ -1296,6 +1646,13 @@ extern "C" pa_status pa_estimate_batched(int n_mat, const pa_handle* handles, pa
     if ((mode & PA_SIGMA_MIN) && hi->n_rows < hi->n_cols)
       return fail(PA_ERR_NOT_SQUARE, "sigma_min needs n_rows >= n_cols (handle %d)", i);
   }
+  if (item_status)
+    for (int it = 0; it < n_mat * k_restarts; ++it) item_status[it] = PA_OK;
+  if (spmm_mode == 0) {  // PA_SIGMA_MIN_LU alone
+    for (int it = 0; it < n_mat * k_restarts; ++it) out[(size_t)it * 3] = NAN;
+    return batched_lu(handles, n_mat, k_restarts, iters[1], lr, beta1, beta2, eps, seed, false, out,
+                      item_status);
+  }
   bool captured = false;
   for (int r0 = 0; r0 < k_restarts; r0 += 8) {
     const int k_used = std::min(8, k_restarts - r0);
@@ -1305,11 +1662,14 @@ extern "C" pa_status pa_estimate_batched(int n_mat, const pa_handle* handles, pa
     const int wave = std::max(1, Gmax / 2);
     for (int i0 = 0; i0 < n_mat; i0 += wave) {
       const int m = std::min(wave, n_mat - i0);
-      if ((st = batched_wave(handles, i0, m, r0, k_used, K, k_restarts, mode, iters, lr, beta1,
-                             beta2, eps, seed, out, item_status, &captured)))
+      if ((st = batched_wave(handles, i0, m, r0, k_used, K, k_restarts, spmm_mode, iters, lr,
+                             beta1, beta2, eps, seed, out, item_status, &captured)))
         return st;
       g_last_batch_graph = captured ? 1 : 0;
     }
   }
+  if (lu)
+    return batched_lu(handles, n_mat, k_restarts, iters[1], lr, beta1, beta2, eps, seed, true, out,
+                      item_status);
   return PA_OK;
 }

@@ -3,6 +3,9 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
 #include <stdint.h>
 
 #include "pa.h"
@@ -228,6 +231,58 @@ cudaError_t launch_equilibrate(int32_t n_rows, int32_t n_cols, const int32_t* rp
                                const double* va, const int32_t* rpt, const int32_t* cit,
                                const double* vat, double* d_row, double* d_col, cudaStream_t s,
                                int64_t* launches);
+// ---- Algorithm 2 (sigma_min through ||A^{-1}|| with given LU factors) ----
+// One triangular system in level-scheduled form, stored in level order:
+// position k holds row order[k]; positions lvl[l] .. lvl[l+1] are the rows of
+// level l, which depend only on rows of earlier levels; the off-diagonal
+// entries of position k are ci/va[rp[k] .. rp[k+1]) (a level's entries are
+// contiguous) and its diagonal is diag[k].
+struct TriSys {
+  int32_t nlev;
+  const int32_t* rp; const int32_t* ci; const double* va; const double* diag;
+  const int32_t* order; const int32_t* lvl;
+};
+// Algorithm 1 on B = A^{-1} = Q U^{-1} L^{-1} P, everything in source order.
+struct LuParams {
+  int32_t n;
+  TriSys L, U, Ut, Lt;       // L t = w, U u = t, U^T a = u, L^T c = a
+  const int32_t* p;          // [n] row i of P A is row p[i] of A (null = identity)
+  double* x; double* xmin;   // iterate, tracked maximiser of ||B x|| / ||x||
+  double* m; double* v; double* dx;
+  double* w; double* t; double* u; double* a; double* c;  // solve vectors
+  const double2* bias;       // as IterParams
+  double* L_trace; double* x_trace; int n_trace;
+  RunState* st;
+  int iters, t0;
+  double beta1, beta2;
+  int smem_mode;             // 0: all in global memory; 1: the five solve vectors
+                             // in shared memory; 2: also each system's lvl, rp, order
+};
+constexpr int kLuThreads = 512;
+constexpr size_t kLuSmemBudget = 200 * 1024;  // dynamic shared memory the LU kernel may use
+// Dynamic shared memory of a given mode (0 when the mode does not fit).
+size_t lu_smem_bytes(const LuParams& p, int mode);
+// Items (device array of n_items LuParams, each with its own vectors and run
+// state), one CTA each; smem = the dynamic shared memory of the launch, which
+// must cover lu_smem_bytes(item, item.smem_mode) of every item.
+cudaError_t launch_lu_iter(const LuParams* items_dev, int n_items, size_t smem, cudaStream_t s,
+                           int64_t* launches);
+// Host analysis for TriSys: checks triangularity and non-zero diagonals,
+// splits off the diagonal and computes the levels.  lower: row i depends on
+// columns j < i; else on j > i.  Returns an empty string or the reason the
+// factor is unusable.
+struct TriHost {
+  std::vector<int32_t> rp, ci, order, lvl;
+  std::vector<double> va, diag;
+};
+std::string tri_analyse(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
+                        bool lower, TriHost* out);
+// CSR of T^T; entries of each row in increasing (reverse = false) or
+// decreasing (reverse = true) order of their source row.
+void csr_transpose_host(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
+                        bool reverse, std::vector<int32_t>* trp, std::vector<int32_t>* tci,
+                        std::vector<double>* tva);
+
 // Residual norms of an approximate solution and the bounds of Theorems 1-4
 // into out[10] (device); part holds 3 * error_bound_blocks(max(n_rows,
 // n_cols)) doubles.

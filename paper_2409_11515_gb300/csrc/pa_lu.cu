@@ -1,0 +1,371 @@
+// pa_lu.cu -- sigma_min through ||A^{-1}||_2 with a given LU factorisation:
+// the paper's Algorithm 2 ("Compute Gradient for A^{-1}") inside Algorithm 1.
+//
+// With P A Q = L U, A^{-1} = Q U^{-1} L^{-1} P and A^{-T} = P^T L^{-T} U^{-T} Q^T.
+// Per iteration, for B = A^{-1}:
+//   r = B x        : w = P x, L t = w, U u = t (r = Q u, so ||r|| = ||u||)
+//   score          : L(x_{t-1}) = log||x|| - log||r|| against L_min
+//   s = B^T r      : U^T a = u, L^T c = a, s = P^T c
+//   grad           : x / ||x||^2 - s / ||r||^2   (Algorithm 2)
+//   Adam, tangent projection, update, normalisation as in Algorithm 1.
+// sigma_min(A) = 1 / sigma_max(B) = ||x_min|| / ||B x_min||.
+//
+// The four triangular solves are level-scheduled: the host sorts the rows of
+// each factor by level (a row's level is one more than the highest level of
+// the rows it depends on), and the solve walks the levels in order, the rows
+// of one level in parallel.  Sparse LU factors of 2D operators in fill-reducing
+// orders have long, thin level sets (hundreds of levels of a few rows for a
+// few thousand unknowns), so one CTA runs the whole iteration: a level then
+// costs one __syncthreads instead of a grid-wide barrier.  The factors are
+// stored in level order, so a level's entries are contiguous and are
+// prefetched into L1 two levels ahead; for small n the solve vectors, and
+// where they fit each system's level and row pointers and row order, live in
+// shared memory.  The kernel waits on nothing outside its CTA.
+#include <math.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "pa_device.cuh"
+#include "pa_internal.h"
+
+namespace pa {
+
+std::string tri_analyse(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
+                        bool lower, TriHost* out) {
+  out->rp.assign((size_t)n + 1, 0);
+  out->ci.clear();
+  out->va.clear();
+  out->diag.assign((size_t)n, 0.0);
+  std::vector<int32_t> level((size_t)n, 0);
+  for (int32_t i = 0; i < n; ++i) {
+    bool have_diag = false;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+      const int32_t j = ci[k];
+      if (j < 0 || j >= n) return "column index out of range in row " + std::to_string(i);
+      if (j == i) {
+        if (have_diag) return "two diagonal entries in row " + std::to_string(i);
+        have_diag = true;
+        out->diag[i] = va[k];
+      } else if ((lower && j > i) || (!lower && j < i)) {
+        return std::string(lower ? "entry above the diagonal" : "entry below the diagonal") +
+               " in row " + std::to_string(i);
+      }
+    }
+    if (!have_diag || out->diag[i] == 0.0 || !std::isfinite(out->diag[i]))
+      return "zero or missing diagonal in row " + std::to_string(i);
+  }
+  // levels: a forward solve visits rows upwards, a backward solve downwards
+  int32_t nlev = 0;
+  for (int32_t s = 0; s < n; ++s) {
+    const int32_t i = lower ? s : n - 1 - s;
+    int32_t lv = 0;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k)
+      if (ci[k] != i) lv = std::max(lv, level[ci[k]] + 1);
+    level[i] = lv;
+    nlev = std::max(nlev, lv + 1);
+  }
+  out->lvl.assign((size_t)nlev + 1, 0);
+  for (int32_t i = 0; i < n; ++i) ++out->lvl[level[i] + 1];
+  for (int32_t k = 0; k < nlev; ++k) out->lvl[k + 1] += out->lvl[k];
+  out->order.assign((size_t)n, 0);
+  std::vector<int32_t> cur(out->lvl.begin(), out->lvl.end() - 1);
+  for (int32_t i = 0; i < n; ++i) out->order[cur[level[i]]++] = i;
+  // rows in level order, each with its off-diagonal entries in stored order
+  std::vector<double> diag_row(out->diag);
+  for (int32_t k = 0; k < n; ++k) {
+    const int32_t i = out->order[k];
+    for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+      if (ci[e] == i) continue;
+      out->ci.push_back(ci[e]);
+      out->va.push_back(va[e]);
+    }
+    out->rp[k + 1] = (int32_t)out->ci.size();
+    out->diag[k] = diag_row[i];
+  }
+  return std::string();
+}
+
+void csr_transpose_host(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
+                        bool reverse, std::vector<int32_t>* trp, std::vector<int32_t>* tci,
+                        std::vector<double>* tva) {
+  trp->assign((size_t)n + 1, 0);
+  for (int32_t k = 0; k < rp[n]; ++k) ++(*trp)[ci[k] + 1];
+  for (int32_t j = 0; j < n; ++j) (*trp)[j + 1] += (*trp)[j];
+  tci->assign((size_t)rp[n], 0);
+  tva->assign((size_t)rp[n], 0.0);
+  std::vector<int32_t> cur(trp->begin(), trp->end() - 1);
+  for (int32_t s = 0; s < n; ++s) {
+    const int32_t i = reverse ? n - 1 - s : s;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+      const int32_t j = ci[k];
+      (*tci)[cur[j]] = i;
+      (*tva)[cur[j]] = va[k];
+      ++cur[j];
+    }
+  }
+}
+
+namespace {
+
+constexpr int kLuWarps = kLuThreads / 32;
+
+struct LuShared {
+  double scratch[2 * kLuThreads];
+  double ca, cb;      // g' = (1 - beta1) grad = ca x + cb s
+  double c, inv;      // projection coefficient and 1 / ||x'||
+  double q_keep;      // ||x||^2 of the current iterate
+  double L_min, L_last;
+  int brk, improved;
+  int t_min, iters_run, status;
+};
+
+// The solve vectors: in dynamic shared memory for small n, else global.
+struct LuVec {
+  double *w, *t, *u, *a, *c;
+};
+
+// Ask L1 for the diagonals, columns and values level `lev` reads (its
+// positions and entries are contiguous), so that they are on chip when the
+// solve reaches that level.  Every prefetched address lies inside its array.
+__device__ __forceinline__ void prefetch_range(const void* base, int bytes, int& l0) {
+  const char* b = reinterpret_cast<const char*>(base);
+  const int nl = (bytes + 127) / 128;
+  for (int l = (int)threadIdx.x - l0; l < nl; l += kLuThreads)
+    if (l >= 0) asm volatile("prefetch.global.L1 [%0];" ::"l"(b + 128 * l));
+  l0 += nl;  // the next range starts where this one's threads left off
+}
+
+__device__ __forceinline__ void prefetch_level(const TriSys& T, int lev) {
+  if (lev >= T.nlev) return;
+  const int k0 = T.lvl[lev], k1 = T.lvl[lev + 1];
+  const int e0 = T.rp[k0], e1 = T.rp[k1];
+  int l0 = 0;
+  prefetch_range(T.diag + k0, 8 * (k1 - k0), l0);
+  prefetch_range(T.ci + e0, 4 * (e1 - e0), l0);
+  prefetch_range(T.va + e0, 8 * (e1 - e0), l0);
+}
+
+// x = T^{-1} b for one level-scheduled triangular system (all threads): a
+// warp per row, its lanes striding the row's entries, then a fixed-order
+// butterfly sum.  (The rounding order differs from plain substitution; the
+// route's iterates are insensitive to it at the 1e-15 level.)
+__device__ __forceinline__ void tri_solve(const TriSys& T, const double* b, double* x) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  prefetch_level(T, 0);
+  prefetch_level(T, 1);
+  for (int lev = 0; lev < T.nlev; ++lev) {
+    prefetch_level(T, lev + 2);
+    const int k1 = T.lvl[lev + 1];
+    for (int k = T.lvl[lev] + warp; k < k1; k += kLuWarps) {
+      const int e1 = T.rp[k + 1];
+      double acc = 0.0;
+      for (int e = T.rp[k] + lane; e < e1; e += 32) acc = fma(T.va[e], x[T.ci[e]], acc);
+      acc = warp_sum(acc);
+      if (lane == 0) {
+        const int i = T.order[k];
+        x[i] = (b[i] - acc) / T.diag[k];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// u = Q^T A^{-1} x: w = P x, L t = w, U u = t.
+__device__ __forceinline__ void apply_inv(const LuParams& p, const LuVec& V, const double* x) {
+  for (int i = threadIdx.x; i < p.n; i += kLuThreads) V.w[i] = x[p.p ? p.p[i] : i];
+  __syncthreads();
+  tri_solve(p.L, V.w, V.t);
+  tri_solve(p.U, V.t, V.u);
+}
+
+// Copy a system's level pointers, row pointers and row order into shared
+// memory at `at` (int32 words) and point T there.
+__device__ __forceinline__ void stage_meta(TriSys& T, int n, int32_t* at) {
+  int32_t* lvl = at;
+  int32_t* rp = lvl + T.nlev + 1;
+  int32_t* order = rp + n + 1;
+  for (int i = threadIdx.x; i <= T.nlev; i += kLuThreads) lvl[i] = T.lvl[i];
+  for (int i = threadIdx.x; i <= n; i += kLuThreads) rp[i] = T.rp[i];
+  for (int i = threadIdx.x; i < n; i += kLuThreads) order[i] = T.order[i];
+  T.lvl = lvl;
+  T.rp = rp;
+  T.order = order;
+}
+
+// One CTA per item: item b runs Algorithm 1 on the inverse of its own matrix
+// from its own start vector, independently of the other CTAs.
+__global__ void __launch_bounds__(kLuThreads, 1) k_lu_iter(const LuParams* __restrict__ items) {
+  LuParams p = items[blockIdx.x];
+  __shared__ LuShared sh;
+  extern __shared__ double dyn[];
+  const int n = p.n, tid = threadIdx.x;
+  LuVec V;
+  if (p.smem_mode >= 1) {
+    V = LuVec{dyn, dyn + n, dyn + 2 * n, dyn + 3 * n, dyn + 4 * n};
+  } else {
+    V = LuVec{p.w, p.t, p.u, p.a, p.c};
+  }
+  if (p.smem_mode == 2) {
+    int32_t* at = reinterpret_cast<int32_t*>(dyn + 5 * n);
+    TriSys* sys[4] = {&p.L, &p.U, &p.Ut, &p.Lt};
+    for (TriSys* T : sys) {
+      const int words = T->nlev + 1 + 2 * n + 1;
+      stage_meta(*T, n, at);
+      at += words;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    sh.L_min = INFINITY;
+    sh.L_last = NAN;
+    sh.t_min = 0;
+    sh.iters_run = 0;
+    sh.status = PA_OK;
+  }
+  __syncthreads();
+  double* x = p.x;
+  for (int t = 1;; ++t) {
+    // ---- r = A^{-1} x (Algorithm 2: solve L U r = x), ||r||^2, ||x||^2
+    apply_inv(p, V, x);
+    {
+      double v[2] = {0.0, 0.0};
+      for (int i = tid; i < n; i += kLuThreads) {
+        v[0] = fma(V.u[i], V.u[i], v[0]);
+        v[1] = fma(x[i], x[i], v[1]);
+      }
+      block_sum_to0<2>(v, sh.scratch);
+      if (tid == 0) {
+        const double rr = v[0], q2 = v[1];
+        int brk = 0, improved = 0;
+        if (!isfinite(rr) || !isfinite(q2) || rr == 0.0) {
+          sh.status = PA_ERR_NONFINITE;
+          brk = 1;
+        } else {
+          if (t > 1) {  // score x_{t-1}: L = log||x|| - log||A^{-1} x||
+            const double L = log(sqrt(q2)) - log(sqrt(rr));
+            sh.L_last = L;
+            if (p.L_trace) p.L_trace[t - 2] = L;
+            if (L < sh.L_min) {
+              sh.L_min = L;
+              sh.t_min = t - 1;
+              improved = 1;
+            }
+          }
+          if (t == p.iters + 1) brk = 1;
+        }
+        const double omb1 = 1.0 - p.beta1;
+        sh.ca = omb1 / q2;
+        sh.cb = -omb1 / rr;
+        sh.q_keep = q2;
+        sh.brk = brk;
+        sh.improved = improved;
+      }
+      __syncthreads();
+    }
+    if (sh.improved) {
+      for (int i = tid; i < n; i += kLuThreads) p.xmin[i] = x[i];
+      __syncthreads();  // the final sigma reads x_min across threads
+    }
+    if (sh.brk) break;
+
+    // ---- s = A^{-T} r (Algorithm 2: solve U^T L^T s = r), into w
+    tri_solve(p.Ut, V.u, V.a);
+    tri_solve(p.Lt, V.a, V.c);
+    for (int i = tid; i < n; i += kLuThreads) V.w[p.p ? p.p[i] : i] = V.c[i];
+    __syncthreads();
+
+    // ---- gradient x/||x||^2 - s/||r||^2, Adam, partials x.dx and dx.dx
+    {
+      const double ca = sh.ca, cb = sh.cb;
+      const double2 bc = p.bias[p.t0 + t - 1];
+      const double b1 = p.beta1, b2 = p.beta2;
+      const double w2 = (1.0 - b2) / ((1.0 - b1) * (1.0 - b1));
+      double v[2] = {0.0, 0.0};
+      for (int j = tid; j < n; j += kLuThreads) {
+        const double xj = x[j];
+        const double g = fma(ca, xj, cb * V.w[j]);
+        const double mj = fma(b1, p.m[j], g);
+        const double vj = fma(b2, p.v[j], w2 * (g * g));
+        p.m[j] = mj;
+        p.v[j] = vj;
+        const double d = (bc.x * mj) / (sqrt(vj) + bc.y);
+        p.dx[j] = d;
+        v[0] = fma(xj, d, v[0]);
+        v[1] = fma(d, d, v[1]);
+      }
+      block_sum_to0<2>(v, sh.scratch);
+      if (tid == 0) {
+        const double p1 = v[0], p2 = v[1];
+        if (!isfinite(p1) || !isfinite(p2)) {
+          sh.status = PA_ERR_NONFINITE;
+          sh.brk = 1;
+        }
+        const double a1c = 1.0 + p1;
+        // ||(1+c) x - dx||^2 = (1+c)^2 q - 2 (1+c) p1 + p2, c = x.dx
+        const double nrm2 = fma(a1c * a1c, sh.q_keep, fma(-2.0 * a1c, p1, p2));
+        sh.c = p1;
+        sh.inv = 1.0 / sqrt(nrm2);
+      }
+      __syncthreads();
+    }
+    if (sh.brk) break;
+
+    // ---- x_t = ((1 + c) x - dx) / ||.||: projection, update, normalisation
+    {
+      const double a1c = 1.0 + sh.c, inv = sh.inv;
+      double* tr = (p.x_trace && t <= p.n_trace) ? p.x_trace + (size_t)(t - 1) * n : nullptr;
+      for (int j = tid; j < n; j += kLuThreads) {
+        const double xn = fma(a1c, x[j], -p.dx[j]) * inv;
+        x[j] = xn;
+        if (tr) tr[j] = xn;
+      }
+      if (tid == 0) sh.iters_run = t;
+      __syncthreads();
+    }
+  }
+
+  // ---- sigma_max(A^{-1}) = ||A^{-1} x_min|| / ||x_min||
+  apply_inv(p, V, p.xmin);
+  double v[2] = {0.0, 0.0};
+  for (int i = tid; i < n; i += kLuThreads) {
+    v[0] = fma(V.u[i], V.u[i], v[0]);
+    v[1] = fma(p.xmin[i], p.xmin[i], v[1]);
+  }
+  block_sum_to0<2>(v, sh.scratch);
+  if (tid == 0) {
+    RunState* st = p.st;
+    st->status = sh.status;
+    st->t_min = sh.t_min;
+    st->L_min = sh.L_min;
+    st->L_last = sh.L_last;
+    st->iters_run = sh.iters_run;
+    st->sigma = sqrt(v[0]) / sqrt(v[1]);
+  }
+}
+
+}  // namespace
+
+size_t lu_smem_bytes(const LuParams& p, int mode) {
+  if (mode == 0) return 0;
+  size_t b = sizeof(double) * 5 * (size_t)p.n;
+  if (mode == 2)
+    for (const TriSys* T : {&p.L, &p.U, &p.Ut, &p.Lt})
+      b += sizeof(int32_t) * ((size_t)T->nlev + 1 + 2 * (size_t)p.n + 1);
+  return b <= kLuSmemBudget ? b : 0;
+}
+
+cudaError_t launch_lu_iter(const LuParams* items_dev, int n_items, size_t smem, cudaStream_t s,
+                           int64_t* launches) {
+  if (smem > 0) {
+    cudaError_t e = cudaFuncSetAttribute(k_lu_iter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_lu_iter<<<n_items, kLuThreads, smem, s>>>(items_dev);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+}  // namespace pa

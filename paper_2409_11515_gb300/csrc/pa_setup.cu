@@ -483,7 +483,7 @@ __global__ void __launch_bounds__(kT) k_start_raw(int32_t n, uint64_t seed,
        i += (int64_t)gridDim.x * blockDim.x) {
     const double u = (double)(splitmix64_at(seed, (uint64_t)i) >> 11) * 0x1.0p-53;
     const double xi = 2.0 * u - 1.0;
-    x[pos[i]] = xi;
+    x[pos ? pos[i] : i] = xi;  // pos == null: source order
     q[0] = fma(xi, xi, q[0]);
   }
   block_sum_to0<1>(q, scratch);

@@ -21,7 +21,7 @@ import numpy as np
 _PKG = Path(__file__).resolve().parent
 LIB_PATH = _PKG / "_build" / "libpa.so"
 
-SIGMA_MAX, SIGMA_MIN, BOTH = 1, 2, 3
+SIGMA_MAX, SIGMA_MIN, BOTH, SIGMA_MIN_LU, BOTH_LU = 1, 2, 3, 4, 5
 HOST, DEVICE = 0, 1
 LOSS_LOGRATIO, LOSS_QUADRATIC = 0, 1
 FP64, MIXED = 0, 1
@@ -38,7 +38,7 @@ STATUS_NAMES = {0: "PA_OK", 1: "PA_WARN_SINGULAR", -1: "PA_ERR_INVALID_ARG",
 EXPORTS = ("pa_options_default", "pa_create", "pa_estimate", "pa_run", "pa_estimate_batched",
            "pa_get_vector", "pa_spmv", "pa_spmv_t", "pa_get_transpose", "pa_get_equilibration",
            "pa_kernel_launches", "pa_destroy", "pa_last_error", "pa_set_allocator",
-           "pa_last_run_profile", "pa_sigma_noalloc", "pa_last_batch_graph", "pa_error_bounds")
+           "pa_last_run_profile", "pa_sigma_noalloc", "pa_last_batch_graph", "pa_error_bounds", "pa_attach_lu")
 
 ERROR_BOUND_KEYS = ("residual_norm", "b_norm", "x_hat_norm", "thm1_lower", "thm1_upper",
                     "thm2_lower", "thm2_upper", "thm3_upper", "thm4_rounding", "singular")
@@ -109,6 +109,8 @@ def _declare(L):
     L.pa_get_transpose.argtypes = [vp, vp, vp, vp]
     L.pa_get_equilibration.restype = C.c_int
     L.pa_get_equilibration.argtypes = [vp, vp, vp]
+    L.pa_attach_lu.restype = C.c_int
+    L.pa_attach_lu.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, C.c_int]
     L.pa_error_bounds.restype = C.c_int
     L.pa_error_bounds.argtypes = [vp, vp, vp, C.c_int, d, d, d, vp]
     L.pa_last_run_profile.restype = C.c_int
@@ -293,6 +295,29 @@ class Handle:
         t = np.zeros((max(g.value, 1), 2))
         _check(load().pa_last_run_profile(self._h, C.byref(g), t.ctypes.data))
         return g.value, t[:g.value]
+
+    def attach_lu(self, L, U, p=None, q=None):
+        """pa_attach_lu: P A Q = L U (L lower, U upper triangular, CSR given as
+        synth.CSR / (row_ptr, col, val, n, n) on the host or as CUDA torch
+        tensors); p[i] = row of A that is row i of P A, q[j] = column of A
+        that is column j of A Q (None = identity)."""
+        i32, f64 = _dtypes()["i32"], _dtypes()["f64"]
+        keep = []
+
+        def arrs(T):
+            rp, ci, va = (T.row_ptr, T.col, T.val) if hasattr(T, "row_ptr") else T[:3]
+            out = [_ptr_and_kind(rp, i32), _ptr_and_kind(ci, i32), _ptr_and_kind(va, f64)]
+            keep.extend(out)
+            return out
+
+        Lp, Up = arrs(L), arrs(U)
+        pp = _ptr_and_kind(p, i32) if p is not None else (None, None, None)
+        qp = _ptr_and_kind(q, i32) if q is not None else (None, None, None)
+        kinds = {a[1] for a in Lp + Up} | {k for k in (pp[1], qp[1]) if k is not None}
+        if len(kinds) != 1:
+            raise ValueError("factors and permutations must all be host arrays or all CUDA tensors")
+        _check(load().pa_attach_lu(self._h, Lp[0][0], Lp[1][0], Lp[2][0], Up[0][0], Up[1][0],
+                                   Up[2][0], pp[0], qp[0], kinds.pop()))
 
     def error_bounds(self, x_hat, b, kappa: float = 0.0, norm_a: float = 0.0,
                      u: float = 0.0) -> dict:

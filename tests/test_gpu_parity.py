@@ -399,3 +399,32 @@ def test_autotune_rejects_negative():
     A = synth.laplacian_2d(6)
     with pytest.raises(pa.PAError):
         pa.create(A, autotune=-1)
+
+
+# ------------------------------------------ 1001 x 1001 (6M rows) checks ---
+
+@pytest.fixture(scope="module")
+def hydro1001():
+    return synth.hydro_operator(1001, n_incl=8, eta_lo=1e18, eta_hi=1e24, seed=4)
+
+
+@pytest.mark.parametrize("mode", [pa.SIGMA_MAX, pa.SIGMA_MIN])
+def test_6m_rows_first_iterates(hydro1001, mode):
+    """The 6,012,006-row operator: L_t for t <= 5 and x_5 against the oracle."""
+    A = hydro1001
+    T = 5
+    x0 = oracle.start_vector(A.n_cols, 1)
+    ro = oracle.projected_adam(A, mode, T, x_init=x0, trace_L=True, **HYPER)
+    with pa.create(A) as h:
+        rg = h.run(mode, T, x0, trace_L=True, **HYPER)
+    assert np.linalg.norm(rg["x_last"] - ro.x_last) <= 1e-10
+    Lo = ro.L_trace
+    assert np.max(np.abs(rg["L_trace"] - Lo) / np.maximum(1, np.abs(Lo))) <= 1e-10
+
+
+def test_6m_rows_equilibration_bit_exact(hydro1001):
+    A = hydro1001
+    dr, dc, _ = oracle.equilibrate_pow2(A)
+    with pa.create(A, precision=pa.MIXED) as h:
+        gr, gc = h.get_equilibration()
+    assert np.array_equal(gr, dr) and np.array_equal(gc, dc)
