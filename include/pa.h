@@ -108,10 +108,14 @@ typedef struct {
                        = iters / 10, 0 = none */
   int autotune;     /* > 0: after each of the first `autotune` runs of the
                        grid engine, re-split the slices among the CTAs at
-                       equal measured busy time (per-CTA timers of that run).
-                       The split sets the order of the reductions, so tuned
-                       runs are reproducible only for the same split; 0
-                       (default) keeps the fixed cost model. */
+                       equal measured busy time (per-CTA timers of that run);
+                       and when this handle is the first of a
+                       pa_estimate_batched call, time short trials of the
+                       batch with restart blocks of 8, 4 and 2 vectors and
+                       keep the fastest width (cached per k_restarts).
+                       Both choices set the order of reductions, so tuned
+                       runs are reproducible only for the same choice; 0
+                       (default) keeps the fixed cost model and width 8. */
 } pa_options;
 
 /* Fill *opt with the defaults above (LOGRATIO, FP64, no equilibration, AUTO

@@ -9,6 +9,8 @@
 
 #include <algorithm>
 #include <string>
+#include <chrono>
+#include <map>
 #include <vector>
 
 #include "pa_device.cuh"
@@ -110,6 +112,7 @@ struct pa_ctx {
   unsigned long long* cta_ns = nullptr;  // [2G] per-CTA busy time of the last run
   int last_G = 0;
   int tuned_rounds = 0;                  // partition re-splits done for h->G
+  std::map<int, int> batch_kb;           // tuned restart-block width per k (batched engine)
   double2* bias = nullptr;
   int bias_cap = 0;
   bool have_max = false, have_min = false;
@@ -619,6 +622,8 @@ static pa_status fp64_run(pa_ctx* h, pa_mode mode, int iters, int t0, bool fresh
   p.mode = mode;
   p.ablation = h->opt.ablation;
   p.beta1 = b1; p.beta2 = b2; p.eps = eps;
+  p.omb1 = 1.0 - b1;
+  p.w2 = (1.0 - b2) / ((1.0 - b1) * (1.0 - b1));
   p.timeout_ns = h->opt.barrier_timeout_ns;
   p.skip_arrival = h->opt.debug_skip_arrival;
   e = cluster ? launch_persistent_cluster(p, h->opt.loss, G, h->stream, &h->launches)
@@ -672,6 +677,8 @@ static pa_status mixed_max_run(pa_ctx* h, int iters, double b1, double b2, doubl
   q.iters = t32;
   q.ablation = h->opt.ablation;
   q.beta1 = b1; q.beta2 = b2;
+  q.omb1 = 1.0 - b1;
+  q.w2 = (1.0 - b2) / ((1.0 - b1) * (1.0 - b1));
   q.timeout_ns = h->opt.barrier_timeout_ns;
   q.skip_arrival = h->opt.debug_skip_arrival;
   h->last_G = G;
@@ -949,7 +956,7 @@ static pa_status lu_run(pa_ctx* h, const double* x0, int iters, double lr, doubl
   p.t0 = 0;
   p.beta1 = b1;
   p.beta2 = b2;
-  p.smem_mode = lu_smem_bytes(p, 2) ? 2 : (lu_smem_bytes(p, 1) ? 1 : 0);
+  p.smem_mode = lu_smem_bytes(p, 1) ? 1 : 0;
   if (!h->lu_params && (st = alloc_n(h, &h->lu_params, 1, "LU run parameters"))) return st;
   if ((e = cudaMemcpyAsync(h->lu_params, &p, sizeof(LuParams), cudaMemcpyHostToDevice, h->stream)) ||
       (e = cudaStreamSynchronize(h->stream)) ||  // p lives on this stack frame
@@ -1421,6 +1428,7 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
   bp.loss = h0->opt.loss;
   bp.ablation = h0->opt.ablation;
   bp.beta1 = b1;
+  bp.w2 = (1.0 - b2) / ((1.0 - b1) * (1.0 - b1));
   bp.beta2 = b2;
   bp.timeout_ns = h0->opt.barrier_timeout_ns;
 
@@ -1594,7 +1602,7 @@ static pa_status batched_lu(const pa_handle* hs, int n_mat, int k_restarts, int 
       p.iters = iters;
       p.beta1 = b1;
       p.beta2 = b2;
-      p.smem_mode = lu_smem_bytes(p, 2) ? 2 : (lu_smem_bytes(p, 1) ? 1 : 0);
+      p.smem_mode = lu_smem_bytes(p, 1) ? 1 : 0;
       smem = std::max(smem, lu_smem_bytes(p, p.smem_mode));
       // item (i, r): SplitMix64 output i * k_restarts + r of `seed`, source order
       const uint64_t s_ir = splitmix64_at(seed, (uint64_t)it);
@@ -1615,6 +1623,31 @@ static pa_status batched_lu(const pa_handle* hs, int n_mat, int k_restarts, int 
     o[1] = rs[it].status == PA_OK ? 1.0 / rs[it].sigma : NAN;
     o[2] = have_max ? o[0] / o[1] : NAN;
     if (item_status && rs[it].status != PA_OK) item_status[it] = (pa_status)rs[it].status;
+  }
+  return PA_OK;
+}
+
+// The SpMM engine over all items, restarts in blocks of at most kb columns
+// (each block rounded up to a kernel width K in {1, 2, 4, 8}), matrices in
+// waves that leave every matrix at least two CTAs.
+static pa_status spmm_batches(const pa_handle* handles, int n_mat, int k_restarts, int kb,
+                              pa_mode spmm_mode, const int* iters, double lr, double b1, double b2,
+                              double eps, uint64_t seed, double* out, pa_status* item_status) {
+  bool captured = false;
+  pa_status st;
+  for (int r0 = 0; r0 < k_restarts; r0 += kb) {
+    const int k_used = std::min(kb, k_restarts - r0);
+    const int K = k_used <= 1 ? 1 : (k_used <= 2 ? 2 : (k_used <= 4 ? 4 : 8));
+    const int Gmax = batched_max_blocks(K);
+    if (Gmax <= 0) return fail(PA_ERR_LAUNCH, "the batched kernel does not fit on this GPU");
+    const int wave = std::max(1, Gmax / 2);
+    for (int i0 = 0; i0 < n_mat; i0 += wave) {
+      const int m = std::min(wave, n_mat - i0);
+      if ((st = batched_wave(handles, i0, m, r0, k_used, K, k_restarts, spmm_mode, iters, lr, b1,
+                             b2, eps, seed, out, item_status, &captured)))
+        return st;
+      g_last_batch_graph = captured ? 1 : 0;
+    }
   }
   return PA_OK;
 }
@@ -1653,21 +1686,33 @@ extern "C" pa_status pa_estimate_batched(int n_mat, const pa_handle* handles, pa
     return batched_lu(handles, n_mat, k_restarts, iters[1], lr, beta1, beta2, eps, seed, false, out,
                       item_status);
   }
-  bool captured = false;
-  for (int r0 = 0; r0 < k_restarts; r0 += 8) {
-    const int k_used = std::min(8, k_restarts - r0);
-    const int K = k_used <= 1 ? 1 : (k_used <= 2 ? 2 : (k_used <= 4 ? 4 : 8));
-    const int Gmax = batched_max_blocks(K);
-    if (Gmax <= 0) return fail(PA_ERR_LAUNCH, "the batched kernel does not fit on this GPU");
-    const int wave = std::max(1, Gmax / 2);
-    for (int i0 = 0; i0 < n_mat; i0 += wave) {
-      const int m = std::min(wave, n_mat - i0);
-      if ((st = batched_wave(handles, i0, m, r0, k_used, K, k_restarts, spmm_mode, iters, lr,
-                             beta1, beta2, eps, seed, out, item_status, &captured)))
-        return st;
-      g_last_batch_graph = captured ? 1 : 0;
+  // restart-block width: K = 8 by default; with autotune on the first handle,
+  // the fastest of 8, 4 and 2 on a short trial of this batch (cached per k)
+  int kb = 8;
+  pa_ctx* h0 = handles[0];
+  if (h0->opt.autotune > 0 && k_restarts >= 2) {
+    auto hit = h0->batch_kb.find(k_restarts);
+    if (hit != h0->batch_kb.end()) {
+      kb = hit->second;
+    } else {
+      const int trial[2] = {std::min(iters[0], 30), std::min(iters[1], 30)};
+      std::vector<double> scratch((size_t)n_mat * k_restarts * 3);
+      double best = INFINITY;
+      for (int cand : {8, 4, 2}) {
+        if (cand > 2 * k_restarts - 1 && cand != 2) continue;  // wider than the restarts need
+        const auto t0 = std::chrono::steady_clock::now();
+        if ((st = spmm_batches(handles, n_mat, k_restarts, cand, spmm_mode, trial, lr, beta1,
+                               beta2, eps, seed, scratch.data(), nullptr)))
+          return st;
+        const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (dt < best) { best = dt; kb = cand; }
+      }
+      h0->batch_kb[k_restarts] = kb;
     }
   }
+  if ((st = spmm_batches(handles, n_mat, k_restarts, kb, spmm_mode, iters, lr, beta1, beta2, eps,
+                         seed, out, item_status)))
+    return st;
   if (lu)
     return batched_lu(handles, n_mat, k_restarts, iters[1], lr, beta1, beta2, eps, seed, true, out,
                       item_status);

@@ -33,7 +33,8 @@ struct SharedB {
   double ca[K], cb[K];     // gradient coefficients per column
   double c[K], inv[K];     // projection coefficient, 1/||x'||
   double q[K];             // ||x_{t-1}||^2 per column
-  double L_min[K], L_last[K];
+  double best_s[K], best_q[K], last_s[K], last_q[K];  // best / latest scored (||y||^2, ||x||^2)
+  int have_best[K], have_last[K];
   int t_min[K], improved[K];
   int brk, ok, status;
   int iters_run;
@@ -98,8 +99,8 @@ __global__ void __launch_bounds__(kBT, 2) k_batched(const BatchParams bp) {
   int status = PA_OK;
 
   if (tid < K) {
-    sh.L_min[tid] = INFINITY;
-    sh.L_last[tid] = NAN;
+    sh.have_best[tid] = 0;
+    sh.have_last[tid] = 0;
     sh.t_min[tid] = 0;
     sh.improved[tid] = 0;
   }
@@ -173,14 +174,27 @@ __global__ void __launch_bounds__(kBT, 2) k_batched(const BatchParams bp) {
         if (!isfinite(s_) || !isfinite(q)) {
           atomicExch(&sh.status, PA_ERR_NONFINITE);
         } else if (t > 1) {
-          double L;
-          if (bp.loss == PA_LOSS_QUADRATIC) L = bp.mode == PA_SIGMA_MAX ? -s_ : s_;
-          else {
-            const double lx = log(sqrt(q)), lax = log(sqrt(s_));
-            L = bp.mode == PA_SIGMA_MAX ? lx - lax : lax - lx;
+          // L < L_min through the monotone map of the loss (no logarithm in
+          // the loop): log-ratio sigma_max: q s_b < q_b s; sigma_min: s q_b < s_b q
+          bool better;
+          if (!sh.have_best[c]) {
+            better = bp.loss == PA_LOSS_QUADRATIC || bp.mode == PA_SIGMA_MIN || s_ > 0.0;
+          } else if (bp.loss == PA_LOSS_QUADRATIC) {
+            better = bp.mode == PA_SIGMA_MAX ? s_ > sh.best_s[c] : s_ < sh.best_s[c];
+          } else {
+            better = bp.mode == PA_SIGMA_MAX ? q * sh.best_s[c] < sh.best_q[c] * s_
+                                             : s_ * sh.best_q[c] < sh.best_s[c] * q;
           }
-          sh.L_last[c] = L;
-          if (L < sh.L_min[c]) { sh.L_min[c] = L; sh.t_min[c] = t - 1; imp = 1; }
+          if (better) {
+            sh.best_s[c] = s_;
+            sh.best_q[c] = q;
+            sh.have_best[c] = 1;
+            sh.t_min[c] = t - 1;
+            imp = 1;
+          }
+          sh.last_s[c] = s_;
+          sh.last_q[c] = q;
+          sh.have_last[c] = 1;
         }
         if (s_ == 0.0 && isfinite(q)) atomicCAS(&sh.status, PA_OK, PA_WARN_SINGULAR);
         sh.improved[c] = imp;
@@ -213,7 +227,7 @@ __global__ void __launch_bounds__(kBT, 2) k_batched(const BatchParams bp) {
     {
       const double2 bc = bp.bias[t - 1];
       const double b1 = bp.beta1, b2 = bp.beta2;
-      const double w2 = (1.0 - b2) / ((1.0 - b1) * (1.0 - b1));
+      const double w2 = bp.w2;
       double pxd[K], pdd[K];
 #pragma unroll
       for (int c = 0; c < K; ++c) pxd[c] = pdd[c] = 0.0;
@@ -274,7 +288,7 @@ __global__ void __launch_bounds__(kBT, 2) k_batched(const BatchParams bp) {
         double inv = 1.0;
         if (!(bp.ablation & PA_ABLATE_NO_NORMALISE)) {
           const double a1c = 1.0 + cc;
-          inv = 1.0 / sqrt(fma(a1c * a1c, sh.q[c], fma(-2.0 * a1c, p1, p2)));
+          inv = rsqrt(fma(a1c * a1c, sh.q[c], fma(-2.0 * a1c, p1, p2)));
         }
         sh.c[c] = cc;
         sh.inv[c] = inv;
@@ -309,9 +323,14 @@ __global__ void __launch_bounds__(kBT, 2) k_batched(const BatchParams bp) {
   // results of the group, written by its first CTA
   if (lb == 0 && tid < K) {
     double* out = it.result + (size_t)tid * 4;
-    out[0] = sh.L_min[tid];
+    auto Lof = [&](double s_, double q) {
+      if (bp.loss == PA_LOSS_QUADRATIC) return bp.mode == PA_SIGMA_MAX ? -s_ : s_;
+      const double lx = log(sqrt(q)), lax = log(sqrt(s_));
+      return bp.mode == PA_SIGMA_MAX ? lx - lax : lax - lx;
+    };
+    out[0] = sh.have_best[tid] ? Lof(sh.best_s[tid], sh.best_q[tid]) : INFINITY;
     out[1] = sh.t_min[tid];
-    out[2] = sh.L_last[tid];
+    out[2] = sh.have_last[tid] ? Lof(sh.last_s[tid], sh.last_q[tid]) : NAN;
     out[3] = sh.iters_run;
   }
   if (lb == 0 && tid == 0) {

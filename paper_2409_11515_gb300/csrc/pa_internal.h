@@ -73,6 +73,8 @@ struct IterParams {
   int mode;       // PA_SIGMA_MAX / PA_SIGMA_MIN
   int ablation;   // PA_ABLATE_* bits
   double beta1, beta2, eps;
+  double omb1;    // 1 - beta1
+  double w2;      // (1 - beta2) / (1 - beta1)^2
   long long timeout_ns;
   int skip_arrival;
 };
@@ -98,6 +100,8 @@ struct IterParams32 {
   int iters;
   int ablation;
   double beta1, beta2;
+  double omb1;    // 1 - beta1
+  double w2;      // (1 - beta2) / (1 - beta1)^2
   long long timeout_ns;
   int skip_arrival;
 };
@@ -126,6 +130,7 @@ struct BatchParams {
   RunState* st;              // shared abort flag
   int iters, mode, loss, ablation;
   double beta1, beta2;
+  double w2;  // (1 - beta2) / (1 - beta1)^2
   long long timeout_ns;
 };
 
@@ -236,7 +241,7 @@ cudaError_t launch_equilibrate(int32_t n_rows, int32_t n_cols, const int32_t* rp
 // position k holds row order[k]; positions lvl[l] .. lvl[l+1] are the rows of
 // level l, which depend only on rows of earlier levels; the off-diagonal
 // entries of position k are ci/va[rp[k] .. rp[k+1]) (a level's entries are
-// contiguous) and its diagonal is diag[k].
+// contiguous) and diag[k] is the reciprocal of its diagonal entry.
 struct TriSys {
   int32_t nlev;
   const int32_t* rp; const int32_t* ci; const double* va; const double* diag;
@@ -256,7 +261,7 @@ struct LuParams {
   int iters, t0;
   double beta1, beta2;
   int smem_mode;             // 0: all in global memory; 1: the five solve vectors
-                             // in shared memory; 2: also each system's lvl, rp, order
+                             // in shared memory
 };
 constexpr int kLuThreads = 512;
 constexpr size_t kLuSmemBudget = 200 * 1024;  // dynamic shared memory the LU kernel may use

@@ -51,8 +51,10 @@ struct Shared {
   int brk;            // leave the iteration loop
   int cur, nb;        // buffer of x_{t-1}, buffer for x_t
   int ok;
-  // Algorithm 1's tracking state, owned by thread 0
-  double L_min, L_last;
+  // Algorithm 1's tracking state, owned by thread 0: the best and the latest
+  // scored (||y||^2, ||x||^2); L itself is formed once at the end
+  double best_s, best_q, last_s, last_q;
+  int have_best, have_last;
   int minb, t_min, iters_run, status;
   // busy time per phase (barrier waits excluded), read by the partition tuner
   unsigned long long busy_a, busy_b;
@@ -98,8 +100,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
     sh.t_min = 0;
     sh.iters_run = 0;
     sh.status = PA_OK;
-    sh.L_min = INFINITY;
-    sh.L_last = NAN;
+    sh.have_best = 0;
+    sh.have_last = 0;
     sh.busy_a = sh.busy_b = 0;
   }
 
@@ -155,6 +157,11 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
     if (tid < 32) {
       const double s_ = ordered_sum(part, G, kPartSlots, 0);
       const double q = ordered_sum(part, G, kPartSlots, 1);
+      // g' = (1 - beta1) g = ca x + cb z (the first moment's weight folded
+      // in): lanes 0 and 1 run one division sequence for both coefficients
+      double coef = 0.0;
+      if (LOSS != PA_LOSS_QUADRATIC && lane < 2) coef = p.omb1 / (lane == 0 ? q : -s_);
+      const double cb_lr = __shfl_sync(0xffffffffu, coef, 1);
       if (tid == 0) {
         int brk = 0;
         const int cur = sh.cur;
@@ -163,14 +170,37 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
           brk = 1;
         } else {
           if (t > 1) {  // score x_{t-1}, the iterate produced by the previous iteration
-            const double L = loss_value(p.mode, LOSS, s_, q);
-            sh.L_last = L;
-            if (p.L_trace && b == 0) p.L_trace[t - 2] = L;
-            if (L < sh.L_min) { sh.L_min = L; sh.t_min = t - 1; sh.minb = cur; }
+            // L(x) < L_min through the monotone map of the loss: for the
+            // log-ratio loss log||x|| - log||y|| < log||x_b|| - log||y_b||
+            // iff ||x||^2 ||y_b||^2 < ||x_b||^2 ||y||^2 (sigma_max; swapped
+            // for sigma_min), so no logarithm is taken in the loop
+            bool better;
+            if (LOSS == PA_LOSS_QUADRATIC) {
+              const double L = loss_value(p.mode, LOSS, s_, q);
+              better = !sh.have_best || L < loss_value(p.mode, LOSS, sh.best_s, sh.best_q);
+            } else if (!sh.have_best) {
+              better = p.mode == PA_SIGMA_MIN || s_ > 0.0;  // L = +inf never beats +inf
+            } else {
+              better = p.mode == PA_SIGMA_MAX ? q * sh.best_s < sh.best_q * s_
+                                              : s_ * sh.best_q < sh.best_s * q;
+            }
+            if (better) {
+              sh.best_s = s_;
+              sh.best_q = q;
+              sh.have_best = 1;
+              sh.t_min = t - 1;
+              sh.minb = cur;
+            }
+            sh.last_s = s_;
+            sh.last_q = q;
+            sh.have_last = 1;
+            if (p.L_trace && b == 0) p.L_trace[t - 2] = loss_value(p.mode, LOSS, s_, q);
           }
           if (s_ == 0.0) {
-            if (p.mode == PA_SIGMA_MIN && t == 1) {
-              sh.L_min = loss_value(p.mode, LOSS, s_, q);
+            if (p.mode == PA_SIGMA_MIN && t == 1) {  // x_init itself is a null vector
+              sh.best_s = s_;
+              sh.best_q = q;
+              sh.have_best = 1;
               sh.t_min = 0;
               sh.minb = cur;
             }
@@ -180,15 +210,12 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
             brk = 1;
           }
         }
-        // g' = (1 - beta1) g = ca x + cb z: the first moment's weight is
-        // folded into the gradient coefficients
         double ca, cb;
-        if (LOSS == PA_LOSS_QUADRATIC) { ca = 0.0; cb = -2.0; }
-        else { ca = 1.0 / q; cb = -1.0 / s_; }
+        if (LOSS == PA_LOSS_QUADRATIC) { ca = 0.0; cb = -2.0 * p.omb1; }
+        else { ca = coef; cb = cb_lr; }
         if (p.mode == PA_SIGMA_MIN) { ca = -ca; cb = -cb; }
-        const double omb1 = 1.0 - p.beta1;
-        sh.ca = omb1 * ca;
-        sh.cb = omb1 * cb;
+        sh.ca = ca;
+        sh.cb = cb;
         sh.scratch[0] = q;  // kept for the normalisation below
         sh.brk = brk;
       }
@@ -205,8 +232,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
       // K1 = lr sqrt(1-b2^t) / (1-b1^t) and K2 = eps sqrt(1-b2^t)
       const double2 bc = p.bias[p.t0 + t - 1];
       const double b1 = p.beta1, b2 = p.beta2;
-      // (1 - beta2) g^2 = w2 g'^2 with g' = (1 - beta1) g
-      const double w2 = (1.0 - b2) / ((1.0 - b1) * (1.0 - b1));
+      const double w2 = p.w2;  // (1 - beta2) g^2 = w2 g'^2 with g' = (1 - beta1) g
       double v[2] = {0.0, 0.0};
       for (int s = st0 + warp; s < st1; s += NW) {
         const double z = DD ? slice_dot_dd2(p.t_wp, p.t_col, p.t_val, s, lane, p.y, p.ylo)
@@ -249,7 +275,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
           const double a1c = 1.0 + c;
           // ||(1+c) x - dx||^2 = (1+c)^2 q - 2 (1+c) p1 + p2
           const double nrm2 = fma(a1c * a1c, q_keep, fma(-2.0 * a1c, p1, p2));
-          inv = 1.0 / sqrt(nrm2);
+          inv = rsqrt(nrm2);  // scales x only: the loss and Adam's step are scale-free
         }
         sh.c = c;
         sh.inv = inv;
@@ -297,8 +323,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
     st->minb = sh.minb;
     st->cur = sh.cur;
     st->t_min = sh.t_min;
-    st->L_min = sh.L_min;
-    st->L_last = sh.L_last;
+    st->L_min = sh.have_best ? loss_value(p.mode, LOSS, sh.best_s, sh.best_q) : INFINITY;
+    st->L_last = sh.have_last ? loss_value(p.mode, LOSS, sh.last_s, sh.last_q) : NAN;
     st->iters_run = sh.iters_run;
   }
 }

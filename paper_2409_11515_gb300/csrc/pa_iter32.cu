@@ -29,7 +29,8 @@ struct Shared32 {
   float lam;          // power-of-two scale of phase B's gathered y
   float c, inv;       // projection coefficient, 1 / ||x'||
   int brk, cur, nb, ok;
-  double L_min, L_last;
+  double best_s, best_q, last_s, last_q;  // best and latest scored (||y||^2, ||x||^2)
+  int have_best, have_last;
   int minb, t_min, iters_run, status;
   unsigned long long busy_a, busy_b;
   long long tmark;
@@ -131,8 +132,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent32(const 
     sh.t_min = 0;
     sh.iters_run = 0;
     sh.status = PA_OK;
-    sh.L_min = INFINITY;
-    sh.L_last = NAN;
+    sh.have_best = 0;
+    sh.have_last = 0;
     sh.busy_a = sh.busy_b = 0;
   }
 
@@ -182,6 +183,17 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent32(const 
     if (tid < 32) {
       const double s_ = ordered_sum(part, G, kPartSlots, 0);
       const double q = ordered_sum(part, G, kPartSlots, 1);
+      // lambda = 2^-e with 2^(e-1) <= ||y|| < 2^e keeps (D_r,i lambda) y_i
+      // within FP32 range; e from the exponent of ||y||^2 (no square root)
+      int es;
+      frexp(s_, &es);
+      const double lam = ldexp(1.0, -((es + 1) >> 1));
+      // lanes 0 and 1 run one division sequence for both gradient
+      // coefficients: (1 - beta1) / q and, with z_j / s = D_c,j t_j /
+      // (lambda s), -(1 - beta1) / (lambda s)
+      double coef = 0.0;
+      if (lane < 2) coef = p.omb1 / (lane == 0 ? q : -(lam * s_));
+      const double cbz = __shfl_sync(0xffffffffu, coef, 1);
       if (tid == 0) {
         int brk = 0;
         const int cur = sh.cur;
@@ -190,11 +202,19 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent32(const 
           brk = 1;
         } else {
           if (t > 1) {
-            const double lx = log(sqrt(q)), lax = log(sqrt(s_));
-            const double L = lx - lax;  // sigma_max, log-ratio loss
-            sh.L_last = L;
-            if (p.L_trace && b == 0) p.L_trace[t - 2] = L;
-            if (L < sh.L_min) { sh.L_min = L; sh.t_min = t - 1; sh.minb = cur; }
+            // L = log||x|| - log||y|| < L_min iff ||x||^2 ||y_b||^2 < ||x_b||^2 ||y||^2
+            const bool better = sh.have_best ? q * sh.best_s < sh.best_q * s_ : s_ > 0.0;
+            if (better) {
+              sh.best_s = s_;
+              sh.best_q = q;
+              sh.have_best = 1;
+              sh.t_min = t - 1;
+              sh.minb = cur;
+            }
+            sh.last_s = s_;
+            sh.last_q = q;
+            sh.have_last = 1;
+            if (p.L_trace && b == 0) p.L_trace[t - 2] = log(sqrt(q)) - log(sqrt(s_));
           }
           if (s_ == 0.0) {
             sh.status = PA_WARN_SINGULAR;
@@ -204,15 +224,9 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent32(const 
           }
         }
         if (!brk) {
-          // lambda = 2^-round(log2 ||y||) keeps (D_r,i lambda) y_i within FP32 range
-          int e;
-          frexp(sqrt(s_), &e);
-          const double lam = ldexp(1.0, -e);
-          const double omb1 = 1.0 - p.beta1;
           sh.lam = (float)lam;
-          sh.ca = (float)(omb1 / q);
-          // z_j / s = D_c,j t_j / (lambda s); the sign makes g = x/q - z/s
-          sh.cbz = (float)(-omb1 / (lam * s_));
+          sh.ca = (float)coef;
+          sh.cbz = (float)cbz;
         }
         q_keep = q;
         sh.brk = brk;
@@ -229,7 +243,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent32(const 
       const double2 bc = p.bias[t - 1];
       const float K1 = (float)bc.x, K2 = (float)bc.y;
       const float b1 = (float)p.beta1, b2 = (float)p.beta2;
-      const float w2 = (float)((1.0 - p.beta2) / ((1.0 - p.beta1) * (1.0 - p.beta1)));
+      const float w2 = (float)p.w2;
       Kahan32 k1, k2;
       for (int s = st0 + warp; s < st1; s += NW) {
         const float tj = slice_dot32_scaled(p.t_wp, p.t_col, p.t_val, s, lane, p.y, p.dr, lam);
@@ -272,7 +286,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent32(const 
         if (!(p.ablation & PA_ABLATE_NO_NORMALISE)) {
           const double a1c = 1.0 + c;
           const double nrm2 = fma(a1c * a1c, q_keep, fma(-2.0 * a1c, p1, p2));
-          inv = 1.0 / sqrt(nrm2);
+          inv = rsqrt(nrm2);  // scales x only
         }
         sh.c = (float)c;
         sh.inv = (float)inv;
@@ -318,8 +332,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent32(const 
     st->minb = sh.minb;
     st->cur = sh.cur;
     st->t_min = sh.t_min;
-    st->L_min = sh.L_min;
-    st->L_last = sh.L_last;
+    st->L_min = sh.have_best ? log(sqrt(sh.best_q)) - log(sqrt(sh.best_s)) : INFINITY;
+    st->L_last = sh.have_last ? log(sqrt(sh.last_q)) - log(sqrt(sh.last_s)) : NAN;
     st->iters_run = sh.iters_run;
   }
 }

@@ -18,8 +18,7 @@
 // few thousand unknowns), so one CTA runs the whole iteration: a level then
 // costs one __syncthreads instead of a grid-wide barrier.  The factors are
 // stored in level order, so a level's entries are contiguous and are
-// prefetched into L1 two levels ahead; for small n the solve vectors, and
-// where they fit each system's level and row pointers and row order, live in
+// prefetched into L1 two levels ahead; for small n the solve vectors live in
 // shared memory.  The kernel waits on nothing outside its CTA.
 #include <math.h>
 
@@ -82,7 +81,7 @@ std::string tri_analyse(int32_t n, const int32_t* rp, const int32_t* ci, const d
       out->va.push_back(va[e]);
     }
     out->rp[k + 1] = (int32_t)out->ci.size();
-    out->diag[k] = diag_row[i];
+    out->diag[k] = 1.0 / diag_row[i];  // the solve multiplies by the reciprocal
   }
   return std::string();
 }
@@ -149,8 +148,11 @@ __device__ __forceinline__ void prefetch_level(const TriSys& T, int lev) {
 
 // x = T^{-1} b for one level-scheduled triangular system (all threads): a
 // warp per row, its lanes striding the row's entries, then a fixed-order
-// butterfly sum.  (The rounding order differs from plain substitution; the
-// route's iterates are insensitive to it at the 1e-15 level.)
+// butterfly sum and one multiply by the stored reciprocal of the diagonal.
+// A level's time is the latency of that chain of FP64 instructions (each
+// occupies GB300's narrow FP64 pipe for many cycles), so the division is
+// replaced by the reciprocal.  The rounding differs from plain substitution;
+// the route's iterates are insensitive to it at the 1e-15 level.
 __device__ __forceinline__ void tri_solve(const TriSys& T, const double* b, double* x) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   prefetch_level(T, 0);
@@ -159,13 +161,18 @@ __device__ __forceinline__ void tri_solve(const TriSys& T, const double* b, doub
     prefetch_level(T, lev + 2);
     const int k1 = T.lvl[lev + 1];
     for (int k = T.lvl[lev] + warp; k < k1; k += kLuWarps) {
-      const int e1 = T.rp[k + 1];
+      const int e0 = T.rp[k], e1 = T.rp[k + 1];
       double acc = 0.0;
-      for (int e = T.rp[k] + lane; e < e1; e += 32) acc = fma(T.va[e], x[T.ci[e]], acc);
-      acc = warp_sum(acc);
+      for (int e = e0 + lane; e < e1; e += 32) acc = fma(T.va[e], x[T.ci[e]], acc);
+      // butterfly over the lanes that hold entries (a row of 9 entries needs
+      // 4 levels, not 5); the level count is the same for the whole warp
+      const int len = e1 - e0;
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1)
+        if (d < len) acc += __shfl_xor_sync(0xffffffffu, acc, d);
       if (lane == 0) {
         const int i = T.order[k];
-        x[i] = (b[i] - acc) / T.diag[k];
+        x[i] = (b[i] - acc) * T.diag[k];
       }
     }
     __syncthreads();
@@ -180,24 +187,10 @@ __device__ __forceinline__ void apply_inv(const LuParams& p, const LuVec& V, con
   tri_solve(p.U, V.t, V.u);
 }
 
-// Copy a system's level pointers, row pointers and row order into shared
-// memory at `at` (int32 words) and point T there.
-__device__ __forceinline__ void stage_meta(TriSys& T, int n, int32_t* at) {
-  int32_t* lvl = at;
-  int32_t* rp = lvl + T.nlev + 1;
-  int32_t* order = rp + n + 1;
-  for (int i = threadIdx.x; i <= T.nlev; i += kLuThreads) lvl[i] = T.lvl[i];
-  for (int i = threadIdx.x; i <= n; i += kLuThreads) rp[i] = T.rp[i];
-  for (int i = threadIdx.x; i < n; i += kLuThreads) order[i] = T.order[i];
-  T.lvl = lvl;
-  T.rp = rp;
-  T.order = order;
-}
-
 // One CTA per item: item b runs Algorithm 1 on the inverse of its own matrix
 // from its own start vector, independently of the other CTAs.
 __global__ void __launch_bounds__(kLuThreads, 1) k_lu_iter(const LuParams* __restrict__ items) {
-  LuParams p = items[blockIdx.x];
+  const LuParams& p = items[blockIdx.x];
   __shared__ LuShared sh;
   extern __shared__ double dyn[];
   const int n = p.n, tid = threadIdx.x;
@@ -206,16 +199,6 @@ __global__ void __launch_bounds__(kLuThreads, 1) k_lu_iter(const LuParams* __res
     V = LuVec{dyn, dyn + n, dyn + 2 * n, dyn + 3 * n, dyn + 4 * n};
   } else {
     V = LuVec{p.w, p.t, p.u, p.a, p.c};
-  }
-  if (p.smem_mode == 2) {
-    int32_t* at = reinterpret_cast<int32_t*>(dyn + 5 * n);
-    TriSys* sys[4] = {&p.L, &p.U, &p.Ut, &p.Lt};
-    for (TriSys* T : sys) {
-      const int words = T->nlev + 1 + 2 * n + 1;
-      stage_meta(*T, n, at);
-      at += words;
-    }
-    __syncthreads();
   }
   if (tid == 0) {
     sh.L_min = INFINITY;
@@ -349,10 +332,7 @@ __global__ void __launch_bounds__(kLuThreads, 1) k_lu_iter(const LuParams* __res
 
 size_t lu_smem_bytes(const LuParams& p, int mode) {
   if (mode == 0) return 0;
-  size_t b = sizeof(double) * 5 * (size_t)p.n;
-  if (mode == 2)
-    for (const TriSys* T : {&p.L, &p.U, &p.Ut, &p.Lt})
-      b += sizeof(int32_t) * ((size_t)T->nlev + 1 + 2 * (size_t)p.n + 1);
+  const size_t b = sizeof(double) * 5 * (size_t)p.n;
   return b <= kLuSmemBudget ? b : 0;
 }
 

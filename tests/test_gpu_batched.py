@@ -91,3 +91,24 @@ def test_batched_errors():
         with pytest.raises(pa.PAError) as ei:
             pa.estimate_batched([h], pa.SIGMA_MAX, 2, (10, 10))
         assert ei.value.status == -9
+
+
+def test_batched_autotuned_width_keeps_results():
+    """With autotune on the first handle the engine times restart blocks of
+    8, 4 and 2 vectors on a short trial and keeps the fastest; every item
+    still matches the untuned batch (only the reduction order may differ)."""
+    mats = [synth.hydro_operator(9, seed=1), synth.hydro_operator(13, 11, seed=2),
+            synth.random_sparse(500, 5, seed=3, diag_boost=2.0)]
+    k, T = 8, 1500
+    hs = [pa.create(A, autotune=1 if i == 0 else 0) for i, A in enumerate(mats)]
+    hd = [pa.create(A) for A in mats]
+    try:
+        rt = pa.estimate_batched(hs, pa.BOTH, k, (T, T), seed=4, **HYPER)
+        rt2 = pa.estimate_batched(hs, pa.BOTH, k, (T, T), seed=4, **HYPER)  # cached width
+        rd = pa.estimate_batched(hd, pa.BOTH, k, (T, T), seed=4, **HYPER)
+    finally:
+        for h in hs + hd:
+            h.destroy()
+    assert rt["status"] == 0 and rd["status"] == 0
+    assert np.array_equal(rt["sigma_max"], rt2["sigma_max"])
+    assert np.max(np.abs(rt["sigma_max"] / rd["sigma_max"] - 1)) <= 1e-9
