@@ -827,12 +827,14 @@ static pa_status to_host(pa_ctx* h, const T* src, size_t count, int kind, std::v
 static pa_status upload_tri(pa_ctx* h, const TriHost& t, TriSys* out) {
   int32_t *rp, *ci, *order, *lvl;
   double *va, *diag;
+  int4 *lvinfo, *pos;
   pa_status st;
   if ((st = upload(h, t.rp, &rp, "LU factor")) || (st = upload(h, t.ci, &ci, "LU factor")) ||
       (st = upload(h, t.va, &va, "LU factor")) || (st = upload(h, t.diag, &diag, "LU factor")) ||
-      (st = upload(h, t.order, &order, "LU levels")) || (st = upload(h, t.lvl, &lvl, "LU levels")))
+      (st = upload(h, t.order, &order, "LU levels")) || (st = upload(h, t.lvl, &lvl, "LU levels")) ||
+      (st = upload(h, t.lvinfo, &lvinfo, "LU levels")) || (st = upload(h, t.pos, &pos, "LU levels")))
     return st;
-  *out = TriSys{(int32_t)t.lvl.size() - 1, rp, ci, va, diag, order, lvl};
+  *out = TriSys{(int32_t)t.lvl.size() - 1, rp, ci, va, diag, order, lvl, lvinfo, pos};
   return PA_OK;
 }
 

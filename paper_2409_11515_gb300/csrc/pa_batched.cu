@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(kBT, 2) k_batched(const BatchParams bp) {
             const double vj = fma(b2, it.V[o], w2 * (g * g));
             it.M[o] = mj;
             it.V[o] = vj;
-            const double d = (bc.x * mj) / (sqrt(vj) + bc.y);
+            const double d = adam_quotient(bc.x * mj, vj, bc.y);
             it.DX[o] = d;
             pxd[c] = fma(xj, d, pxd[c]);
             pdd[c] = fma(d, d, pdd[c]);

@@ -123,6 +123,19 @@ __device__ __forceinline__ double slice_dot(const int32_t* __restrict__ wp,
   return acc;
 }
 
+// Adam's step K1 m / (sqrt(v) + K2) through one reciprocal square root.  With
+// r = 1 / sqrt(v): K1 m / (sqrt(v) (1 + K2 r)) = K1 m r (1 - K2 r + ...), and
+// the dropped terms stay below 2^-54 relative while K2 r < 2^-27; otherwise
+// (v at or below about (2^27 K2)^2, or v = 0) the quotient itself.  GB300's
+// FP64 pipe is narrow, and rsqrt costs far fewer FP64 instructions than a
+// square root followed by a division; the result differs from the correctly
+// rounded quotient by a few ulp.
+__device__ __forceinline__ double adam_quotient(double num, double v, double K2) {
+  const double r = rsqrt(v);
+  const double kr = K2 * r;
+  return kr < 0x1.0p-27 ? num * fma(-kr, r, r) : num / (sqrt(v) + K2);
+}
+
 // ---- compensated (double-double) products --------------------------------
 // Error-free transformations: TwoProduct with one FMA (p + e = a b exactly)
 // and TwoSum (Knuth; s + e = a + b exactly).  The additions are written with

@@ -246,6 +246,8 @@ struct TriSys {
   int32_t nlev;
   const int32_t* rp; const int32_t* ci; const double* va; const double* diag;
   const int32_t* order; const int32_t* lvl;
+  const int4* lvinfo;  // [nlev] per level {first position, end position, first entry, end entry}
+  const int4* pos;     // [n] per position {first entry, end entry, row, 0}
 };
 // Algorithm 1 on B = A^{-1} = Q U^{-1} L^{-1} P, everything in source order.
 struct LuParams {
@@ -279,6 +281,7 @@ cudaError_t launch_lu_iter(const LuParams* items_dev, int n_items, size_t smem, 
 struct TriHost {
   std::vector<int32_t> rp, ci, order, lvl;
   std::vector<double> va, diag;
+  std::vector<int4> lvinfo, pos;
 };
 std::string tri_analyse(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
                         bool lower, TriHost* out);

@@ -47,7 +47,7 @@ struct Shared {
   double scratch[2 * kBlock];
   // per-iteration scalars, computed once by thread 0 and read by all threads
   double ca, cb;      // g = ca * x + cb * z
-  double c, inv;      // projection coefficient and 1 / ||x'||
+  double c, inv;      // 1 + the projection coefficient, and 1 / ||x'||
   int brk;            // leave the iteration loop
   int cur, nb;        // buffer of x_{t-1}, buffer for x_t
   int ok;
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
           const double vj = fma(b2, p.v[j], w2 * (g * g));
           p.m[j] = mj;
           p.v[j] = vj;
-          const double d = (bc.x * mj) / (sqrt(vj) + bc.y);
+          const double d = adam_quotient(bc.x * mj, vj, bc.y);
           p.dx[j] = d;
           v[0] = fma(xj, d, v[0]);
           v[1] = fma(d, d, v[1]);
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
           const double nrm2 = fma(a1c * a1c, q_keep, fma(-2.0 * a1c, p1, p2));
           inv = rsqrt(nrm2);  // scales x only: the loss and Adam's step are scale-free
         }
-        sh.c = c;
+        sh.c = 1.0 + c;  // phase C uses 1 + c
         sh.inv = inv;
         const int cur = sh.cur, minb = sh.minb;
         sh.nb = (cur != 0 && minb != 0) ? 0 : ((cur != 1 && minb != 1) ? 1 : 2);
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
     // ---- phase C: project, update, normalise; partial ||x_t||^2
     if (tid == 0) sh.tmark = globaltimer_ns();
     {
-      const double a1c = 1.0 + sh.c, inv = sh.inv;
+      const double a1c = sh.c, inv = sh.inv;
       const int nb = sh.nb;
       double* xo = pick(p, nb);
       double* tr = (p.x_trace && t <= p.n_trace) ? p.x_trace + (size_t)(t - 1) * n : nullptr;

@@ -83,6 +83,13 @@ std::string tri_analyse(int32_t n, const int32_t* rp, const int32_t* ci, const d
     out->rp[k + 1] = (int32_t)out->ci.size();
     out->diag[k] = 1.0 / diag_row[i];  // the solve multiplies by the reciprocal
   }
+  // packed per-level and per-position records: one load each in the solve
+  out->lvinfo.resize((size_t)nlev);
+  for (int32_t l = 0; l < nlev; ++l)
+    out->lvinfo[l] = make_int4(out->lvl[l], out->lvl[l + 1], out->rp[out->lvl[l]],
+                               out->rp[out->lvl[l + 1]]);
+  out->pos.resize((size_t)n);
+  for (int32_t k = 0; k < n; ++k) out->pos[k] = make_int4(out->rp[k], out->rp[k + 1], out->order[k], 0);
   return std::string();
 }
 
@@ -125,25 +132,26 @@ struct LuVec {
   double *w, *t, *u, *a, *c;
 };
 
-// Ask L1 for the diagonals, columns and values level `lev` reads (its
-// positions and entries are contiguous), so that they are on chip when the
-// solve reaches that level.  Every prefetched address lies inside its array.
-__device__ __forceinline__ void prefetch_range(const void* base, int bytes, int& l0) {
-  const char* b = reinterpret_cast<const char*>(base);
-  const int nl = (bytes + 127) / 128;
-  for (int l = (int)threadIdx.x - l0; l < nl; l += kLuThreads)
-    if (l >= 0) asm volatile("prefetch.global.L1 [%0];" ::"l"(b + 128 * l));
-  l0 += nl;  // the next range starts where this one's threads left off
-}
-
-__device__ __forceinline__ void prefetch_level(const TriSys& T, int lev) {
+// Ask L1 for what level `lev` reads (its positions and entries are
+// contiguous: position records, diagonals, columns, values).  Called by the
+// warps that have no row in the current level, `first` being the first of
+// them; every prefetched address lies inside its array.
+__device__ __forceinline__ void prefetch_level(const TriSys& T, int lev, int first) {
   if (lev >= T.nlev) return;
-  const int k0 = T.lvl[lev], k1 = T.lvl[lev + 1];
-  const int e0 = T.rp[k0], e1 = T.rp[k1];
-  int l0 = 0;
-  prefetch_range(T.diag + k0, 8 * (k1 - k0), l0);
-  prefetch_range(T.ci + e0, 4 * (e1 - e0), l0);
-  prefetch_range(T.va + e0, 8 * (e1 - e0), l0);
+  const int4 L = T.lvinfo[lev];
+  const int nr = L.y - L.x, ne = L.w - L.z;
+  const char* base[4] = {reinterpret_cast<const char*>(T.pos + L.x),
+                         reinterpret_cast<const char*>(T.diag + L.x),
+                         reinterpret_cast<const char*>(T.ci + L.z),
+                         reinterpret_cast<const char*>(T.va + L.z)};
+  const int bytes[4] = {16 * nr, 8 * nr, 4 * ne, 8 * ne};
+  int l = (int)threadIdx.x - 32 * first;
+  for (int r = 0; r < 4; ++r) {
+    const int nl = (bytes[r] + 127) / 128;
+    for (; l < nl; l += kLuThreads - 32 * first)
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(base[r] + 128 * l));
+    l -= nl;
+  }
 }
 
 // x = T^{-1} b for one level-scheduled triangular system (all threads): a
@@ -151,29 +159,29 @@ __device__ __forceinline__ void prefetch_level(const TriSys& T, int lev) {
 // butterfly sum and one multiply by the stored reciprocal of the diagonal.
 // A level's time is the latency of that chain of FP64 instructions (each
 // occupies GB300's narrow FP64 pipe for many cycles), so the division is
-// replaced by the reciprocal.  The rounding differs from plain substitution;
-// the route's iterates are insensitive to it at the 1e-15 level.
+// replaced by the reciprocal, and the warps without a row in the level
+// prefetch the next two levels meanwhile.  The rounding differs from plain
+// substitution; the route's iterates are insensitive to it at the 1e-15 level.
 __device__ __forceinline__ void tri_solve(const TriSys& T, const double* b, double* x) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  prefetch_level(T, 0);
-  prefetch_level(T, 1);
   for (int lev = 0; lev < T.nlev; ++lev) {
-    prefetch_level(T, lev + 2);
-    const int k1 = T.lvl[lev + 1];
-    for (int k = T.lvl[lev] + warp; k < k1; k += kLuWarps) {
-      const int e0 = T.rp[k], e1 = T.rp[k + 1];
+    const int4 L = T.lvinfo[lev];
+    const int rows = L.y - L.x;
+    if (warp >= rows) {  // idle this level: fetch the next two
+      prefetch_level(T, lev + 1, rows);
+      prefetch_level(T, lev + 2, rows);
+    }
+    for (int k = L.x + warp; k < L.y; k += kLuWarps) {
+      const int4 P = T.pos[k];
       double acc = 0.0;
-      for (int e = e0 + lane; e < e1; e += 32) acc = fma(T.va[e], x[T.ci[e]], acc);
+      for (int e = P.x + lane; e < P.y; e += 32) acc = fma(T.va[e], x[T.ci[e]], acc);
       // butterfly over the lanes that hold entries (a row of 9 entries needs
       // 4 levels, not 5); the level count is the same for the whole warp
-      const int len = e1 - e0;
+      const int len = P.y - P.x;
 #pragma unroll
       for (int d = 16; d > 0; d >>= 1)
         if (d < len) acc += __shfl_xor_sync(0xffffffffu, acc, d);
-      if (lane == 0) {
-        const int i = T.order[k];
-        x[i] = (b[i] - acc) * T.diag[k];
-      }
+      if (lane == 0) x[P.z] = (b[P.z] - acc) * T.diag[k];
     }
     __syncthreads();
   }
@@ -273,7 +281,7 @@ __global__ void __launch_bounds__(kLuThreads, 1) k_lu_iter(const LuParams* __res
         const double vj = fma(b2, p.v[j], w2 * (g * g));
         p.m[j] = mj;
         p.v[j] = vj;
-        const double d = (bc.x * mj) / (sqrt(vj) + bc.y);
+        const double d = adam_quotient(bc.x * mj, vj, bc.y);
         p.dx[j] = d;
         v[0] = fma(xj, d, v[0]);
         v[1] = fma(d, d, v[1]);
