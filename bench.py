@@ -243,7 +243,8 @@ def run_ours(args):
                              eta_lo=WORKLOAD["eta_lo"], eta_hi=WORKLOAD["eta_hi"],
                              seed=WORKLOAD["seed"])
     stream = torch.cuda.Stream()
-    h = pa.create(A, stream=stream, autotune=args.autotune)
+    tune_rounds = min(args.autotune, 2 * args.warmup)  # all of them inside the warm-up
+    h = pa.create(A, stream=stream, autotune=tune_rounds)
     it_per_step = ITERS_MAX + ITERS_MIN
 
     def step(handle):
@@ -328,7 +329,7 @@ def run_ours(args):
     _barrier(ws)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        with pa.create(A, stream=stream, autotune=args.autotune) as he:
+        with pa.create(A, stream=stream, autotune=tune_rounds) as he:
             he.estimate(pa.SIGMA_MAX, ITERS_MAX, seed=START_SEED, **HYPER)
             re = he.estimate(pa.SIGMA_MIN, ITERS_MIN, seed=START_SEED, **HYPER)
     torch.cuda.synchronize()
@@ -343,8 +344,8 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded hydro-mechanical operator generator)",
             "config": dict(_config(A), parallelism=f"replicas{ws}" if ws > 1 else "single_gpu",
-                           partition=(f"measured-cost tuner, {args.autotune} rounds in warm-up"
-                                      if args.autotune > 0 else "fixed cost model")),
+                           partition=(f"measured-cost tuner, {tune_rounds} rounds in warm-up"
+                                      if tune_rounds > 0 else "fixed cost model")),
             "kappa_estimates_per_s": ws * args.steps / (ms / 1e3),
             "result": {"sigma_max": r["sigma_max"], "sigma_min": r["sigma_min"],
                        "kappa": r["kappa"], "status": r["status"]},
@@ -658,9 +659,9 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--autotune", type=int, default=3,
+    ap.add_argument("--autotune", type=int, default=6,
                     help="partition-tuner rounds on the FP64 handle (0 = fixed cost model); "
-                         "they run in the warm-up steps")
+                         "one per run, so the default 3 warm-up steps (two runs each) hold them")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")

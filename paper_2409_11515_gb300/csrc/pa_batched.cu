@@ -131,6 +131,7 @@ __global__ void __launch_bounds__(kBT, 2) k_batched(const BatchParams bp) {
 #pragma unroll
       for (int c = 0; c < K; ++c) sv[c] = 0.0;
       for (int s = sa0 + warp; s < sa1; s += NW) {
+        if (s + NW < sa1) prefetch_slice_l2(it.a_wp, it.a_col, it.a_val, s + NW, lane);
         const int w0 = __ldg(it.a_wp + s), w = __ldg(it.a_wp + s + 1) - w0;
         const int64_t base = 32ll * w0 + lane;
         double acc[K];
@@ -232,6 +233,7 @@ __global__ void __launch_bounds__(kBT, 2) k_batched(const BatchParams bp) {
 #pragma unroll
       for (int c = 0; c < K; ++c) pxd[c] = pdd[c] = 0.0;
       for (int s = st0 + warp; s < st1; s += NW) {
+        if (s + NW < st1) prefetch_slice_l2(it.t_wp, it.t_col, it.t_val, s + NW, lane);
         const int w0 = __ldg(it.t_wp + s), w = __ldg(it.t_wp + s + 1) - w0;
         const int64_t base = 32ll * w0 + lane;
         double z[K];

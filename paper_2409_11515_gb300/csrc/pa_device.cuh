@@ -123,6 +123,24 @@ __device__ __forceinline__ double slice_dot(const int32_t* __restrict__ wp,
   return acc;
 }
 
+// Ask L2 for slice s's columns and values (one warp; s must be a valid
+// slice): issued one slice ahead of its use, it turns the warp's dependent
+// HBM latency into overlapped traffic.  Every address lies inside the slice.
+template <typename V>
+__device__ __forceinline__ void prefetch_slice_l2(const int32_t* __restrict__ wp,
+                                                  const int32_t* col, const V* val, int s,
+                                                  int lane) {
+  const int w0 = __ldg(wp + s), w1 = __ldg(wp + s + 1);
+  // 32 lanes x 4 bytes of column and 32 x sizeof(V) bytes of value per entry
+  const int nbc = 128 * (w1 - w0), nbv = 32 * (int)sizeof(V) * (w1 - w0);
+  const char* cb = reinterpret_cast<const char*>(col + 32ll * w0);
+  const char* vb = reinterpret_cast<const char*>(val + 32ll * w0);
+  for (int l = lane; 128 * l < nbc + nbv; l += 32) {
+    const char* a = 128 * l < nbc ? cb + 128 * l : vb + (128 * l - nbc);
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+  }
+}
+
 // Adam's step K1 m / (sqrt(v) + K2) through one reciprocal square root.  With
 // r = 1 / sqrt(v): K1 m / (sqrt(v) (1 + K2 r)) = K1 m r (1 - K2 r + ...), and
 // the dropped terms stay below 2^-54 relative while K2 r < 2^-27; otherwise

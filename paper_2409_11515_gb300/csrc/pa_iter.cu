@@ -130,6 +130,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
     {
       double v[2] = {0.0, qloc};
       for (int s = sa0 + warp; s < sa1; s += NW) {
+        if (s + NW < sa1) prefetch_slice_l2(p.a_wp, p.a_col, p.a_val, s + NW, lane);
         const int r = 32 * s + lane;
         double yr;
         if (DD) {
@@ -235,6 +236,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
       const double w2 = p.w2;  // (1 - beta2) g^2 = w2 g'^2 with g' = (1 - beta1) g
       double v[2] = {0.0, 0.0};
       for (int s = st0 + warp; s < st1; s += NW) {
+        if (!DD && s + NW < st1) prefetch_slice_l2(p.t_wp, p.t_col, p.t_val, s + NW, lane);
         const double z = DD ? slice_dot_dd2(p.t_wp, p.t_col, p.t_val, s, lane, p.y, p.ylo)
                             : slice_dot(p.t_wp, p.t_col, p.t_val, s, lane, p.y);
         const int j = 32 * s + lane;

@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent32(const 
     {
       double v[2] = {0.0, qk.value()};
       for (int s = sa0 + warp; s < sa1; s += NW) {
+        if (s + NW < sa1) prefetch_slice_l2(p.a_wp, p.a_col, p.a_val, s + NW, lane);
         const float u = slice_dot32(p.a_wp, p.a_col, p.a_val, s, lane, p.W);
         const int r = 32 * s + lane;
         if (r < p.n_rows) {
@@ -246,6 +247,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent32(const 
       const float w2 = (float)p.w2;
       Kahan32 k1, k2;
       for (int s = st0 + warp; s < st1; s += NW) {
+        if (s + NW < st1) prefetch_slice_l2(p.t_wp, p.t_col, p.t_val, s + NW, lane);
         const float tj = slice_dot32_scaled(p.t_wp, p.t_col, p.t_val, s, lane, p.y, p.dr, lam);
         const int j = 32 * s + lane;
         if (j < n) {
