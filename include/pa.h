@@ -106,9 +106,11 @@ typedef struct {
   int fp64_tail;    /* MIXED sigma_max: the last iterations, run in FP64 from
                        the FP32 state (x, m, v) near convergence; < 0 (default)
                        = iters / 10, 0 = none */
-  int autotune;     /* > 0: after each of the first `autotune` runs of the
-                       grid engine, re-split the slices among the CTAs at
-                       equal measured busy time (per-CTA timers of that run);
+  int autotune;     /* > 0: after each of the first `autotune` - 1 runs of
+                       the grid engine, re-split the slices among the CTAs at
+                       equal measured busy time (per-CTA timers of that run),
+                       and after run `autotune` keep the fastest of the
+                       partitions those runs used (cost-model start included);
                        and when this handle is the first of a
                        pa_estimate_batched call, time short trials of the
                        batch with restart blocks of 8, 4 and 2 vectors and

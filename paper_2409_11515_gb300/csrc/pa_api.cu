@@ -111,7 +111,11 @@ struct pa_ctx {
   unsigned* ready = nullptr;
   unsigned long long* cta_ns = nullptr;  // [2G] per-CTA busy time of the last run
   int last_G = 0;
-  int tuned_rounds = 0;                  // partition re-splits done for h->G
+  int tuned_rounds = 0;                  // tuner rounds done for h->G
+  double tune_best = INFINITY;           // fastest per-iteration time seen while tuning
+  std::vector<int32_t> tune_best_a, tune_best_t;  // the partitions of that run
+  cudaEvent_t tune_ev[2] = {nullptr, nullptr};
+  float last_run_ms = 0.f;               // the latest timed grid run
   std::map<int, int> batch_kb;           // tuned restart-block width per k (batched engine)
   double2* bias = nullptr;
   int bias_cap = 0;
@@ -180,6 +184,8 @@ extern "C" void pa_destroy(pa_handle h) {
     else cudaFreeAsync(b.p, h->stream);
   }
   cudaStreamSynchronize(h->stream);
+  for (cudaEvent_t ev : h->tune_ev)
+    if (ev) cudaEventDestroy(ev);
   delete h;
 }
 
@@ -476,6 +482,7 @@ static pa_status ensure_partitions(pa_ctx* h, int G) {
     return cuda_fail(e, "finding neighbour dependencies");
   h->G = G;
   h->tuned_rounds = 0;
+  h->tune_best = INFINITY;
   return PA_OK;
 }
 
@@ -510,8 +517,12 @@ static void resplit(std::vector<int32_t>& part, const std::vector<int32_t>& wp,
   part = np;
 }
 
-// One round of the partition tuner, from the per-CTA timers of the last run.
-static pa_status tune_partitions(pa_ctx* h) {
+// One round of the partition tuner, from the per-CTA timers of the last run
+// and its time per iteration.  Every round but the last re-splits at equal
+// measured cost; the last installs the fastest partition seen over the
+// rounds (the cost-model start included), so one noisy measurement cannot
+// leave a bad split behind.
+static pa_status tune_partitions(pa_ctx* h, double t_iter) {
   const int G = h->G;
   std::vector<unsigned long long> t((size_t)2 * G);
   std::vector<int32_t> pa_((size_t)G + 1), pt_((size_t)G + 1);
@@ -524,20 +535,30 @@ static pa_status tune_partitions(pa_ctx* h) {
       (e = cudaMemcpyAsync(wpt.data(), h->sq.wp, sizeof(int32_t) * wpt.size(), cudaMemcpyDeviceToHost, h->stream)) ||
       (e = cudaStreamSynchronize(h->stream)))
     return cuda_fail(e, "reading the run profile for the tuner");
-  std::vector<double> ba(G), bb(G);
-  for (int b = 0; b < G; ++b) {
-    ba[b] = (double)t[2 * b];
-    bb[b] = (double)t[2 * b + 1];
+  if (t_iter < h->tune_best) {
+    h->tune_best = t_iter;
+    h->tune_best_a = pa_;
+    h->tune_best_t = pt_;
   }
-  resplit(pa_, wpa, ba, 2);
-  resplit(pt_, wpt, bb, 30);
+  ++h->tuned_rounds;
+  if (h->tuned_rounds < h->opt.autotune) {
+    std::vector<double> ba(G), bb(G);
+    for (int b = 0; b < G; ++b) {
+      ba[b] = (double)t[2 * b];
+      bb[b] = (double)t[2 * b + 1];
+    }
+    resplit(pa_, wpa, ba, 2);
+    resplit(pt_, wpt, bb, 30);
+  } else {
+    pa_ = h->tune_best_a;
+    pt_ = h->tune_best_t;
+  }
   if ((e = cudaMemcpyAsync(h->part_a, pa_.data(), sizeof(int32_t) * pa_.size(), cudaMemcpyHostToDevice, h->stream)) ||
       (e = cudaMemcpyAsync(h->part_t, pt_.data(), sizeof(int32_t) * pt_.size(), cudaMemcpyHostToDevice, h->stream)) ||
       (e = launch_dependencies(h->sa.wp, h->sa.col, h->sa.val, h->part_a, h->part_t, G, h->dep,
                                h->stream, &h->launches)) ||
       (e = cudaStreamSynchronize(h->stream)))
     return cuda_fail(e, "applying the tuned partition");
-  ++h->tuned_rounds;
   return PA_OK;
 }
 
@@ -767,12 +788,28 @@ static pa_status run_one(pa_ctx* h, pa_mode mode, int iters, double lr, double b
   if (mixed && mode == PA_SIGMA_MAX) {
     if ((st = mixed_max_run(h, iters, b1, b2, eps, G, maxG, L_trace_dev, out)) < 0) return st;
   } else {
+    const bool tuning = !cluster && !mixed && h->opt.autotune > 0 &&
+                        h->tuned_rounds < h->opt.autotune && iters >= 20;
+    cudaError_t e;
+    if (tuning) {
+      for (cudaEvent_t& ev : h->tune_ev)
+        if (!ev && (e = cudaEventCreate(&ev))) return cuda_fail(e, "creating the tuner's events");
+      if ((e = cudaEventRecord(h->tune_ev[0], h->stream))) return cuda_fail(e, "timing the run");
+    }
     if ((st = fp64_run(h, mode, iters, 0, true, mixed, b1, b2, eps, G, maxG, L_trace_dev,
                        x_trace_dev, n_trace, out, cluster)))
       return st;
+    if (tuning) {
+      float ms = 0.f;
+      if ((e = cudaEventRecord(h->tune_ev[1], h->stream)) ||
+          (e = cudaEventSynchronize(h->tune_ev[1])) ||
+          (e = cudaEventElapsedTime(&ms, h->tune_ev[0], h->tune_ev[1])))
+        return cuda_fail(e, "timing the run");
+      h->last_run_ms = ms;
+    }
     double* keep = mode == PA_SIGMA_MAX ? h->xmin_max : h->xmin_min;
-    cudaError_t e = launch_unpermute(h->n_cols, 1, h->sq.pos, pick64h(h, out->minb), keep,
-                                     h->stream, &h->launches);
+    e = launch_unpermute(h->n_cols, 1, h->sq.pos, pick64h(h, out->minb), keep, h->stream,
+                         &h->launches);
     if (e != cudaSuccess) return cuda_fail(e, "keeping x_min");
     if ((st = status_error(out))) return st;
   }
@@ -781,7 +818,7 @@ static pa_status run_one(pa_ctx* h, pa_mode mode, int iters, double lr, double b
   // the partition tuner learns from plain FP64 grid-engine runs long enough
   // to time (the FP32 and compensated kernels have other cost profiles)
   if (!cluster && !mixed && h->opt.autotune > 0 && h->tuned_rounds < h->opt.autotune && iters >= 20 &&
-      (st = tune_partitions(h)))
+      (st = tune_partitions(h, h->last_run_ms / iters)))
     return st;
   return (pa_status)out->status;
 }
