@@ -110,6 +110,7 @@ struct pa_ctx {
   int32_t *part_a = nullptr, *part_t = nullptr, *dep = nullptr;
   unsigned* ready = nullptr;
   unsigned long long* cta_ns = nullptr;  // [2G] per-CTA busy time of the last run
+  unsigned long long* cta_lat = nullptr; // [G] per-CTA phase-A completion latency
   int last_G = 0;
   int tuned_rounds = 0;                  // tuner rounds done for h->G
   double tune_best = INFINITY;           // fastest per-iteration time seen while tuning
@@ -459,6 +460,8 @@ static pa_status ensure_partitions(pa_ctx* h, int G) {
   if (h->dep) dev_free(h, h->dep);
   if (h->ready) dev_free(h, h->ready);
   if (h->cta_ns) dev_free(h, h->cta_ns);
+  if (h->cta_lat) dev_free(h, h->cta_lat);
+  h->cta_lat = nullptr;
   h->part_a = h->part_t = h->dep = nullptr;
   h->partials = nullptr;
   h->ready = nullptr;
@@ -469,6 +472,7 @@ static pa_status ensure_partitions(pa_ctx* h, int G) {
       (st = alloc_n(h, &h->dep, (size_t)2 * G, "dependencies")) ||
       (st = alloc_n(h, &h->ready, (size_t)G, "ready flags")) ||
       (st = alloc_n(h, &h->cta_ns, (size_t)2 * G, "CTA timers")) ||
+      (st = alloc_n(h, &h->cta_lat, (size_t)G, "CTA timers")) ||
       (st = alloc_n(h, &h->partials, (size_t)G * kPartSlots, "partials")))
     return st;
   cudaError_t e;
@@ -524,11 +528,12 @@ static void resplit(std::vector<int32_t>& part, const std::vector<int32_t>& wp,
 // leave a bad split behind.
 static pa_status tune_partitions(pa_ctx* h, double t_iter) {
   const int G = h->G;
-  std::vector<unsigned long long> t((size_t)2 * G);
+  std::vector<unsigned long long> t((size_t)2 * G), lat((size_t)G);
   std::vector<int32_t> pa_((size_t)G + 1), pt_((size_t)G + 1);
   std::vector<int32_t> wpa((size_t)h->sa.n_slices + 1), wpt((size_t)h->sq.n_slices + 1);
   cudaError_t e;
   if ((e = cudaMemcpyAsync(t.data(), h->cta_ns, sizeof(unsigned long long) * t.size(), cudaMemcpyDeviceToHost, h->stream)) ||
+      (e = cudaMemcpyAsync(lat.data(), h->cta_lat, sizeof(unsigned long long) * lat.size(), cudaMemcpyDeviceToHost, h->stream)) ||
       (e = cudaMemcpyAsync(pa_.data(), h->part_a, sizeof(int32_t) * pa_.size(), cudaMemcpyDeviceToHost, h->stream)) ||
       (e = cudaMemcpyAsync(pt_.data(), h->part_t, sizeof(int32_t) * pt_.size(), cudaMemcpyDeviceToHost, h->stream)) ||
       (e = cudaMemcpyAsync(wpa.data(), h->sa.wp, sizeof(int32_t) * wpa.size(), cudaMemcpyDeviceToHost, h->stream)) ||
@@ -542,9 +547,13 @@ static pa_status tune_partitions(pa_ctx* h, double t_iter) {
   }
   ++h->tuned_rounds;
   if (h->tuned_rounds < h->opt.autotune) {
+    // phase A is split by how late each CTA's y is ready (its phase C, its
+    // wait for neighbours and its phase A), phases B and C by busy time
     std::vector<double> ba(G), bb(G);
+    bool have_lat = true;
+    for (int b = 0; b < G; ++b) have_lat = have_lat && lat[b] > 0;
     for (int b = 0; b < G; ++b) {
-      ba[b] = (double)t[2 * b];
+      ba[b] = have_lat ? (double)lat[b] : (double)t[2 * b];
       bb[b] = (double)t[2 * b + 1];
     }
     resplit(pa_, wpa, ba, 2);
@@ -631,6 +640,7 @@ static pa_status fp64_run(pa_ctx* h, pa_mode mode, int iters, int t0, bool fresh
   p.partials = h->partials;
   p.ready = h->ready;
   p.cta_ns = h->cta_ns;
+  p.cta_lat = h->cta_lat;
   h->last_G = G;
   p.dep = h->dep;
   p.bias = h->bias;

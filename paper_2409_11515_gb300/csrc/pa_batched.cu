@@ -75,7 +75,17 @@ __device__ __forceinline__ bool group_barrier(unsigned* counter, unsigned& targe
 __device__ __forceinline__ double slot_sum(const double* slots, int nt) {
   const int lane = threadIdx.x & 31;
   double a = 0.0;
-  for (int t = lane; t < nt; t += 32) a += slots[t];
+  for (int base = 0; base < nt; base += 256) {  // loads before adds, pairwise
+    double u[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int t = base + lane + 32 * j;
+      u[j] = t < nt ? slots[t] : 0.0;
+    }
+    u[0] += u[1]; u[2] += u[3]; u[4] += u[5]; u[6] += u[7];
+    u[0] += u[2]; u[4] += u[6];
+    a += u[0] + u[4];
+  }
   return warp_sum(a);
 }
 

@@ -66,12 +66,27 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* scratch) {
 }
 
 // Fixed-order sum of part[k * stride + slot], k < count, done by every warp
-// that calls it; all lanes and all callers get identical bits.
+// that calls it; all lanes and all callers get identical bits.  Each lane
+// issues the loads of up to 16 values before adding any (a loop that adds as
+// it loads waits one L2 latency per value: 6 us for 304 values on GB300),
+// then adds them pairwise, then a butterfly across the lanes.
 __device__ __forceinline__ double ordered_sum(const double* part, int count, int stride, int slot) {
   const int lane = threadIdx.x & 31;
-  double a = 0.0;
-  for (int k = lane; k < count; k += 32) a += part[(size_t)k * stride + slot];
-  return warp_sum(a);
+  double acc = 0.0;
+  for (int base = 0; base < count; base += 512) {
+    double v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int k = base + lane + 32 * i;
+      v[i] = k < count ? part[(size_t)k * stride + slot] : 0.0;
+    }
+#pragma unroll
+    for (int w = 1; w < 16; w *= 2)
+#pragma unroll
+      for (int i = 0; i + w < 16; i += 2 * w) v[i] += v[i + w];
+    acc += v[0];
+  }
+  return warp_sum(acc);
 }
 
 // Dot product of one CSR row with a dense vector, entries in storage order,
@@ -237,10 +252,10 @@ __device__ __forceinline__ double slice_dot_dd2(const int32_t* __restrict__ wp,
   return __dadd_rn(sum, c);
 }
 
-// Block sum of NV per-thread values, result in thread 0 only.  Every thread
-// stores its values in `scratch` (NV * blockDim.x doubles); warp 0 adds them
-// in a fixed order (lane l sums threads l, l+32, ... sequentially, then a
-// butterfly), so the result does not depend on timing.
+// Block sum of NV per-thread values, result in warp 0 (thread 0 uses it).
+// Every thread stores its values in `scratch` (NV * blockDim.x doubles); warp
+// 0 adds them in a fixed order (lane l: threads l, l+32, ... in a fixed
+// pairwise tree, then a butterfly), so the result does not depend on timing.
 template <int NV>
 __device__ __forceinline__ void block_sum_to0(double (&v)[NV], double* scratch) {
   const int nt = blockDim.x;
@@ -251,8 +266,20 @@ __device__ __forceinline__ void block_sum_to0(double (&v)[NV], double* scratch) 
   if (threadIdx.x < 32) {
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
+      // eight shared-memory values per chunk loaded before they are added
+      // pairwise (a running sum would chain one FP64 latency per value)
       double a = 0.0;
-      for (int t = threadIdx.x; t < nt; t += 32) a += scratch[i * nt + t];
+      for (int base = 0; base < nt; base += 256) {
+        double u[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int t = base + (int)threadIdx.x + 32 * j;
+          u[j] = t < nt ? scratch[i * nt + t] : 0.0;
+        }
+        u[0] += u[1]; u[2] += u[3]; u[4] += u[5]; u[6] += u[7];
+        u[0] += u[2]; u[4] += u[6];
+        a += u[0] + u[4];
+      }
       v[i] = warp_sum(a);
     }
   }
@@ -300,14 +327,17 @@ __device__ __forceinline__ bool grid_barrier(RunState* st, unsigned& target, uns
 // reaches t), with the same time limit and abort flag as grid_barrier.  Only
 // the CTAs whose x rows this CTA's products read take part, so this replaces
 // a grid-wide barrier between the update of x and the next product.
+// The lanes of warp 0 poll the flags in parallel (lane l takes CTAs lo + l,
+// lo + l + 32, ...), so flags that are already set cost one L2 round trip,
+// not one per neighbour.
 __device__ __forceinline__ bool wait_ready(RunState* st, const unsigned* ready, int lo, int hi,
                                            unsigned t, long long timeout_ns, int site,
                                            int& ok_slot) {
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
     int ok = 1;
     const long long t0 = globaltimer_ns();
     int spins = 0;
-    for (int j = lo; j <= hi && ok; ++j) {
+    for (int j = lo + (int)threadIdx.x; j <= hi && ok; j += 32) {
       while (true) {
         const unsigned c = ld_acquire_u32(ready + j);
         if ((int)(c - t) >= 0) break;
@@ -322,8 +352,11 @@ __device__ __forceinline__ bool wait_ready(RunState* st, const unsigned* ready, 
         }
       }
     }
-    __threadfence();
-    ok_slot = ok;
+    ok = __all_sync(0xffffffffu, ok);  // every lane's wait is bounded, so all arrive
+    if (threadIdx.x == 0) {
+      __threadfence();
+      ok_slot = ok;
+    }
   }
   __syncthreads();
   return ok_slot != 0;

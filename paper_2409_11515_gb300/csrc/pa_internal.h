@@ -62,6 +62,8 @@ struct IterParams {
   double* partials;                    // [G][kPartSlots]
   unsigned* ready;                     // [G] last iteration whose x_t each CTA has written
   unsigned long long* cta_ns;          // [2G] per-CTA time in phases A and B+C (ns), or null
+  unsigned long long* cta_lat;         // [G] per-CTA sum over iterations of (end of phase A -
+                                       // start of the previous phase C), or null
   const int32_t* dep;                  // [2G] CTAs whose x rows CTA b's phase A reads: [lo, hi]
   const double2* bias;                 // [iters]: {lr sqrt(1-b2^t)/(1-b1^t), eps sqrt(1-b2^t)}
   double* L_trace;                     // [iters] or null

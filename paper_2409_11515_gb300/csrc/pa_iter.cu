@@ -58,7 +58,8 @@ struct Shared {
   int minb, t_min, iters_run, status;
   // busy time per phase (barrier waits excluded), read by the partition tuner
   unsigned long long busy_a, busy_b;
-  long long tmark;
+  unsigned long long lat_a;  // sum of (end of phase A - start of the previous phase C)
+  long long tmark, tc;
 };
 
 __device__ __forceinline__ double* pick(const IterParams& p, int k) {
@@ -103,6 +104,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
     sh.have_best = 0;
     sh.have_last = 0;
     sh.busy_a = sh.busy_b = 0;
+    sh.lat_a = 0;
+    sh.tc = 0;
   }
 
   const int dlo = p.dep[2 * b], dhi = p.dep[2 * b + 1];
@@ -149,7 +152,10 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
       if (tid == 0) {
         part[b * kPartSlots + 0] = v[0];
         part[b * kPartSlots + 1] = v[1];
-        sh.busy_a += (unsigned long long)(globaltimer_ns() - sh.tmark);
+        const long long now = globaltimer_ns();
+        sh.busy_a += (unsigned long long)(now - sh.tmark);
+        // how late this CTA's y is: phase C, the neighbour wait and phase A
+        if (sh.tc) sh.lat_a += (unsigned long long)(now - sh.tc);
       }
     }
     const bool skip = (p.skip_arrival == t) && (b == 0);
@@ -290,7 +296,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
     if (sh.brk) break;
 
     // ---- phase C: project, update, normalise; partial ||x_t||^2
-    if (tid == 0) sh.tmark = globaltimer_ns();
+    if (tid == 0) sh.tc = sh.tmark = globaltimer_ns();
     {
       const double a1c = sh.c, inv = sh.inv;
       const int nb = sh.nb;
@@ -319,6 +325,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
     p.cta_ns[2 * b] = sh.busy_a;
     p.cta_ns[2 * b + 1] = sh.busy_b;
   }
+  if (tid == 0 && p.cta_lat) p.cta_lat[b] = sh.lat_a;
   if (b == 0 && tid == 0) {
     if (status == PA_ERR_TIMEOUT || ld_relaxed_u32(&st->abort) != 0u) sh.status = PA_ERR_TIMEOUT;
     st->status = sh.status;
