@@ -53,14 +53,16 @@ __device__ __forceinline__ bool group_barrier(unsigned* counter, unsigned& targe
     while (true) {
       const unsigned c = ld_acquire_u32(counter);
       if ((int)(c - target) >= 0) break;
-      if (ld_relaxed_u32(&st->abort) != 0u) { ok = 0; break; }
-      if (++spins > 64) {
-        if (globaltimer_ns() - t0 > timeout_ns) {
-          atomicExch(&st->abort, 1u);
-          ok = 0;
-          break;
+      if ((++spins & 7) == 0) {  // abort flag and clock every 8th poll
+        if (ld_relaxed_u32(&st->abort) != 0u) { ok = 0; break; }
+        if (spins > 64) {
+          if (globaltimer_ns() - t0 > timeout_ns) {
+            atomicExch(&st->abort, 1u);
+            ok = 0;
+            break;
+          }
+          __nanosleep(64);
         }
-        __nanosleep(64);
       }
     }
     __threadfence();

@@ -306,14 +306,18 @@ __device__ __forceinline__ bool grid_barrier(RunState* st, unsigned& target, uns
     while (true) {
       const unsigned c = ld_acquire_u32(&st->barrier);
       if ((int)(c - target) >= 0) break;
-      if (ld_relaxed_u32(&st->abort) != 0u) { ok = 0; break; }
-      if (++spins > 64) {
-        if (globaltimer_ns() - t0 > timeout_ns) {
-          if (atomicExch(&st->abort, 1u) == 0u) st->timeout_site = site;
-          ok = 0;
-          break;
+      // the abort flag and the clock every 8th poll: one L2 round trip per
+      // poll, not two, while the barrier is about to complete
+      if ((++spins & 7) == 0) {
+        if (ld_relaxed_u32(&st->abort) != 0u) { ok = 0; break; }
+        if (spins > 64) {
+          if (globaltimer_ns() - t0 > timeout_ns) {
+            if (atomicExch(&st->abort, 1u) == 0u) st->timeout_site = site;
+            ok = 0;
+            break;
+          }
+          __nanosleep(64);
         }
-        __nanosleep(64);
       }
     }
     __threadfence();
@@ -341,14 +345,16 @@ __device__ __forceinline__ bool wait_ready(RunState* st, const unsigned* ready, 
       while (true) {
         const unsigned c = ld_acquire_u32(ready + j);
         if ((int)(c - t) >= 0) break;
-        if (ld_relaxed_u32(&st->abort) != 0u) { ok = 0; break; }
-        if (++spins > 64) {
-          if (globaltimer_ns() - t0 > timeout_ns) {
-            if (atomicExch(&st->abort, 1u) == 0u) st->timeout_site = site;
-            ok = 0;
-            break;
+        if ((++spins & 7) == 0) {  // abort flag and clock every 8th poll
+          if (ld_relaxed_u32(&st->abort) != 0u) { ok = 0; break; }
+          if (spins > 64) {
+            if (globaltimer_ns() - t0 > timeout_ns) {
+              if (atomicExch(&st->abort, 1u) == 0u) st->timeout_site = site;
+              ok = 0;
+              break;
+            }
+            __nanosleep(32);
           }
-          __nanosleep(32);
         }
       }
     }
