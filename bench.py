@@ -580,6 +580,66 @@ def _lu_factors(A):
             np.argsort(lu.perm_c).astype(np.int32))
 
 
+def run_hydro21(args):
+    """The small configuration: the 21 x 21 hydro operator (2,646 rows, 4
+    inclusions, seed 1), FP64, 2000 sigma_max + 2000 sigma_min iterations of
+    Algorithm 1 per estimate on the thread-block-cluster engine (the grid
+    engine's time beside it), and sigma_min through COLAMD LU factors
+    (Algorithm 2, 500 iterations) for the kappa_2 the direct route cannot
+    reach on this operator."""
+    if _dist()[0] > 1:
+        raise SystemExit("this workload runs on one GPU (launch it without torchrun)")
+    import torch
+    from paper_2409_11515_gb300 import build, pa, synth
+    build.build()
+    pa.load()
+    torch.cuda.set_device(0)
+    A = synth.hydro_operator(21, seed=1)
+    stream = torch.cuda.Stream()
+    it = (2000, 2000)
+    res = {}
+    for name, engine in (("cluster", pa.ENGINE_CLUSTER), ("grid", pa.ENGINE_GRID)):
+        with pa.create(A, stream=stream, engine=engine, grid_blocks=16) as h:
+            for _ in range(args.warmup):
+                h.estimate(pa.BOTH, 50, seed=START_SEED, **HYPER)
+            times = []
+            for _ in range(args.steps):
+                r, dt = _timed(stream, lambda: h.estimate(pa.BOTH, it[0], seed=START_SEED, **HYPER))
+                times.append(dt)
+            res[name] = {"iterations_per_s": (it[0] + it[1]) * len(times) / sum(times),
+                         "us_per_iteration": 1e6 * sum(times) / ((it[0] + it[1]) * len(times)),
+                         "sigma_max": r["sigma_max"], "sigma_min_direct": r["sigma_min"]}
+    f = _lu_factors(A)
+    with pa.create(A, stream=stream) as h:
+        h.attach_lu(*f)
+        h.estimate(pa.SIGMA_MIN_LU, 20, seed=START_SEED, **HYPER)
+        rl, tl = _timed(stream, lambda: h.estimate(pa.BOTH_LU, 500, seed=START_SEED, **HYPER))
+    import oracle
+    oracle.build()
+    x0 = oracle.start_vector(A.n_cols, START_SEED)
+    t0 = time.perf_counter()
+    oracle.projected_adam(A, oracle.SIGMA_MAX, it[0], x_init=x0, **HYPER)
+    oracle.projected_adam(A, oracle.SIGMA_MIN, it[1], x_init=x0, **HYPER)
+    t_cpu = time.perf_counter() - t0
+    c = res["cluster"]
+    line = {
+        "metric": METRIC, "value": c["iterations_per_s"], "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * (it[0] + it[1]) / c["iterations_per_s"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded hydro-mechanical operator)",
+        "config": {"workload": "hydro-mechanical 21x21 cells, 2,646 rows, 2000 sigma_max + 2000 "
+                               "sigma_min iterations, thread-block-cluster engine (16 CTAs)",
+                   "n_rows": int(A.n_rows), "nnz": int(A.nnz), "l2": "working set inside L2"},
+        "engines": res,
+        "lu_route": {"sigma_max": rl["sigma_max"], "sigma_min": rl["sigma_min"], "kappa": rl["kappa"],
+                     "estimate_s": tl, "iters": 500},
+        "cpu_baseline": {"value": (it[0] + it[1]) / t_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "2000 + 2000 iterations of the same operator (serial C oracle)"},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_lu64(args):
     """The paper's full kappa_2 route on many small operators: 64 hydro
     operators with sides drawn from 7..31 cells (seed 6), 8 restarts each;
@@ -666,10 +726,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision leg")
-    ap.add_argument("--workload", choices=["hydro401", "batched", "mixed1001", "stress2001",
-                                           "lu64"],
+    ap.add_argument("--workload", choices=["hydro401", "hydro21", "batched", "mixed1001",
+                                           "stress2001", "lu64"],
                     default="hydro401",
-                    help="hydro401: the benchmark line; batched: 64 operators x 8 restarts; "
+                    help="hydro401: the benchmark line; hydro21: the small operator (cluster "
+                         "engine, LU route); batched: 64 operators x 8 restarts; "
                          "mixed1001: 1001x1001 mixed vs FP64; stress2001: 2001x1001, 32 restarts; "
                          "lu64: 64 small operators, kappa through the LU route")
     ap.add_argument("--iters-max", type=int, default=ITERS_MAX,
@@ -687,6 +748,8 @@ def main():
         return run_stress2001(args)
     if args.workload == "lu64":
         return run_lu64(args)
+    if args.workload == "hydro21":
+        return run_hydro21(args)
     return run_ours(args)
 
 

@@ -102,7 +102,7 @@ struct pa_ctx {
   int32_t* lu_p = nullptr;        // row permutation (null = identity)
   std::vector<void*> lu_bufs;     // device arrays of the factors
   double* xmin_lu = nullptr;      // x_min of the latest LU-route run (source order)
-  double *lu_w = nullptr, *lu_t = nullptr, *lu_u = nullptr, *lu_a = nullptr, *lu_c = nullptr;
+  double *lu_w = nullptr, *lu_y = nullptr;  // s = P^T c, the solve vector (global fallback)
   LuParams* lu_params = nullptr;  // device copy of the latest run's parameters
   double *xmin_max = nullptr, *xmin_min = nullptr;
   RunState* st = nullptr;
@@ -872,16 +872,15 @@ static pa_status to_host(pa_ctx* h, const T* src, size_t count, int kind, std::v
 }
 
 static pa_status upload_tri(pa_ctx* h, const TriHost& t, TriSys* out) {
-  int32_t *rp, *ci, *order, *lvl;
-  double *va, *diag;
-  int4 *lvinfo, *pos;
+  double *dinv, *va;
+  int4 *linfo, *items;
+  int32_t* ci;
   pa_status st;
-  if ((st = upload(h, t.rp, &rp, "LU factor")) || (st = upload(h, t.ci, &ci, "LU factor")) ||
-      (st = upload(h, t.va, &va, "LU factor")) || (st = upload(h, t.diag, &diag, "LU factor")) ||
-      (st = upload(h, t.order, &order, "LU levels")) || (st = upload(h, t.lvl, &lvl, "LU levels")) ||
-      (st = upload(h, t.lvinfo, &lvinfo, "LU levels")) || (st = upload(h, t.pos, &pos, "LU levels")))
+  if ((st = upload(h, t.dinv, &dinv, "LU factor")) || (st = upload(h, t.linfo, &linfo, "LU steps")) ||
+      (st = upload(h, t.items, &items, "LU steps")) || (st = upload(h, t.ci, &ci, "LU factor")) ||
+      (st = upload(h, t.va, &va, "LU factor")))
     return st;
-  *out = TriSys{(int32_t)t.lvl.size() - 1, rp, ci, va, diag, order, lvl, lvinfo, pos};
+  *out = TriSys{t.nproc, t.max_items, t.max_ent, dinv, linfo, items, ci, va};
   return PA_OK;
 }
 
@@ -954,10 +953,7 @@ extern "C" pa_status pa_attach_lu(pa_handle h, const int32_t* l_row_ptr, const i
   if (!h->xmin_lu &&
       ((st = alloc_n(h, &h->xmin_lu, (size_t)n, "x_min")) ||
        (st = alloc_n(h, &h->lu_w, (size_t)n, "LU vectors")) ||
-       (st = alloc_n(h, &h->lu_t, (size_t)n, "LU vectors")) ||
-       (st = alloc_n(h, &h->lu_u, (size_t)n, "LU vectors")) ||
-       (st = alloc_n(h, &h->lu_a, (size_t)n, "LU vectors")) ||
-       (st = alloc_n(h, &h->lu_c, (size_t)n, "LU vectors"))))
+       (st = alloc_n(h, &h->lu_y, (size_t)n, "LU vectors"))))
     return (free_lu(h), st);
   h->have_lu = true;
   return PA_OK;
@@ -992,10 +988,7 @@ static pa_status lu_run(pa_ctx* h, const double* x0, int iters, double lr, doubl
   p.v = h->v;
   p.dx = h->dx;
   p.w = h->lu_w;
-  p.t = h->lu_t;
-  p.u = h->lu_u;
-  p.a = h->lu_a;
-  p.c = h->lu_c;
+  p.y = h->lu_y;
   p.bias = h->bias;
   p.L_trace = L_trace_dev;
   p.x_trace = x_trace_dev;
@@ -1005,11 +998,11 @@ static pa_status lu_run(pa_ctx* h, const double* x0, int iters, double lr, doubl
   p.t0 = 0;
   p.beta1 = b1;
   p.beta2 = b2;
-  p.smem_mode = lu_smem_bytes(p, 1) ? 1 : 0;
+  const size_t smem = lu_layout(&p);
   if (!h->lu_params && (st = alloc_n(h, &h->lu_params, 1, "LU run parameters"))) return st;
   if ((e = cudaMemcpyAsync(h->lu_params, &p, sizeof(LuParams), cudaMemcpyHostToDevice, h->stream)) ||
       (e = cudaStreamSynchronize(h->stream)) ||  // p lives on this stack frame
-      (e = launch_lu_iter(h->lu_params, 1, lu_smem_bytes(p, p.smem_mode), h->stream, &h->launches)) ||
+      (e = launch_lu_iter(h->lu_params, 1, smem, p.smem_mode == 1, h->stream, &h->launches)) ||
       (e = cudaMemcpyAsync(out, h->st, sizeof(RunState), cudaMemcpyDeviceToHost, h->stream)) ||
       (e = cudaStreamSynchronize(h->stream)))
     return cuda_fail(e, "running the LU route");
@@ -1622,13 +1615,14 @@ static pa_status batched_lu(const pa_handle* hs, int n_mat, int k_restarts, int 
     return cuda_fail(e, "preparing the LU items");
   std::vector<LuParams> items((size_t)n_items);
   size_t smem = 0;
+  bool all_smem = true;
   for (int i = 0; i < n_mat; ++i) {
     pa_ctx* hi = hs[i];
     const size_t n = (size_t)hi->n_rows;
     for (int r = 0; r < k_restarts; ++r) {
       const int it = i * k_restarts + r;
       double* buf = nullptr;
-      if ((st = sc.get(&buf, 10 * n, "LU item vectors"))) return st;
+      if ((st = sc.get(&buf, 7 * n, "LU item vectors"))) return st;
       LuParams& p = items[it];
       p.n = hi->n_rows;
       p.L = hi->lu_sys[0];
@@ -1642,17 +1636,14 @@ static pa_status batched_lu(const pa_handle* hs, int n_mat, int k_restarts, int 
       p.v = buf + 3 * n;
       p.dx = buf + 4 * n;
       p.w = buf + 5 * n;
-      p.t = buf + 6 * n;
-      p.u = buf + 7 * n;
-      p.a = buf + 8 * n;
-      p.c = buf + 9 * n;
+      p.y = buf + 6 * n;
       p.bias = bias;
       p.st = states + it;
       p.iters = iters;
       p.beta1 = b1;
       p.beta2 = b2;
-      p.smem_mode = lu_smem_bytes(p, 1) ? 1 : 0;
-      smem = std::max(smem, lu_smem_bytes(p, p.smem_mode));
+      smem = std::max(smem, lu_layout(&p));
+      all_smem = all_smem && p.smem_mode == 1;
       // item (i, r): SplitMix64 output i * k_restarts + r of `seed`, source order
       const uint64_t s_ir = splitmix64_at(seed, (uint64_t)it);
       if ((e = launch_start_vector(hi->n_rows, s_ir, nullptr, p.x, blockpart, s, &h0->launches)) ||
@@ -1663,7 +1654,7 @@ static pa_status batched_lu(const pa_handle* hs, int n_mat, int k_restarts, int 
   }
   std::vector<RunState> rs((size_t)n_items);
   if ((e = cudaMemcpyAsync(items_dev, items.data(), sizeof(LuParams) * n_items, cudaMemcpyHostToDevice, s)) ||
-      (e = launch_lu_iter(items_dev, n_items, smem, s, &h0->launches)) ||
+      (e = launch_lu_iter(items_dev, n_items, smem, all_smem, s, &h0->launches)) ||
       (e = cudaMemcpyAsync(rs.data(), states, sizeof(RunState) * n_items, cudaMemcpyDeviceToHost, s)) ||
       (e = cudaStreamSynchronize(s)))
     return cuda_fail(e, "running the batched LU route");

@@ -239,51 +239,68 @@ cudaError_t launch_equilibrate(int32_t n_rows, int32_t n_cols, const int32_t* rp
                                const double* vat, double* d_row, double* d_col, cudaStream_t s,
                                int64_t* launches);
 // ---- Algorithm 2 (sigma_min through ||A^{-1}|| with given LU factors) ----
-// One triangular system in level-scheduled form, stored in level order:
-// position k holds row order[k]; positions lvl[l] .. lvl[l+1] are the rows of
-// level l, which depend only on rows of earlier levels; the off-diagonal
-// entries of position k are ci/va[rp[k] .. rp[k+1]) (a level's entries are
-// contiguous) and diag[k] is the reciprocal of its diagonal entry.
+// One triangular system T x = b in level-scheduled, column-level form.  A
+// row's level is one more than the highest level of the rows it depends on.
+// Each row's off-diagonal entries are split into segments by the level of
+// their column; the segment whose columns are at level l is applied in step l
+// (l = 0 .. nproc-1, nproc = levels - 1), when those x_j are final:
+//   x_i <- x_i + sum_{j in segment} va_ij x_j,  va_ij = -T_ij / T_ii,
+// starting from x_i = b_i / T_ii (dinv), so a row is final after its last
+// segment and no step needs a division or a subtraction.  Step l's items
+// (one per segment) are items[linfo[l].x .. linfo[l].y & kItemMask); a
+// one-entry segment is the item {row, column, value as two words}, a longer
+// one {~row, first entry, end entry, 0} with its entries in ci/va, and step
+// l's entries are ci/va[linfo[l].z .. linfo[l].w).  Bits 27.. of linfo[l].y
+// hold log2 of the lanes per item.  ci/va are padded so that 16-byte windows
+// around any step's entries stay inside.
+constexpr int kItemMask = (1 << 27) - 1;
 struct TriSys {
-  int32_t nlev;
-  const int32_t* rp; const int32_t* ci; const double* va; const double* diag;
-  const int32_t* order; const int32_t* lvl;
-  const int4* lvinfo;  // [nlev] per level {first position, end position, first entry, end entry}
-  const int4* pos;     // [n] per position {first entry, end entry, row, 0}
+  int32_t nproc;
+  int32_t max_items;   // most items in one step
+  int32_t max_ent;     // largest 16-byte window of one step's entries
+  const double* dinv;  // [n] 1 / T_ii
+  const int4* linfo;   // [nproc]
+  const int4* items;
+  const int32_t* ci;
+  const double* va;
 };
 // Algorithm 1 on B = A^{-1} = Q U^{-1} L^{-1} P, everything in source order.
 struct LuParams {
   int32_t n;
-  TriSys L, U, Ut, Lt;       // L t = w, U u = t, U^T a = u, L^T c = a
+  TriSys L, U, Ut, Lt;       // L t = P x, U u = t, U^T a = u, L^T c = a
   const int32_t* p;          // [n] row i of P A is row p[i] of A (null = identity)
   double* x; double* xmin;   // iterate, tracked maximiser of ||B x|| / ||x||
   double* m; double* v; double* dx;
-  double* w; double* t; double* u; double* a; double* c;  // solve vectors
+  double* w;                 // s = P^T c
+  double* y;                 // the solve vector when it is not in shared memory
   const double2* bias;       // as IterParams
   double* L_trace; double* x_trace; int n_trace;
   RunState* st;
   int iters, t0;
   double beta1, beta2;
-  int smem_mode;             // 0: all in global memory; 1: the five solve vectors
-                             // in shared memory
+  int smem_mode;             // 1: the solve vector in shared memory; 0: in global
+  int slot_items, slot_ent;  // items and entries one staging slot holds
 };
 constexpr int kLuThreads = 512;
-constexpr size_t kLuSmemBudget = 200 * 1024;  // dynamic shared memory the LU kernel may use
-// Dynamic shared memory of a given mode (0 when the mode does not fit).
-size_t lu_smem_bytes(const LuParams& p, int mode);
+constexpr size_t kLuSmemBudget = 218 * 1024;  // dynamic shared memory the LU kernel may use
+// Chooses p->smem_mode and the slot sizes from n and the factors' largest steps;
+// returns the item's dynamic shared memory.
+size_t lu_layout(LuParams* p);
 // Items (device array of n_items LuParams, each with its own vectors and run
 // state), one CTA each; smem = the dynamic shared memory of the launch, which
-// must cover lu_smem_bytes(item, item.smem_mode) of every item.
-cudaError_t launch_lu_iter(const LuParams* items_dev, int n_items, size_t smem, cudaStream_t s,
-                           int64_t* launches);
+// must cover lu_layout() of every item; all_smem: every item has smem_mode 1
+// (else all items run with their solve vector in global memory).
+cudaError_t launch_lu_iter(const LuParams* items_dev, int n_items, size_t smem, bool all_smem,
+                           cudaStream_t s, int64_t* launches);
 // Host analysis for TriSys: checks triangularity and non-zero diagonals,
-// splits off the diagonal and computes the levels.  lower: row i depends on
+// computes the levels and builds the step lists.  lower: row i depends on
 // columns j < i; else on j > i.  Returns an empty string or the reason the
 // factor is unusable.
 struct TriHost {
-  std::vector<int32_t> rp, ci, order, lvl;
-  std::vector<double> va, diag;
-  std::vector<int4> lvinfo, pos;
+  int32_t nproc = 0, max_items = 0, max_ent = 0;
+  std::vector<double> dinv, va;
+  std::vector<int4> linfo, items;
+  std::vector<int32_t> ci;
 };
 std::string tri_analyse(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
                         bool lower, TriHost* out);
