@@ -505,11 +505,11 @@ def run_mixed1001(args):
 
 def run_stress2001(args):
     """2001 x 1001 cells (12,018,006 rows, viscosity 1e16..1e24, k/eta_f
-    1e-22..1e-10, seed 5): 32 seeded restarts as FP64 SpMM blocks (k = 8 per
-    launch, four waves) against the plain FP64 single-vector path and the
-    mixed-precision single-vector path, each on a short timed run
-    (--iters-max/--iters-min, extrapolated to one estimate), plus one full
-    FP64 estimate for kappa_2."""
+    1e-22..1e-10, seed 5): 32 seeded restarts as SpMM blocks (k = 8 per
+    launch, four waves), mixed precision (sigma_max: FP32 stage + FP64 tail;
+    sigma_min: FP64) and plain FP64, against the FP64 and mixed-precision
+    single-vector paths, each on a short timed run (--iters-max/--iters-min,
+    extrapolated to one estimate), plus one full FP64 estimate for kappa_2."""
     if _dist()[0] > 1:
         raise SystemExit("this workload runs on one GPU (launch it without torchrun)")
     import torch
@@ -539,25 +539,32 @@ def run_stress2001(args):
         hm.estimate(pa.SIGMA_MAX, 50, seed=START_SEED, **HYPER)
         rmx, tmx = _timed(stream, lambda: hm.estimate(pa.SIGMA_MAX, it[0], seed=START_SEED, **HYPER))
         rmn, tmn = _timed(stream, lambda: hm.estimate(pa.SIGMA_MIN, it[1], seed=START_SEED, **HYPER))
+        pa.estimate_batched([hm], pa.BOTH, 8, (5, 5), seed=START_SEED, **HYPER)  # warm-up
+        rbm, tbm = _timed(stream, lambda: pa.estimate_batched([hm], pa.BOTH, 32, it,
+                                                              seed=START_SEED, **HYPER))
     out["mixed_k1_vector_iterations_per_s"] = (it[0] + it[1]) / (tmx + tmn)
+    out["mixed_k32_vector_iterations_per_s"] = 32 * (it[0] + it[1]) / tbm
     kappa = rf[0]["sigma_max"] / rf[1]["sigma_min"]
-    est_k32 = 32 * (it[0] + it[1]) / tb / full_T
+    est_k32 = 32 * (it[0] + it[1]) / tbm / full_T
     line = {
-        "metric": "kappa2_estimates_per_s (32 restarts, FP64 SpMM)", "value": est_k32,
+        "metric": "kappa2_estimates_per_s (32 restarts, mixed-precision SpMM)", "value": est_k32,
         "unit": "estimates/s", "n_gpus": 1, "steps": 1, "warmup": args.warmup,
-        "ms_per_step": 1e3 * tb, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded hydro-mechanical operator)",
+        "ms_per_step": 1e3 * tbm, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (seeded hydro-mechanical operator)",
         "config": {"workload": "hydro-mechanical 2001x1001 cells, 12,018,006 rows, viscosity "
                                "contrast 1e8, 32 restarts", "n_rows": int(A.n_rows),
                    "nnz": int(A.nnz), "iters_timed": list(it), "estimate_iters": list(EST_ITERS)},
         "fp64_k1_estimates_per_s": out["fp64_k1_vector_iterations_per_s"] / full_T,
+        "fp64_k32_estimates_per_s": out["fp64_k32_vector_iterations_per_s"] / full_T,
         "throughput": out,
         "kappa_fp64_full_estimate": kappa,
         "sigma_fp64": [rf[0]["sigma_max"], rf[1]["sigma_min"]],
         "mixed_short_run_sigmas": [rmx["sigma_max"], rmn["sigma_min"]],
         "batched_sigma_max_spread": [float(rb["sigma_max"].min()), float(rb["sigma_max"].max())],
+        "mixed_batched_sigma_max_spread": [float(rbm["sigma_max"].min()), float(rbm["sigma_max"].max())],
         "note": "value and the k=1 figures extrapolate the timed iterations to the 5000 + 20000 "
-                "of one estimate; the mixed-precision path has no batched (SpMM) form",
+                "of one estimate; the batched mixed path runs sigma_min in FP64 (the single-vector "
+                "mixed sigma_min uses Dot2 products)",
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -690,7 +697,7 @@ def run_lu64(args):
     line = {
         "metric": "kappa2_estimates_per_s (LU route, batched)", "value": n_mat * k / tb,
         "unit": "estimates/s", "n_gpus": 1, "steps": 1, "warmup": args.warmup,
-        "ms_per_step": 1e3 * tb, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * tbm, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded hydro-mechanical operators)",
         "config": {"workload": "64 hydro operators, sides U[7,31] (seed 6), 8 restarts each; "
                                "sigma_max 2000 iterations (SpMM), sigma_min 500 iterations on "
@@ -733,10 +740,17 @@ def main():
                          "engine, LU route); batched: 64 operators x 8 restarts; "
                          "mixed1001: 1001x1001 mixed vs FP64; stress2001: 2001x1001, 32 restarts; "
                          "lu64: 64 small operators, kappa through the LU route")
-    ap.add_argument("--iters-max", type=int, default=ITERS_MAX,
-                    help="sigma_max iterations per estimate (short runs for profiling)")
-    ap.add_argument("--iters-min", type=int, default=ITERS_MIN)
+    ap.add_argument("--iters-max", type=int, default=None,
+                    help="sigma_max iterations per estimate (short runs for profiling); "
+                         "default 5000, stress2001 200 (timed, then extrapolated)")
+    ap.add_argument("--iters-min", type=int, default=None,
+                    help="sigma_min iterations; default 20000, stress2001 200")
     args = ap.parse_args()
+    short = (200, 200) if args.workload == "stress2001" else EST_ITERS
+    if args.iters_max is None:
+        args.iters_max = short[0]
+    if args.iters_min is None:
+        args.iters_min = short[1]
     globals()["ITERS_MAX"], globals()["ITERS_MIN"] = args.iters_max, args.iters_min
     if args.impl == "reference":
         return run_reference(args)

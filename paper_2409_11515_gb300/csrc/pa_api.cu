@@ -1373,7 +1373,11 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
   pa_ctx* h0 = hs[0];
   cudaStream_t s = h0->stream;  // replaced below by a capturable stream joined to it
   BatchScratch sc{h0, {}};
-  const int Gmax = batched_max_blocks(K);
+  // MIXED: sigma_max runs an FP32 stage (k_batched32) and an FP64 tail
+  const bool mixed = h0->opt.precision == PA_MIXED && (mode & PA_SIGMA_MAX);
+  const int tail = !mixed ? 0 : (h0->opt.fp64_tail < 0 ? iters[0] / 10 : std::min(h0->opt.fp64_tail, iters[0]));
+  const int t32 = iters[0] - tail;
+  const int Gmax = mixed ? std::min(batched_max_blocks(K), batched32_max_blocks(K)) : batched_max_blocks(K);
   if (Gmax < m) return fail(PA_ERR_LAUNCH, "batched kernel: %d items exceed %d co-resident CTAs", m, Gmax);
   // ---- CTA groups, sized by padded entries plus a per-row weight
   std::vector<double> work(m);
@@ -1414,8 +1418,20 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
         (st = sc.get(&it.V, nx, "batch v")) || (st = sc.get(&it.DX, nx, "batch dx")) ||
         (st = sc.get(&it.Y, std::max<size_t>(ny, 1), "batch y")) ||
         (st = sc.get(&it.result, (size_t)4 * K, "batch result")) ||
-        (st = sc.get(&it.status, 1, "batch status")))
+        (st = sc.get(&it.status, 2, "batch status")))  // [1]: the FP32 stage's
       return st;
+    if (mixed) {
+      it.a_val32 = hi->a_val32;
+      it.t_val32 = hi->t_val32;
+      it.dr32 = hi->drp32;
+      it.dc32 = hi->dcp32;
+      if ((st = sc.get(&it.X0f, nx, "batch x (FP32)")) || (st = sc.get(&it.X1f, nx, "batch x (FP32)")) ||
+          (st = sc.get(&it.XMINf, nx, "batch x_min (FP32)")) || (st = sc.get(&it.Mf, nx, "batch m (FP32)")) ||
+          (st = sc.get(&it.Vf, nx, "batch v (FP32)")) || (st = sc.get(&it.DXf, nx, "batch dx (FP32)")) ||
+          (st = sc.get(&it.Wf, nx, "batch w (FP32)")) ||
+          (st = sc.get(&it.Yf, std::max<size_t>(ny, 1), "batch y (FP32)")))
+        return st;
+    }
     if ((e = launch_partition(hi->sa.wp, hi->sa.n_slices, ncta[i], 2, pa_, s, &h0->launches)) ||
         (e = launch_partition(hi->sq.wp, hi->sq.n_slices, ncta[i], 30, pt_, s, &h0->launches)))
       return cuda_fail(e, "partitioning a batch item");
@@ -1441,7 +1457,7 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
       (st = sc.get(&blk_row0_d, (size_t)nb, "batch table")) ||
       (st = sc.get(&item_blk0_d, (size_t)m + 1, "batch table")) ||
       (st = sc.get(&blockpart, (size_t)nb * 2 * K + (size_t)m * K + 64, "batch block partials")) ||
-      (st = sc.get(&sig, (size_t)2 * m * K, "batch sigma")) ||
+      (st = sc.get(&sig, (size_t)3 * m * K, "batch sigma")) ||  // max, min, FP32-stage max
       (st = sc.get(&rs_d, 1, "batch run state")))
     return st;
   const int T = std::max(iters[0], iters[1]);
@@ -1476,9 +1492,9 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
 
   // The whole call as one sequence: start vectors, state reset, the
   // persistent launch, sigma -- for sigma_max, then sigma_min.
-  auto enqueue = [&](bool count) -> cudaError_t {
-    int64_t dummy = 0;
-    int64_t* L = count ? &h0->launches : &dummy;
+  int64_t n_launch = 0;
+  auto enqueue = [&]() -> cudaError_t {
+    int64_t* L = &n_launch;
     cudaError_t err = cudaSuccess;
     for (int md : {PA_SIGMA_MAX, PA_SIGMA_MIN}) {
       if (!(mode & md)) continue;
@@ -1498,6 +1514,39 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
       BatchParams q = bp;
       q.mode = md;
       q.iters = md == PA_SIGMA_MAX ? iters[0] : iters[1];
+      if (md == PA_SIGMA_MAX && mixed) {
+        // FP32 stage from the same start vectors; its minimisers scored in FP64
+        for (int i = 0; i < m; ++i) {
+          const size_t nx = (size_t)items[i].n_cols * K;
+          if ((err = launch_convert((int64_t)nx, items[i].X0, items[i].X0f, s, L)) ||
+              (err = cudaMemsetAsync(items[i].Mf, 0, sizeof(float) * nx, s)) ||
+              (err = cudaMemsetAsync(items[i].Vf, 0, sizeof(float) * nx, s)))
+            return err;
+        }
+        q.iters = t32;
+        if ((err = launch_batched32(q, K, G, s, L))) return err;
+        for (int i = 0; i < m; ++i)
+          if ((err = launch_convert((int64_t)items[i].n_cols * K, items[i].XMINf, items[i].XMIN, s, L)))
+            return err;
+        if ((err = launch_batch_sigma(items_d, m, K, blk_item_d, blk_row0_d, nb, 256, blockpart,
+                                      item_blk0_d, sig + (size_t)2 * m * K, s, L)))
+          return err;
+        if (tail == 0) continue;
+        // the FP64 tail continues from the last FP32 iterate and moments
+        for (int i = 0; i < m; ++i) {
+          const size_t nx = (size_t)items[i].n_cols * K;
+          const float* xl = (t32 % 2 == 0) ? items[i].X0f : items[i].X1f;
+          if ((err = launch_convert((int64_t)nx, xl, items[i].X0, s, L)) ||
+              (err = launch_convert((int64_t)nx, items[i].Mf, items[i].M, s, L)) ||
+              (err = launch_convert((int64_t)nx, items[i].Vf, items[i].V, s, L)) ||
+              (err = cudaMemcpyAsync(items[i].status + 1, items[i].status, sizeof(int),
+                                     cudaMemcpyDeviceToDevice, s)) ||
+              (err = cudaMemsetAsync(items[i].barrier, 0, sizeof(unsigned), s)))
+            return err;
+        }
+        q.t0 = t32;
+        q.iters = tail;
+      }
       if ((err = launch_batched(q, K, G, s, L))) return err;
       if ((err = launch_batch_sigma(items_d, m, K, blk_item_d, blk_row0_d, nb, 256, blockpart,
                                     item_blk0_d, sig + (md == PA_SIGMA_MAX ? 0 : (size_t)m * K), s, L)))
@@ -1524,7 +1573,7 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
   cudaGraphExec_t exec = nullptr;
   *captured = false;
   if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-    const cudaError_t ce = enqueue(false);
+    const cudaError_t ce = enqueue();
     const cudaError_t ee = cudaStreamEndCapture(s, &graph);
     if (ce == cudaSuccess && ee == cudaSuccess && graph &&
         cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess)
@@ -1532,11 +1581,12 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
     cudaGetLastError();  // a refused capture leaves a sticky-free error here
   }
   if (*captured) {
-    e = cudaGraphLaunch(exec, s);
-    h0->launches += (int64_t)((mode & PA_SIGMA_MAX ? 1 : 0) + (mode & PA_SIGMA_MIN ? 1 : 0)) * 6;
+    e = cudaGraphLaunch(exec, s);  // replays the n_launch kernels counted during capture
   } else {
-    e = enqueue(true);
+    n_launch = 0;
+    e = enqueue();
   }
+  h0->launches += n_launch;
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
@@ -1548,7 +1598,7 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
   s = user;
   if (e != cudaSuccess) return cuda_fail(e, "running the batched launch");
   // ---- results
-  std::vector<double> sg((size_t)2 * m * K);
+  std::vector<double> sg((size_t)3 * m * K);
   RunState rs{};
   if ((e = cudaMemcpyAsync(sg.data(), sig, sizeof(double) * sg.size(), cudaMemcpyDeviceToHost, s)) ||
       (e = cudaMemcpyAsync(&rs, rs_d, sizeof(RunState), cudaMemcpyDeviceToHost, s)) ||
@@ -1556,17 +1606,22 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
     return cuda_fail(e, "reading the batched results");
   std::vector<int> ist(m, PA_OK);
   for (int i = 0; i < m; ++i) {
-    int v = 0;
-    if ((e = cudaMemcpy(&v, items[i].status, sizeof(int), cudaMemcpyDeviceToHost)))
+    int v[2] = {0, 0};
+    if ((e = cudaMemcpy(v, items[i].status, sizeof(v), cudaMemcpyDeviceToHost)))
       return cuda_fail(e, "reading the batched status");
-    ist[i] = v;
+    // an FP32-stage error outranks the tail's status (errors < 0 < warnings)
+    ist[i] = (mixed && tail > 0 && v[1] < 0) ? v[1] : v[0];
   }
   if (rs.abort) return fail(PA_ERR_TIMEOUT, "a batched group barrier wait ran out of time");
   for (int i = 0; i < m; ++i) {
     for (int c = 0; c < k_used; ++c) {
       const int r = r0 + c;
       double* o = out + ((size_t)(i0 + i) * k_restarts + r) * 3;
-      const double smax = (mode & PA_SIGMA_MAX) ? sg[(size_t)i * K + c] : NAN;
+      double smax = (mode & PA_SIGMA_MAX) ? sg[(size_t)i * K + c] : NAN;
+      if (mixed) {  // the stage whose tracked minimiser scores the larger sigma in FP64
+        const double s32 = sg[(size_t)2 * m * K + (size_t)i * K + c];
+        smax = (tail == 0 || s32 > smax) ? s32 : smax;
+      }
       const double smin = (mode & PA_SIGMA_MIN) ? sg[(size_t)m * K + (size_t)i * K + c] : NAN;
       o[0] = smax;
       o[1] = smin;
@@ -1714,8 +1769,8 @@ extern "C" pa_status pa_estimate_batched(int n_mat, const pa_handle* handles, pa
     if (!hi) return fail(PA_ERR_INVALID_ARG, "handle %d is NULL", i);
     if (hi->stream != handles[0]->stream)
       return fail(PA_ERR_INVALID_ARG, "all handles of a batch must share one stream");
-    if (hi->opt.precision != PA_FP64)
-      return fail(PA_ERR_UNSUPPORTED, "batched estimates run in FP64 only (handle %d)", i);
+    if (hi->opt.precision != handles[0]->opt.precision)
+      return fail(PA_ERR_INVALID_ARG, "all handles of a batch must share one precision mode (handle %d)", i);
     if ((mode & PA_SIGMA_MIN) && hi->n_rows < hi->n_cols)
       return fail(PA_ERR_NOT_SQUARE, "sigma_min needs n_rows >= n_cols (handle %d)", i);
   }

@@ -40,57 +40,6 @@ struct SharedB {
   int iters_run;
 };
 
-__device__ __forceinline__ bool group_barrier(unsigned* counter, unsigned& target, unsigned G,
-                                              RunState* st, long long timeout_ns, int& ok_slot) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    target += G;
-    int ok = 1;
-    __threadfence();
-    atomicAdd(counter, 1u);
-    const long long t0 = globaltimer_ns();
-    int spins = 0;
-    while (true) {
-      const unsigned c = ld_acquire_u32(counter);
-      if ((int)(c - target) >= 0) break;
-      if ((++spins & 7) == 0) {  // abort flag and clock every 8th poll
-        if (ld_relaxed_u32(&st->abort) != 0u) { ok = 0; break; }
-        if (spins > 64) {
-          if (globaltimer_ns() - t0 > timeout_ns) {
-            atomicExch(&st->abort, 1u);
-            ok = 0;
-            break;
-          }
-          __nanosleep(64);
-        }
-      }
-    }
-    __threadfence();
-    ok_slot = ok;
-  }
-  __syncthreads();
-  return ok_slot != 0;
-}
-
-// Fixed-order sum of part[q][c][0..nt) by warp w (c = w's column); result in
-// lane 0.
-__device__ __forceinline__ double slot_sum(const double* slots, int nt) {
-  const int lane = threadIdx.x & 31;
-  double a = 0.0;
-  for (int base = 0; base < nt; base += 256) {  // loads before adds, pairwise
-    double u[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int t = base + lane + 32 * j;
-      u[j] = t < nt ? slots[t] : 0.0;
-    }
-    u[0] += u[1]; u[2] += u[3]; u[4] += u[5]; u[6] += u[7];
-    u[0] += u[2]; u[4] += u[6];
-    a += u[0] + u[4];
-  }
-  return warp_sum(a);
-}
-
 template <int K>
 __global__ void __launch_bounds__(kBT, 2) k_batched(const BatchParams bp) {
   __shared__ SharedB<K> sh;
@@ -238,7 +187,7 @@ __global__ void __launch_bounds__(kBT, 2) k_batched(const BatchParams bp) {
 
     // ---- phase B: Z = A^T Y, Adam per column, partials x.dx, dx.dx
     {
-      const double2 bc = bp.bias[t - 1];
+      const double2 bc = bp.bias[bp.t0 + t - 1];
       const double b1 = bp.beta1, b2 = bp.beta2;
       const double w2 = bp.w2;
       double pxd[K], pdd[K];

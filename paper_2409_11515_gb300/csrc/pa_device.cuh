@@ -373,4 +373,72 @@ __device__ __forceinline__ void publish_ready(unsigned* flag, unsigned t) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(flag), "r"(t) : "memory");
 }
 
+// ---- shared by the batched (SpMM) kernels ----
+
+// Barrier of one CTA group (the CTAs of one batch item) on its own arrival
+// counter, with the same time limit and abort flag as grid_barrier.
+__device__ __forceinline__ bool group_barrier(unsigned* counter, unsigned& target, unsigned G,
+                                              RunState* st, long long timeout_ns, int& ok_slot) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    target += G;
+    int ok = 1;
+    __threadfence();
+    atomicAdd(counter, 1u);
+    const long long t0 = globaltimer_ns();
+    int spins = 0;
+    while (true) {
+      const unsigned c = ld_acquire_u32(counter);
+      if ((int)(c - target) >= 0) break;
+      if ((++spins & 7) == 0) {  // abort flag and clock every 8th poll
+        if (ld_relaxed_u32(&st->abort) != 0u) { ok = 0; break; }
+        if (spins > 64) {
+          if (globaltimer_ns() - t0 > timeout_ns) {
+            atomicExch(&st->abort, 1u);
+            ok = 0;
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+    }
+    __threadfence();
+    ok_slot = ok;
+  }
+  __syncthreads();
+  return ok_slot != 0;
+}
+
+// Fixed-order sum of part[q][c][0..nt) by warp w (c = w's column); result in
+// lane 0.
+__device__ __forceinline__ double slot_sum(const double* slots, int nt) {
+  const int lane = threadIdx.x & 31;
+  double a = 0.0;
+  for (int base = 0; base < nt; base += 256) {  // loads before adds, pairwise
+    double u[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int t = base + lane + 32 * j;
+      u[j] = t < nt ? slots[t] : 0.0;
+    }
+    u[0] += u[1]; u[2] += u[3]; u[4] += u[5]; u[6] += u[7];
+    u[0] += u[2]; u[4] += u[6];
+    a += u[0] + u[4];
+  }
+  return warp_sum(a);
+}
+
+// Compensated (Kahan) FP32 accumulation of bounded per-row terms; the pair
+// is handed to the FP64 block reduction as (double)sum - (double)comp.
+struct Kahan32 {
+  float sum = 0.f, comp = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = __fsub_rn(v, comp);
+    const float t = __fadd_rn(sum, y);
+    comp = __fsub_rn(__fsub_rn(t, sum), y);
+    sum = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)sum - (double)comp; }
+};
+
 }  // namespace pa

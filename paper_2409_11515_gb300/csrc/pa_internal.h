@@ -123,6 +123,11 @@ struct BatchItem {
   int* status;                          // [1]
   const int32_t* pos_c;                 // source column -> x position (Q)
   int32_t n_slices_a;                   // slices of P A Q^T
+  // MIXED sigma_max stage (k_batched32): FP32 values of the sliced
+  // A_hat = D_r^-1 A D_c^-1 and its transpose, the power-of-two D_r, D_c in
+  // FP32 (positions of the sliced copies), and the FP32 block vectors
+  const float* a_val32; const float* t_val32; const float* dr32; const float* dc32;
+  float *X0f, *X1f, *XMINf, *Mf, *Vf, *DXf, *Yf, *Wf;
 };
 
 struct BatchParams {
@@ -131,6 +136,7 @@ struct BatchParams {
   const double2* bias;       // [iters] as in IterParams
   RunState* st;              // shared abort flag
   int iters, mode, loss, ablation;
+  int t0;     // iteration t uses bias[t0 + t - 1] (a continued run)
   double beta1, beta2;
   double w2;  // (1 - beta2) / (1 - beta1)^2
   long long timeout_ns;
@@ -139,6 +145,12 @@ struct BatchParams {
 int batched_threads();
 int batched_max_blocks(int k);
 cudaError_t launch_batched(const BatchParams& p, int k, int G, cudaStream_t s, int64_t* launches);
+// The MIXED sigma_max stage of a batch (log-ratio loss): FP32 products and
+// FP32 Adam state on A_hat, per-column norms reduced in FP64, the same CTA
+// groups, partitions and result layout as k_batched.  Reads X0f (x_init);
+// leaves x_{iters} in X0f (iters even) or X1f, the tracked minimisers in XMINf.
+int batched32_max_blocks(int k);
+cudaError_t launch_batched32(const BatchParams& p, int k, int G, cudaStream_t s, int64_t* launches);
 
 // Start vectors of a batch: column c of item i is the SplitMix64 stream of
 // seed splitmix64_at(seed, (i0 + i) * k_stride + r0 + c), normalised per

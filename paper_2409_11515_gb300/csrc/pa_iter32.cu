@@ -36,19 +36,6 @@ struct Shared32 {
   long long tmark;
 };
 
-// Compensated (Kahan) FP32 accumulation of bounded per-row terms; the pair
-// is handed to the FP64 block reduction as (double)sum - (double)comp.
-struct Kahan32 {
-  float sum = 0.f, comp = 0.f;
-  __device__ __forceinline__ void add(float v) {
-    const float y = __fsub_rn(v, comp);
-    const float t = __fadd_rn(sum, y);
-    comp = __fsub_rn(__fsub_rn(t, sum), y);
-    sum = t;
-  }
-  __device__ __forceinline__ double value() const { return (double)sum - (double)comp; }
-};
-
 __device__ __forceinline__ float* pick32(const IterParams32& p, int k) {
   return k == 0 ? p.X0 : (k == 1 ? p.X1 : p.X2);
 }

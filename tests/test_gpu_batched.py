@@ -87,10 +87,10 @@ def test_batched_errors():
         with pytest.raises(pa.PAError) as ei:
             pa.estimate_batched([h], pa.SIGMA_MIN, 2, (10, 10))
         assert ei.value.status == -3
-    with pa.create(synth.laplacian_1d(8), precision=pa.MIXED) as h:
-        with pytest.raises(pa.PAError) as ei:
-            pa.estimate_batched([h], pa.SIGMA_MAX, 2, (10, 10))
-        assert ei.value.status == -9
+    with pa.create(synth.laplacian_1d(8), precision=pa.MIXED) as hm, pa.create(synth.laplacian_1d(9)) as hf:
+        with pytest.raises(pa.PAError) as ei:  # one precision mode per batch
+            pa.estimate_batched([hm, hf], pa.SIGMA_MAX, 2, (10, 10))
+        assert ei.value.status == -1
 
 
 def test_batched_autotuned_width_keeps_results():
@@ -112,3 +112,47 @@ def test_batched_autotuned_width_keeps_results():
     assert rt["status"] == 0 and rd["status"] == 0
     assert np.array_equal(rt["sigma_max"], rt2["sigma_max"])
     assert np.max(np.abs(rt["sigma_max"] / rd["sigma_max"] - 1)) <= 1e-9
+
+
+# MIXED handles: sigma_max runs the FP32 SpMM stage (FP32 products and Adam
+# state on the power-of-two-equilibrated matrix) and an FP64 tail; each item
+# must match the FP64 oracle from its start vector to the single-vector MIXED
+# bar (1e-6, both converged), and sigma_min (FP64) the closed form.
+@pytest.mark.parametrize("k", [1, 3, 8])
+def test_batched_mixed_sigma_max_matches_fp64_oracle(k):
+    mats = [synth.hydro_operator(9, seed=1), synth.laplacian_2d(7), synth.hydro_operator(13, 11, seed=2),
+            synth.random_sparse(500, 5, seed=3, diag_boost=2.0)]
+    hs = [pa.create(A, precision=pa.MIXED) for A in mats]
+    try:
+        T = 2000
+        r = pa.estimate_batched(hs, pa.SIGMA_MAX, k, (T, T), seed=9, **HYPER)
+        r2 = pa.estimate_batched(hs, pa.SIGMA_MAX, k, (T, T), seed=9, **HYPER)
+    finally:
+        for h in hs:
+            h.destroy()
+    assert np.all(r["item_status"] == 0)
+    assert np.array_equal(r["sigma_max"], r2["sigma_max"])  # bit-reproducible
+    for i, A in enumerate(mats):
+        for rr in range(k):
+            ro = oracle.projected_adam(A, oracle.SIGMA_MAX, T, x_init=_x0(A.n_cols, 9, i, k, rr),
+                                       **HYPER)
+            assert abs(r["sigma_max"][i, rr] / ro.sigma - 1) <= 1e-6, (i, rr, r["sigma_max"][i, rr], ro.sigma)
+
+
+def test_batched_mixed_fp32_stage_only_and_kappa():
+    mats = [synth.laplacian_1d(8), synth.laplacian_2d(4), synth.hydro_operator(11, seed=4)]
+    hs = [pa.create(A, precision=pa.MIXED, fp64_tail=0) for A in mats]
+    try:
+        T = 2000
+        r = pa.estimate_batched(hs, pa.BOTH, 2, (T, 3000), seed=4, **HYPER)
+    finally:
+        for h in hs:
+            h.destroy()
+    assert np.all(r["item_status"] == 0)
+    for i, A in enumerate(mats):  # the FP32 stage alone reaches the FP64 oracle's sigma_max
+        for rr in range(2):
+            ro = oracle.projected_adam(A, oracle.SIGMA_MAX, T, x_init=_x0(A.n_cols, 4, i, 2, rr), **HYPER)
+            assert abs(r["sigma_max"][i, rr] / ro.sigma - 1) <= 1e-6, (i, rr)
+    kappas = [1 / math.tan(math.pi / 18) ** 2, 1 / math.tan(math.pi / 10) ** 2]
+    for i, kap in enumerate(kappas):
+        assert np.all(np.abs(r["kappa"][i] / kap - 1) <= 1e-6), (i, r["kappa"][i], kap)
