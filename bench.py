@@ -507,7 +507,7 @@ def run_stress2001(args):
     """2001 x 1001 cells (12,018,006 rows, viscosity 1e16..1e24, k/eta_f
     1e-22..1e-10, seed 5): 32 seeded restarts as SpMM blocks (k = 8 per
     launch, four waves), mixed precision (sigma_max: FP32 stage + FP64 tail;
-    sigma_min: FP64) and plain FP64, against the FP64 and mixed-precision
+    sigma_min: Dot2 products) and plain FP64, against the FP64 and mixed-precision
     single-vector paths, each on a short timed run (--iters-max/--iters-min,
     extrapolated to one estimate), plus one full FP64 estimate for kappa_2."""
     if _dist()[0] > 1:
@@ -563,8 +563,8 @@ def run_stress2001(args):
         "batched_sigma_max_spread": [float(rb["sigma_max"].min()), float(rb["sigma_max"].max())],
         "mixed_batched_sigma_max_spread": [float(rbm["sigma_max"].min()), float(rbm["sigma_max"].max())],
         "note": "value and the k=1 figures extrapolate the timed iterations to the 5000 + 20000 "
-                "of one estimate; the batched mixed path runs sigma_min in FP64 (the single-vector "
-                "mixed sigma_min uses Dot2 products)",
+                "of one estimate; mixed precision: sigma_max FP32 stage + FP64 tail, sigma_min "
+                "with Dot2 products (k = 1 and k = 32 alike)",
     }
     print(json.dumps(line), flush=True)
     return 0

@@ -202,9 +202,8 @@ pa_status pa_run(pa_handle h, pa_mode mode, int iters, double lr, double beta1, 
  * FP32 stage (FP32 products and Adam state on D_r^-1 A D_c^-1, norms in
  * FP64) for iters[0] - fp64_tail iterations and then the FP64 tail from that
  * state (fp64_tail of the first handle); each item's sigma_max is the larger
- * of the two stages' tracked minimisers scored in FP64.  sigma_min of a
- * batch runs in FP64 (the Dot2 products of the single-vector MIXED sigma_min
- * have no batched form).  Host outputs:
+ * of the two stages' tracked minimisers scored in FP64; sigma_min runs with
+ * Dot2 (compensated) products, as in pa_estimate.  Host outputs:
  *   out[(i * k_restarts + r) * 3 + {0,1,2}] = {sigma_max, sigma_min, kappa}
  *   item_status[i * k_restarts + r]  (may be NULL)
  * mode selects which sigmas run (the others are written as NaN). */

@@ -1377,7 +1377,11 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
   const bool mixed = h0->opt.precision == PA_MIXED && (mode & PA_SIGMA_MAX);
   const int tail = !mixed ? 0 : (h0->opt.fp64_tail < 0 ? iters[0] / 10 : std::min(h0->opt.fp64_tail, iters[0]));
   const int t32 = iters[0] - tail;
-  const int Gmax = mixed ? std::min(batched_max_blocks(K), batched32_max_blocks(K)) : batched_max_blocks(K);
+  // ... and sigma_min with Dot2 products, like the single-vector MIXED run
+  const bool dd_min = h0->opt.precision == PA_MIXED && (mode & PA_SIGMA_MIN);
+  int Gmax = batched_max_blocks(K);
+  if (mixed) Gmax = std::min(Gmax, batched32_max_blocks(K));
+  if (dd_min) Gmax = std::min(Gmax, batched_max_blocks(K, true));
   if (Gmax < m) return fail(PA_ERR_LAUNCH, "batched kernel: %d items exceed %d co-resident CTAs", m, Gmax);
   // ---- CTA groups, sized by padded entries plus a per-row weight
   std::vector<double> work(m);
@@ -1420,6 +1424,7 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
         (st = sc.get(&it.result, (size_t)4 * K, "batch result")) ||
         (st = sc.get(&it.status, 2, "batch status")))  // [1]: the FP32 stage's
       return st;
+    if (dd_min && (st = sc.get(&it.YLO, std::max<size_t>(ny, 1), "batch y (low parts)"))) return st;
     if (mixed) {
       it.a_val32 = hi->a_val32;
       it.t_val32 = hi->t_val32;
@@ -1529,7 +1534,7 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
           if ((err = launch_convert((int64_t)items[i].n_cols * K, items[i].XMINf, items[i].XMIN, s, L)))
             return err;
         if ((err = launch_batch_sigma(items_d, m, K, blk_item_d, blk_row0_d, nb, 256, blockpart,
-                                      item_blk0_d, sig + (size_t)2 * m * K, s, L)))
+                                      item_blk0_d, sig + (size_t)2 * m * K, false, s, L)))
           return err;
         if (tail == 0) continue;
         // the FP64 tail continues from the last FP32 iterate and moments
@@ -1547,9 +1552,11 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
         q.t0 = t32;
         q.iters = tail;
       }
-      if ((err = launch_batched(q, K, G, s, L))) return err;
+      const bool dd = md == PA_SIGMA_MIN && dd_min;
+      if ((err = launch_batched(q, K, G, dd, s, L))) return err;
       if ((err = launch_batch_sigma(items_d, m, K, blk_item_d, blk_row0_d, nb, 256, blockpart,
-                                    item_blk0_d, sig + (md == PA_SIGMA_MAX ? 0 : (size_t)m * K), s, L)))
+                                    item_blk0_d, sig + (md == PA_SIGMA_MAX ? 0 : (size_t)m * K), dd,
+                                    s, L)))
         return err;
     }
     return cudaSuccess;

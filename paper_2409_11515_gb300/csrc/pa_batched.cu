@@ -40,7 +40,9 @@ struct SharedB {
   int iters_run;
 };
 
-template <int K>
+// DD: the products of phase A with Dot2 (TwoProd + TwoSum) kept as y_hi +
+// y_lo, and phase B's A^T (y_hi + y_lo) likewise (the MIXED sigma_min).
+template <int K, bool DD>
 __global__ void __launch_bounds__(kBT, 2) k_batched(const BatchParams bp) {
   __shared__ SharedB<K> sh;
   const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -95,19 +97,28 @@ __global__ void __launch_bounds__(kBT, 2) k_batched(const BatchParams bp) {
         if (s + NW < sa1) prefetch_slice_l2(it.a_wp, it.a_col, it.a_val, s + NW, lane);
         const int w0 = __ldg(it.a_wp + s), w = __ldg(it.a_wp + s + 1) - w0;
         const int64_t base = 32ll * w0 + lane;
-        double acc[K];
+        double acc[K], cmp[K];
 #pragma unroll
-        for (int c = 0; c < K; ++c) acc[c] = 0.0;
+        for (int c = 0; c < K; ++c) acc[c] = cmp[c] = 0.0;
         for (int k = 0; k < w; ++k) {
           const double a = __ldg(it.a_val + base + 32ll * k);
           const double* xr = x + (size_t)__ldg(it.a_col + base + 32ll * k) * K;
 #pragma unroll
-          for (int c = 0; c < K; ++c) acc[c] = fma(a, xr[c], acc[c]);
+          for (int c = 0; c < K; ++c) {
+            if (DD) dot2_step(a, xr[c], acc[c], cmp[c]);
+            else acc[c] = fma(a, xr[c], acc[c]);
+          }
         }
         const int r = 32 * s + lane;
         if (r < it.n_rows) {
 #pragma unroll
           for (int c = 0; c < K; ++c) {
+            if (DD) {
+              double hi, lo;
+              two_sum(acc[c], cmp[c], hi, lo);
+              acc[c] = hi;
+              it.YLO[(size_t)r * K + c] = lo;
+            }
             it.Y[(size_t)r * K + c] = acc[c];
             sv[c] = fma(acc[c], acc[c], sv[c]);
           }
@@ -197,14 +208,26 @@ __global__ void __launch_bounds__(kBT, 2) k_batched(const BatchParams bp) {
         if (s + NW < st1) prefetch_slice_l2(it.t_wp, it.t_col, it.t_val, s + NW, lane);
         const int w0 = __ldg(it.t_wp + s), w = __ldg(it.t_wp + s + 1) - w0;
         const int64_t base = 32ll * w0 + lane;
-        double z[K];
+        double z[K], zc[K];
 #pragma unroll
-        for (int c = 0; c < K; ++c) z[c] = 0.0;
+        for (int c = 0; c < K; ++c) z[c] = zc[c] = 0.0;
         for (int k = 0; k < w; ++k) {
           const double a = __ldg(it.t_val + base + 32ll * k);
-          const double* yr = it.Y + (size_t)__ldg(it.t_col + base + 32ll * k) * K;
+          const size_t i = (size_t)__ldg(it.t_col + base + 32ll * k) * K;
+          const double* yr = it.Y + i;
 #pragma unroll
-          for (int c = 0; c < K; ++c) z[c] = fma(a, yr[c], z[c]);
+          for (int c = 0; c < K; ++c) {
+            if (DD) {
+              dot2_step(a, yr[c], z[c], zc[c]);
+              dot2_step(a, it.YLO[i + c], z[c], zc[c]);
+            } else {
+              z[c] = fma(a, yr[c], z[c]);
+            }
+          }
+        }
+        if (DD) {
+#pragma unroll
+          for (int c = 0; c < K; ++c) z[c] = __dadd_rn(z[c], zc[c]);
         }
         const int j = 32 * s + lane;
         if (j < n) {
@@ -378,7 +401,7 @@ __global__ void __launch_bounds__(kRowsPerBlock) k_bstart_scale(const BatchItem*
 
 // sigma partials: block b covers slices [row0/32, row0/32 + 8) of P A Q^T
 // and x rows [row0, row0 + 256) of item i.
-template <int K>
+template <int K, bool DD>
 __global__ void __launch_bounds__(kRowsPerBlock) k_bsigma_part(const BatchItem* items,
                                                                const int32_t* blk_item,
                                                                const int32_t* blk_row0,
@@ -394,14 +417,25 @@ __global__ void __launch_bounds__(kRowsPerBlock) k_bsigma_part(const BatchItem* 
   if (s < it.n_slices_a) {
     const int w0 = __ldg(it.a_wp + s), w = __ldg(it.a_wp + s + 1) - w0;
     const int64_t base = 32ll * w0 + lane;
-    double acc[K];
+    double acc[K], cmp[K];
 #pragma unroll
-    for (int c = 0; c < K; ++c) acc[c] = 0.0;
+    for (int c = 0; c < K; ++c) acc[c] = cmp[c] = 0.0;
     for (int k = 0; k < w; ++k) {
       const double a = __ldg(it.a_val + base + 32ll * k);
       const double* xr = it.XMIN + (size_t)__ldg(it.a_col + base + 32ll * k) * K;
 #pragma unroll
-      for (int c = 0; c < K; ++c) acc[c] = fma(a, xr[c], acc[c]);
+      for (int c = 0; c < K; ++c) {
+        if (DD) dot2_step(a, xr[c], acc[c], cmp[c]);
+        else acc[c] = fma(a, xr[c], acc[c]);
+      }
+    }
+    if (DD) {  // y rounded from its double-double value
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        double hi, lo;
+        two_sum(acc[c], cmp[c], hi, lo);
+        acc[c] = hi;
+      }
     }
     if (32 * s + lane < it.n_rows)
 #pragma unroll
@@ -459,9 +493,10 @@ cudaError_t batch_start_k(const BatchItem* items, int n_items, int k_used, int k
 template <int K>
 cudaError_t batch_sigma_k(const BatchItem* items, int n_items, const int32_t* blk_item,
                           const int32_t* blk_row0, int nb, double* blockpart,
-                          const int32_t* item_blk0, double* out, cudaStream_t s,
+                          const int32_t* item_blk0, double* out, bool dd, cudaStream_t s,
                           int64_t* launches) {
-  k_bsigma_part<K><<<nb, kRowsPerBlock, 0, s>>>(items, blk_item, blk_row0, blockpart);
+  if (dd) k_bsigma_part<K, true><<<nb, kRowsPerBlock, 0, s>>>(items, blk_item, blk_row0, blockpart);
+  else k_bsigma_part<K, false><<<nb, kRowsPerBlock, 0, s>>>(items, blk_item, blk_row0, blockpart);
   const int warps = n_items * K;
   k_bsigma_final<K><<<(warps * 32 + 255) / 256, 256, 0, s>>>(n_items, item_blk0, blockpart, out);
   *launches += 2;
@@ -487,31 +522,31 @@ cudaError_t launch_batch_start(const BatchItem* items_dev, int n_items, int K, i
 cudaError_t launch_batch_sigma(const BatchItem* items_dev, int n_items, int K,
                                const int32_t* blk_item, const int32_t* blk_row0, int nb,
                                int /*rows_per_block*/, double* blockpart,
-                               const int32_t* item_blk0, double* out, cudaStream_t s,
+                               const int32_t* item_blk0, double* out, bool dd, cudaStream_t s,
                                int64_t* launches) {
   switch (K) {
-    case 1: return batch_sigma_k<1>(items_dev, n_items, blk_item, blk_row0, nb, blockpart, item_blk0, out, s, launches);
-    case 2: return batch_sigma_k<2>(items_dev, n_items, blk_item, blk_row0, nb, blockpart, item_blk0, out, s, launches);
-    case 4: return batch_sigma_k<4>(items_dev, n_items, blk_item, blk_row0, nb, blockpart, item_blk0, out, s, launches);
-    case 8: return batch_sigma_k<8>(items_dev, n_items, blk_item, blk_row0, nb, blockpart, item_blk0, out, s, launches);
+    case 1: return batch_sigma_k<1>(items_dev, n_items, blk_item, blk_row0, nb, blockpart, item_blk0, out, dd, s, launches);
+    case 2: return batch_sigma_k<2>(items_dev, n_items, blk_item, blk_row0, nb, blockpart, item_blk0, out, dd, s, launches);
+    case 4: return batch_sigma_k<4>(items_dev, n_items, blk_item, blk_row0, nb, blockpart, item_blk0, out, dd, s, launches);
+    case 8: return batch_sigma_k<8>(items_dev, n_items, blk_item, blk_row0, nb, blockpart, item_blk0, out, dd, s, launches);
     default: return cudaErrorInvalidValue;
   }
 }
 
-static void* batched_fn(int k) {
+static void* batched_fn(int k, bool dd) {
   switch (k) {
-    case 1: return (void*)k_batched<1>;
-    case 2: return (void*)k_batched<2>;
-    case 4: return (void*)k_batched<4>;
-    case 8: return (void*)k_batched<8>;
+    case 1: return dd ? (void*)k_batched<1, true> : (void*)k_batched<1, false>;
+    case 2: return dd ? (void*)k_batched<2, true> : (void*)k_batched<2, false>;
+    case 4: return dd ? (void*)k_batched<4, true> : (void*)k_batched<4, false>;
+    case 8: return dd ? (void*)k_batched<8, true> : (void*)k_batched<8, false>;
     default: return nullptr;
   }
 }
 
 int batched_threads() { return kBT; }
 
-int batched_max_blocks(int k) {
-  void* fn = batched_fn(k);
+int batched_max_blocks(int k, bool dd) {
+  void* fn = batched_fn(k, dd);
   if (!fn) return -1;
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
@@ -520,8 +555,9 @@ int batched_max_blocks(int k) {
   return per * sms;
 }
 
-cudaError_t launch_batched(const BatchParams& p, int k, int G, cudaStream_t s, int64_t* launches) {
-  void* fn = batched_fn(k);
+cudaError_t launch_batched(const BatchParams& p, int k, int G, bool dd, cudaStream_t s,
+                           int64_t* launches) {
+  void* fn = batched_fn(k, dd);
   if (!fn) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(G);

@@ -119,6 +119,7 @@ struct BatchItem {
   double* partials;                     // [ncta][4][K]
   unsigned* barrier;                    // the group's arrival counter
   double *X0, *X1, *XMIN, *M, *V, *DX, *Y;
+  double* YLO;                          // low parts of Y (Dot2 products only)
   double* result;                       // [K][4]: L_min, t_min, L_last, iterations
   int* status;                          // [1]
   const int32_t* pos_c;                 // source column -> x position (Q)
@@ -143,8 +144,10 @@ struct BatchParams {
 };
 
 int batched_threads();
-int batched_max_blocks(int k);
-cudaError_t launch_batched(const BatchParams& p, int k, int G, cudaStream_t s, int64_t* launches);
+// dd: Dot2 products in both phases (YLO holds the low parts of Y).
+int batched_max_blocks(int k, bool dd = false);
+cudaError_t launch_batched(const BatchParams& p, int k, int G, bool dd, cudaStream_t s,
+                           int64_t* launches);
 // The MIXED sigma_max stage of a batch (log-ratio loss): FP32 products and
 // FP32 Adam state on A_hat, per-column norms reduced in FP64, the same CTA
 // groups, partitions and result layout as k_batched.  Reads X0f (x_init);
@@ -165,7 +168,7 @@ cudaError_t launch_batch_start(const BatchItem* items_dev, int n_items, int K, i
 cudaError_t launch_batch_sigma(const BatchItem* items_dev, int n_items, int K,
                                const int32_t* blk_item, const int32_t* blk_row0, int nb,
                                int rows_per_block, double* blockpart, const int32_t* item_blk0,
-                               double* out, cudaStream_t s, int64_t* launches);
+                               double* out, bool dd, cudaStream_t s, int64_t* launches);
 
 // Record a message for pa_last_error() (printf-style) and return st.
 pa_status set_error(pa_status st, const char* fmt, ...);

@@ -156,3 +156,24 @@ def test_batched_mixed_fp32_stage_only_and_kappa():
     kappas = [1 / math.tan(math.pi / 18) ** 2, 1 / math.tan(math.pi / 10) ** 2]
     for i, kap in enumerate(kappas):
         assert np.all(np.abs(r["kappa"][i] / kap - 1) <= 1e-6), (i, r["kappa"][i], kap)
+
+
+def test_batched_mixed_sigma_min_dot2_matches_oracle():
+    # a MIXED batch runs sigma_min with Dot2 products (the oracle's FLAG_DD
+    # reading of them); on matrices where sigma_min converges the batched
+    # items reach the oracle's value from the same start vectors
+    mats = [synth.laplacian_1d(12), synth.laplacian_2d(6)]
+    hs = [pa.create(A, precision=pa.MIXED) for A in mats]
+    try:
+        T = 3000
+        r = pa.estimate_batched(hs, pa.SIGMA_MIN, 2, (T, T), seed=7, **HYPER)
+    finally:
+        for h in hs:
+            h.destroy()
+    assert np.all(r["item_status"] == 0)
+    assert np.all(np.isnan(r["sigma_max"]))
+    for i, A in enumerate(mats):
+        for rr in range(2):
+            ro = oracle.projected_adam(A, oracle.SIGMA_MIN, T, x_init=_x0(A.n_cols, 7, i, 2, rr),
+                                       flags=oracle.FLAG_DD, **HYPER)
+            assert abs(r["sigma_min"][i, rr] / ro.sigma - 1) <= 1e-6, (i, rr, r["sigma_min"][i, rr], ro.sigma)
