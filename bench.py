@@ -377,8 +377,9 @@ def run_ours(args):
 
 def run_batched_workload(args):
     """64 hydro operators with sides drawn from 51..301 (seed 3), 8 restarts
-    each, FP64: vector-iterations per second of pa_estimate_batched (one
-    persistent launch per sigma mode, one CUDA graph) against the
+    each, FP64 (or --precision mixed: FP32 sigma_max stage + FP64 tail, Dot2
+    sigma_min): vector-iterations per second of pa_estimate_batched (one
+    persistent launch sequence per sigma mode, one CUDA graph) against the
     single-vector path looping over the same (matrix, restart) items."""
     if _dist()[0] > 1:
         raise SystemExit("the batched workload runs on one GPU (launch it without torchrun)")
@@ -390,8 +391,11 @@ def run_batched_workload(args):
     n_mat, k = 64, 8
     mats = synth.hydro_batch(n_mat, 51, 301, seed=3)
     stream = torch.cuda.Stream()
+    mixed = args.precision == "mixed"
+    prec = pa.MIXED if mixed else pa.FP64
     # the first handle's autotune picks the restart-block width on a short trial
-    hs = [pa.create(A, stream=stream, autotune=1 if i == 0 else 0) for i, A in enumerate(mats)]
+    hs = [pa.create(A, stream=stream, precision=prec, autotune=1 if i == 0 else 0)
+          for i, A in enumerate(mats)]
     rows = sum(A.n_rows for A in mats)
     nnz = sum(A.nnz for A in mats)
     it = (args.iters_max, args.iters_min)
@@ -422,11 +426,11 @@ def run_batched_workload(args):
         h.destroy()
     full_T = EST_ITERS[0] + EST_ITERS[1]
     line = {
-        "metric": "kappa2_estimates_per_s (batched, FP64)",
+        "metric": "kappa2_estimates_per_s (batched, %s)" % ("mixed precision" if mixed else "FP64"),
         "value": n_mat * k / (tb * full_T / (it[0] + it[1])),
         "unit": "estimates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": tb * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic (seeded hydro-mechanical operators)",
+        "dtype": "f32+f64" if mixed else "f64", "data": "synthetic (seeded hydro-mechanical operators)",
         "config": {"workload": "64 hydro operators, sides U[51,301] (seed 3), 8 restarts each, "
                                "one persistent SpMM launch per sigma mode in a CUDA graph",
                    "rows_total": rows, "nnz_total": nnz, "k": k,
@@ -740,6 +744,8 @@ def main():
                          "engine, LU route); batched: 64 operators x 8 restarts; "
                          "mixed1001: 1001x1001 mixed vs FP64; stress2001: 2001x1001, 32 restarts; "
                          "lu64: 64 small operators, kappa through the LU route")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+                    help="batched workload: the handles' precision mode")
     ap.add_argument("--iters-max", type=int, default=None,
                     help="sigma_max iterations per estimate (short runs for profiling); "
                          "default 5000, stress2001 200 (timed, then extrapolated)")
