@@ -208,6 +208,9 @@ __global__ void __launch_bounds__(kBT, 2) k_batched(const BatchParams bp) {
         if (s + NW < st1) prefetch_slice_l2(it.t_wp, it.t_col, it.t_val, s + NW, lane);
         const int w0 = __ldg(it.t_wp + s), w = __ldg(it.t_wp + s + 1) - w0;
         const int64_t base = 32ll * w0 + lane;
+        // DD: Dot2 over the a y_hi terms; the a y_lo terms, O(u) of them, are
+        // added by FMA to the compensation sum (O(u^2) relative error), as in
+        // slice_dot_dd2
         double z[K], zc[K];
 #pragma unroll
         for (int c = 0; c < K; ++c) z[c] = zc[c] = 0.0;
@@ -219,7 +222,7 @@ __global__ void __launch_bounds__(kBT, 2) k_batched(const BatchParams bp) {
           for (int c = 0; c < K; ++c) {
             if (DD) {
               dot2_step(a, yr[c], z[c], zc[c]);
-              dot2_step(a, it.YLO[i + c], z[c], zc[c]);
+              zc[c] = fma(a, it.YLO[i + c], zc[c]);
             } else {
               z[c] = fma(a, yr[c], z[c]);
             }

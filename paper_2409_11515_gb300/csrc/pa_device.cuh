@@ -228,6 +228,9 @@ __device__ __forceinline__ double slice_dot_dd2(const int32_t* __restrict__ wp,
                                                 const int32_t* __restrict__ col,
                                                 const double* __restrict__ val, int s,
                                                 int lane, const double* xh, const double* xl) {
+  // sum a (xh + xl): Dot2 over the a xh terms; the a xl terms are O(u) of
+  // them, so adding them by FMA to the compensation sum costs only O(u^2)
+  // relative error
   const int w0 = __ldg(wp + s), w = __ldg(wp + s + 1) - w0;
   const int64_t base = 32ll * w0 + lane;
   double sum = 0.0, c = 0.0;
@@ -238,16 +241,16 @@ __device__ __forceinline__ double slice_dot_dd2(const int32_t* __restrict__ wp,
     const double a0 = __ldg(val + e), a1 = __ldg(val + e + 32);
     const double h0 = xh[j0], l0 = xl[j0], h1 = xh[j1], l1 = xl[j1];
     dot2_step(a0, h0, sum, c);
-    dot2_step(a0, l0, sum, c);
+    c = fma(a0, l0, c);
     dot2_step(a1, h1, sum, c);
-    dot2_step(a1, l1, sum, c);
+    c = fma(a1, l1, c);
   }
   for (; k < w; ++k) {
     const int64_t e = base + 32ll * k;
     const double a = __ldg(val + e);
     const int32_t j = __ldg(col + e);
     dot2_step(a, xh[j], sum, c);
-    dot2_step(a, xl[j], sum, c);
+    c = fma(a, xl[j], c);
   }
   return __dadd_rn(sum, c);
 }
