@@ -158,7 +158,7 @@ def profiled_traffic_per_iteration():
     src = dram = None
     for line in prof.read_text().splitlines():
         if line.startswith("kernel source sha256[:16]:"):
-            src = line.split(":", 1)[1].strip()
+            src = line.rsplit(":", 1)[1].strip()
         if line.startswith("dram bytes per iteration:"):
             dram = float(line.split(":", 1)[1].strip())
     return dram if (src == kernel_source_hash() and dram) else None
