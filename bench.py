@@ -701,7 +701,7 @@ def run_lu64(args):
     line = {
         "metric": "kappa2_estimates_per_s (LU route, batched)", "value": n_mat * k / tb,
         "unit": "estimates/s", "n_gpus": 1, "steps": 1, "warmup": args.warmup,
-        "ms_per_step": 1e3 * tbm, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * tb, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded hydro-mechanical operators)",
         "config": {"workload": "64 hydro operators, sides U[7,31] (seed 6), 8 restarts each; "
                                "sigma_max 2000 iterations (SpMM), sigma_min 500 iterations on "
