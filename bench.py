@@ -748,11 +748,11 @@ def main():
                     help="batched workload: the handles' precision mode")
     ap.add_argument("--iters-max", type=int, default=None,
                     help="sigma_max iterations per estimate (short runs for profiling); "
-                         "default 5000, stress2001 200 (timed, then extrapolated)")
+                         "default 5000, stress2001 200, batched 500 (timed, then extrapolated)")
     ap.add_argument("--iters-min", type=int, default=None,
-                    help="sigma_min iterations; default 20000, stress2001 200")
+                    help="sigma_min iterations; default 20000, stress2001 200, batched 500")
     args = ap.parse_args()
-    short = (200, 200) if args.workload == "stress2001" else EST_ITERS
+    short = {"stress2001": (200, 200), "batched": (500, 500)}.get(args.workload, EST_ITERS)
     if args.iters_max is None:
         args.iters_max = short[0]
     if args.iters_min is None:
