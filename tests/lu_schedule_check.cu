@@ -1,0 +1,164 @@
+// Host-side check of the LU route's step schedule (tri_analyse): for random
+// triangular factors it walks the steps the way the kernel does (items of a
+// step in any order, a group of 2^lg lanes per item with a butterfly sum) on
+// the CPU and compares the result with plain substitution.  It also checks
+// that every 16-byte staging window stays inside the padded arrays, that a
+// step reads only rows finished in earlier steps and writes each row once,
+// and that malformed factors are rejected.  Prints "ALL OK" on success.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include "pa_internal.h"
+
+using namespace pa;
+
+static int g_fail = 0;
+#define CHECK(c, ...)              \
+  do {                             \
+    if (!(c)) {                    \
+      std::printf(__VA_ARGS__);    \
+      std::printf("\n");           \
+      g_fail = 1;                  \
+      return;                      \
+    }                              \
+  } while (0)
+
+struct Csr {
+  int n = 0;
+  std::vector<int> rp, ci;
+  std::vector<double> va;
+};
+
+static Csr random_triangle(std::mt19937& g, int n, double dens, bool lower) {
+  Csr T;
+  T.n = n;
+  T.rp.push_back(0);
+  std::uniform_real_distribution<double> u(0.0, 1.0), off(-0.4, 0.4);
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) {
+      const bool side = lower ? j < i : j > i;
+      if (j == i) {
+        T.ci.push_back(j);
+        T.va.push_back((u(g) < 0.5 ? -1.0 : 1.0) * (1.5 + 3.0 * u(g)));
+      } else if (side && u(g) < dens) {
+        T.ci.push_back(j);
+        T.va.push_back(off(g));
+      }
+    }
+    T.rp.push_back((int)T.ci.size());
+  }
+  return T;
+}
+
+static void check_one(const Csr& T, bool lower) {
+  const int n = T.n;
+  TriHost h;
+  const std::string why = tri_analyse(n, T.rp.data(), T.ci.data(), T.va.data(), lower, &h);
+  CHECK(why.empty(), "analyse refused a valid factor: %s", why.c_str());
+  // plain substitution
+  std::mt19937 g(3);
+  std::uniform_real_distribution<double> u(-1.0, 1.0);
+  std::vector<double> b(n), ref(n), x(n);
+  for (double& v : b) v = u(g);
+  for (int s = 0; s < n; ++s) {
+    const int i = lower ? s : n - 1 - s;
+    double acc = b[i], d = 0.0;
+    for (int k = T.rp[i]; k < T.rp[i + 1]; ++k) {
+      if (T.ci[k] == i) d = T.va[k];
+      else acc -= T.va[k] * ref[T.ci[k]];
+    }
+    ref[i] = acc / d;
+  }
+  // the schedule, as the kernel applies it
+  for (int i = 0; i < n; ++i) x[i] = b[i] * h.dinv[i];
+  std::vector<int> done(n, -1);  // step in which row i received its last segment
+  std::vector<int> touched(n, -1);
+  const int E = (int)h.ci.size();
+  for (int l = 0; l < h.nproc; ++l) {
+    const int4 I = h.linfo[l];
+    const int i0 = I.x, i1 = I.y & kItemMask, lg = I.y >> 27;
+    CHECK(lg >= 0 && lg <= 5 && i0 <= i1 && i1 <= (int)h.items.size(), "bad step record %d", l);
+    CHECK(I.z <= I.w && I.w <= E, "bad entry range at step %d", l);
+    const int va0 = I.z & ~1, vb = (I.w + 1) & ~1, ca0 = I.z & ~3, cb = (I.w + 3) & ~3;
+    CHECK(vb <= (int)h.va.size() && cb <= (int)h.ci.size(), "window past the padded arrays at %d", l);
+    CHECK(i1 - i0 <= h.max_items && vb - va0 <= h.max_ent && cb - ca0 <= h.max_ent,
+          "step %d exceeds the recorded maxima", l);
+    const int G = 1 << lg;
+    for (int k = i0; k < i1; ++k) {
+      const int4 r = h.items[k];
+      std::vector<double> lane(G, 0.0);
+      int row;
+      if (r.x >= 0) {  // one entry: {row, column, value}
+        row = r.x;
+        CHECK(r.y >= 0 && r.y < n && done[r.y] < l, "step %d reads unfinished x[%d]", l, r.y);
+        double v;
+        const int w[2] = {r.z, r.w};
+        std::memcpy(&v, w, sizeof v);
+        lane[0] = std::fma(v, x[r.y], x[row]);
+      } else {  // {~row, first entry, end entry}
+        row = ~r.x;
+        CHECK(r.y >= I.z && r.z <= I.w && r.z - r.y >= 2, "bad segment at step %d", l);
+        lane[0] = x[row];
+        for (int gl = 0; gl < G; ++gl)
+          for (int e = r.y + gl; e < r.z; e += G) {
+            const int c = h.ci[e];
+            CHECK(c >= 0 && c < n && done[c] < l, "step %d reads unfinished x[%d]", l, c);
+            lane[gl] = std::fma(h.va[e], x[c], lane[gl]);
+          }
+      }
+      CHECK(row >= 0 && row < n, "row out of range at step %d", l);
+      CHECK(touched[row] != l, "row %d written twice in step %d", row, l);
+      touched[row] = l;
+      for (int d = G >> 1; d > 0; d >>= 1) {
+        std::vector<double> nx(G);
+        for (int q = 0; q < G; ++q) nx[q] = lane[q] + lane[q ^ d];
+        lane = nx;
+      }
+      x[row] = lane[0];
+    }
+    for (int i = 0; i < n; ++i)
+      if (touched[i] == l) done[i] = l;
+  }
+  double err = 0.0, nrm = 0.0;
+  for (int i = 0; i < n; ++i) {
+    err = std::fmax(err, std::fabs(x[i] - ref[i]));
+    nrm = std::fmax(nrm, std::fabs(ref[i]));
+  }
+  CHECK(err <= 1e-12 * (nrm > 0 ? nrm : 1.0), "n=%d lower=%d: |x - ref| = %.3e of %.3e", n, lower,
+        err, nrm);
+}
+
+static void check_rejections() {
+  const int rp[3] = {0, 1, 3};
+  const int ci_zero[3] = {0, 0, 1};
+  const double va_zero[3] = {2.0, 1.0, 0.0};  // zero diagonal in row 1
+  TriHost h;
+  CHECK(!tri_analyse(2, rp, ci_zero, va_zero, true, &h).empty(), "zero diagonal accepted");
+  const int ci_up[3] = {0, 1, 1};  // row 1 holds (1, 1) twice
+  const double va_up[3] = {2.0, 1.0, 3.0};
+  CHECK(!tri_analyse(2, rp, ci_up, va_up, true, &h).empty(), "two diagonals accepted");
+  const int rp2[3] = {0, 2, 3};
+  const int ci_side[3] = {0, 1, 1};  // (0, 1) above the diagonal of a lower factor
+  const double va_side[3] = {2.0, 1.0, 3.0};
+  CHECK(!tri_analyse(2, rp2, ci_side, va_side, true, &h).empty(), "entry above the diagonal accepted");
+  CHECK(tri_analyse(2, rp2, ci_side, va_side, false, &h).empty(), "valid upper factor refused");
+}
+
+int main() {
+  std::mt19937 g(11);
+  const int sizes[] = {1, 2, 5, 33, 64, 150, 300};
+  const double dens[] = {0.0, 0.02, 0.1, 0.4, 1.0};
+  for (int n : sizes)
+    for (double d : dens)
+      for (int lower = 0; lower < 2; ++lower) {
+        check_one(random_triangle(g, n, d, lower != 0), lower != 0);
+        if (g_fail) return 1;
+      }
+  check_rejections();
+  if (g_fail) return 1;
+  std::printf("ALL OK\n");
+  return 0;
+}
