@@ -1715,6 +1715,13 @@ static pa_status batched_lu(const pa_handle* hs, int n_mat, int k_restarts, int 
     }
   }
   std::vector<RunState> rs((size_t)n_items);
+  // CTAs start in index order: the items with the most solve steps go first,
+  // so the last wave holds short items (each item keeps its own run state)
+  std::stable_sort(items.begin(), items.end(), [](const LuParams& a, const LuParams& b) {
+    const int64_t sa = (int64_t)a.L.nproc + a.U.nproc + a.Ut.nproc + a.Lt.nproc;
+    const int64_t sb = (int64_t)b.L.nproc + b.U.nproc + b.Ut.nproc + b.Lt.nproc;
+    return sa > sb;
+  });
   if ((e = cudaMemcpyAsync(items_dev, items.data(), sizeof(LuParams) * n_items, cudaMemcpyHostToDevice, s)) ||
       (e = launch_lu_iter(items_dev, n_items, smem, all_smem, s, &h0->launches)) ||
       (e = cudaMemcpyAsync(rs.data(), states, sizeof(RunState) * n_items, cudaMemcpyDeviceToHost, s)) ||
