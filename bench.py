@@ -227,6 +227,29 @@ def cpu_baseline(A, x0):
                       "(serial C oracle, one host core)"}
 
 
+def oracle_iteration_rate(A, iters, x0):
+    """Iterations per second of the serial CPU oracle on A: `iters` sigma_max
+    and `iters` sigma_min iterations from x0 (one host core)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.projected_adam(A, oracle.SIGMA_MAX, iters, x_init=x0, **HYPER)
+    oracle.projected_adam(A, oracle.SIGMA_MIN, iters, x_init=x0, **HYPER)
+    return 2 * iters / (time.perf_counter() - t0)
+
+
+def oracle_estimate_baseline(A, iters):
+    """cpu_baseline in kappa_2 estimates/s for one large operator: the oracle's
+    iteration rate on a short run, extrapolated to one estimate."""
+    import oracle
+    rate = oracle_iteration_rate(A, iters, oracle.start_vector(A.n_cols, START_SEED))
+    full_T = EST_ITERS[0] + EST_ITERS[1]
+    return {"value": rate / full_T, "unit": "estimates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{iters} sigma_max + {iters} sigma_min iterations of the same operator "
+                      f"(serial C oracle, one host core, {rate:.3g} iterations/s), "
+                      f"extrapolated to {EST_ITERS[0]} + {EST_ITERS[1]}"}
+
+
 def run_ours(args):
     ws, rank, local = _dist()
     import torch
@@ -441,6 +464,19 @@ def run_batched_workload(args):
                                "sample": f"every 8th matrix, all 8 restarts ({frac:.2%} of rows)"},
         "note": "value extrapolates the timed iterations to the 5000 + 20000 of one estimate",
     }
+    if not args.no_cpu_baseline:
+        import oracle
+        cs = list(range(0, n_mat, 16))
+        t_cpu = sum(2 * 50 / oracle_iteration_rate(mats[i], 50, oracle.start_vector(mats[i].n_cols, 1))
+                    for i in cs)
+        # seconds per row-iteration, then one estimate of the batch's average operator
+        per_row_it = t_cpu / sum(mats[i].n_rows * 100 for i in cs)
+        t_est = per_row_it * (rows / n_mat) * full_T
+        line["cpu_baseline"] = {"value": 1.0 / t_est, "unit": "estimates/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": "every 16th operator, one restart, 50 + 50 iterations "
+                                          "(serial C oracle, one host core), row-weighted and "
+                                          "extrapolated to one estimate of the average operator"}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -503,6 +539,8 @@ def run_mixed1001(args):
         "note": "the comparator is this build's FP64 path (parity-tested against the CPU "
                 "oracle); a full-length oracle run at this size takes hours on one core",
     }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_estimate_baseline(A, 10)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -570,6 +608,8 @@ def run_stress2001(args):
                 "of one estimate; mixed precision: sigma_max FP32 stage + FP64 tail, sigma_min "
                 "with Dot2 products (k = 1 and k = 32 alike)",
     }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_estimate_baseline(A, 10)
     print(json.dumps(line), flush=True)
     return 0
 
