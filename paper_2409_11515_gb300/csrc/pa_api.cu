@@ -1422,7 +1422,7 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
         (st = sc.get(&it.V, nx, "batch v")) || (st = sc.get(&it.DX, nx, "batch dx")) ||
         (st = sc.get(&it.Y, std::max<size_t>(ny, 1), "batch y")) ||
         (st = sc.get(&it.result, (size_t)4 * K, "batch result")) ||
-        (st = sc.get(&it.status, 2, "batch status")))  // [1]: the FP32 stage's
+        (st = sc.get(&it.status, 3, "batch status")))  // [1] the FP32 stage's, [2] sigma_max's
       return st;
     if (dd_min && (st = sc.get(&it.YLO, std::max<size_t>(ny, 1), "batch y (low parts)"))) return st;
     if (mixed) {
@@ -1558,6 +1558,11 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
                                     item_blk0_d, sig + (md == PA_SIGMA_MAX ? 0 : (size_t)m * K), dd,
                                     s, L)))
         return err;
+      if (md == PA_SIGMA_MAX && (mode & PA_SIGMA_MIN))  // keep sigma_max's status
+        for (int i = 0; i < m; ++i)
+          if ((err = cudaMemcpyAsync(items[i].status + 2, items[i].status, sizeof(int),
+                                     cudaMemcpyDeviceToDevice, s)))
+            return err;
     }
     return cudaSuccess;
   };
@@ -1613,11 +1618,19 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
     return cuda_fail(e, "reading the batched results");
   std::vector<int> ist(m, PA_OK);
   for (int i = 0; i < m; ++i) {
-    int v[2] = {0, 0};
+    int v[3] = {0, 0, 0};
     if ((e = cudaMemcpy(v, items[i].status, sizeof(v), cudaMemcpyDeviceToHost)))
       return cuda_fail(e, "reading the batched status");
-    // an FP32-stage error outranks the tail's status (errors < 0 < warnings)
-    ist[i] = (mixed && tail > 0 && v[1] < 0) ? v[1] : v[0];
+    // the item's status over every launch that ran for it: the first error
+    // (< 0), else a warning (> 0), else PA_OK
+    int worst = v[0];
+    const bool have[3] = {true, mixed && tail > 0, mode == PA_BOTH};
+    for (int j = 1; j < 3; ++j) {
+      if (!have[j]) continue;
+      if (v[j] < 0 && worst >= 0) worst = v[j];
+      else if (v[j] > 0 && worst == 0) worst = v[j];
+    }
+    ist[i] = worst;
   }
   if (rs.abort) return fail(PA_ERR_TIMEOUT, "a batched group barrier wait ran out of time");
   for (int i = 0; i < m; ++i) {
