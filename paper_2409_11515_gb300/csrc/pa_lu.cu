@@ -12,8 +12,8 @@
 //
 // The triangular solves are level-scheduled.  Sparse LU factors of 2D
 // operators in fill-reducing orders have long, thin level sets: hundreds of
-// levels of a few rows, most of them rows of the dense triangles that nested
-// dissection leaves at the separators, each depending on the previous row.
+// levels of a few rows, most of them rows of the dense triangles that such
+// orders leave at the separators, each depending on the previous row.
 // A row-per-warp solve pays a dot product, a butterfly sum and a division per
 // level; on GB300, where every dependent FP64 instruction costs tens of
 // cycles, that chain is the whole cost.  Here each row's entries are split
