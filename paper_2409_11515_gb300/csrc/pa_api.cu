@@ -1524,6 +1524,7 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
         for (int i = 0; i < m; ++i) {
           const size_t nx = (size_t)items[i].n_cols * K;
           if ((err = launch_convert((int64_t)nx, items[i].X0, items[i].X0f, s, L)) ||
+              (err = launch_convert((int64_t)nx, items[i].X0, items[i].XMINf, s, L)) ||  // x_min = x_init
               (err = cudaMemsetAsync(items[i].Mf, 0, sizeof(float) * nx, s)) ||
               (err = cudaMemsetAsync(items[i].Vf, 0, sizeof(float) * nx, s)))
             return err;

@@ -177,3 +177,25 @@ def test_batched_mixed_sigma_min_dot2_matches_oracle():
             ro = oracle.projected_adam(A, oracle.SIGMA_MIN, T, x_init=_x0(A.n_cols, 7, i, 2, rr),
                                        flags=oracle.FLAG_DD, **HYPER)
             assert abs(r["sigma_min"][i, rr] / ro.sigma - 1) <= 1e-6, (i, rr, r["sigma_min"][i, rr], ro.sigma)
+
+
+def test_batched_mixed_with_no_fp32_iterations():
+    # fp64_tail = iters: the FP32 stage runs no iteration, so its tracked
+    # minimiser must be x_init and the FP64 tail decides; iters = 0 scores
+    # x_init itself (through its FP32 copy: 1e-6)
+    mats = [synth.laplacian_2d(7), synth.hydro_operator(9, seed=1)]
+    T = 1500
+    hs = [pa.create(A, precision=pa.MIXED, fp64_tail=T) for A in mats]
+    try:
+        r = pa.estimate_batched(hs, pa.SIGMA_MAX, 2, (T, T), seed=5, **HYPER)
+        r0 = pa.estimate_batched(hs, pa.SIGMA_MAX, 2, (0, 0), seed=5, **HYPER)
+    finally:
+        for h in hs:
+            h.destroy()
+    assert np.all(r["item_status"] == 0) and np.all(r0["item_status"] == 0)
+    for i, A in enumerate(mats):
+        for rr in range(2):
+            x0 = _x0(A.n_cols, 5, i, 2, rr)
+            ro = oracle.projected_adam(A, oracle.SIGMA_MAX, T, x_init=x0, **HYPER)
+            assert abs(r["sigma_max"][i, rr] / ro.sigma - 1) <= 1e-6, (i, rr)
+            assert abs(r0["sigma_max"][i, rr] / oracle.sigma(A, x0) - 1) <= 1e-6, (i, rr)
