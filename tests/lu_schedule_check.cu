@@ -4,7 +4,8 @@
 // the CPU and compares the result with plain substitution.  It also checks
 // that every 16-byte staging window stays inside the padded arrays, that a
 // step reads only rows finished in earlier steps and writes each row once,
-// and that malformed factors are rejected.  Prints "ALL OK" on success.
+// that malformed factors are rejected, and that the shared-memory layout of
+// lu_layout stays within its budget.  Prints "ALL OK" on success.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -147,6 +148,36 @@ static void check_rejections() {
   CHECK(tri_analyse(2, rp2, ci_side, va_side, false, &h).empty(), "valid upper factor refused");
 }
 
+// lu_layout: the dynamic shared memory it asks for stays within the budget,
+// the slots keep 16-byte alignment, and the solve vector goes to shared
+// memory exactly when it fits beside a minimal ring.
+static void check_layout() {
+  const int ns[] = {1, 7, 294, 2646, 10086, 26000, 40000};
+  const int wins[] = {1, 64, 500, 3000, 20000};
+  for (int n : ns)
+    for (int wi : wins) {
+      LuParams p{};
+      p.n = n;
+      TriSys t{};
+      t.max_items = wi;
+      t.max_ent = wi + 3;
+      p.L = p.U = p.Ut = p.Lt = t;
+      const size_t smem = lu_layout(&p);
+      CHECK(smem <= kLuSmemBudget, "n=%d win=%d: %zu bytes over the budget", n, wi, smem);
+      CHECK(p.slot_items > 0 && p.slot_ent > 0 && p.slot_ent % 4 == 0, "n=%d win=%d: bad slot caps", n, wi);
+      const size_t slot = 32 + 16 * (size_t)p.slot_items + 12 * (size_t)p.slot_ent;
+      CHECK(slot % 16 == 0, "n=%d: slot of %zu bytes breaks 16-byte alignment", n, slot);
+      const size_t vec = sizeof(double) * ((size_t)n + (n & 1));
+      CHECK((p.smem_mode == 1) == (smem > vec && vec + 7 * (32 + 20 * 64) <= kLuSmemBudget),
+            "n=%d win=%d: solve-vector placement", n, wi);
+      CHECK(smem == (p.smem_mode == 1 ? vec : 0) + 7 * slot, "n=%d win=%d: size mismatch", n, wi);
+      if (p.slot_items >= wi && p.slot_ent >= ((wi + 3 + 3) & ~3)) continue;
+      // capped: the ring then uses (nearly) all of what is left
+      const size_t left = kLuSmemBudget - (p.smem_mode == 1 ? vec : 0);
+      CHECK(7 * slot + 7 * (16 + 12 * 4 + 16) >= left / 2, "n=%d win=%d: ring needlessly small", n, wi);
+    }
+}
+
 int main() {
   std::mt19937 g(11);
   const int sizes[] = {1, 2, 5, 33, 64, 150, 300};
@@ -158,6 +189,8 @@ int main() {
         if (g_fail) return 1;
       }
   check_rejections();
+  if (g_fail) return 1;
+  check_layout();
   if (g_fail) return 1;
   std::printf("ALL OK\n");
   return 0;
