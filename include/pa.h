@@ -62,9 +62,9 @@ typedef enum {
 
 enum { PA_HOST = 0, PA_DEVICE = 1 };                   /* pointer kinds        */
 enum { PA_LOSS_LOGRATIO = 0, PA_LOSS_QUADRATIC = 1 };  /* loss forms           */
-enum { PA_FP64 = 0, PA_MIXED = 1 };                    /* precision modes      */
+enum { PA_FP64 = 0, PA_MIXED = 1, PA_DF64 = 2 };       /* precision modes      */
 enum { PA_EQ_NONE = 0, PA_EQ_STORAGE = 1, PA_EQ_TARGET = 2 }; /* equilibration */
-enum { PA_ENGINE_AUTO = 0, PA_ENGINE_GRID = 1, PA_ENGINE_CLUSTER = 2 };
+enum { PA_ENGINE_AUTO = 0, PA_ENGINE_GRID = 1, PA_ENGINE_CLUSTER = 2, PA_ENGINE_MERGED = 3 };
 enum { PA_ABLATE_NO_TANGENT = 1, PA_ABLATE_NO_NORMALISE = 2 };
 
 typedef struct {
@@ -80,7 +80,14 @@ typedef struct {
    * iterations in FP64 from that state; x_min is whichever tracked iterate
    * of the two stages scores the larger ||A x|| / ||x|| in FP64.  sigma_min
    * uses compensated (double-double, Dot2) products for A x and A^T y and
-   * for its final sigma. */
+   * for its final sigma.  DF64 (log-ratio loss only): the input stays FP64
+   * and sigma is recomputed from it in FP64, but the iteration stores its
+   * matrix values (as 2^-k A, k from the largest |a_ij|, exact) and vectors
+   * as double-float pairs (hi + lo, two floats, about 48 significant bits,
+   * the same 8 bytes per value) and runs its products and its per-row Adam
+   * arithmetic in double-float on the FP32 pipe, with the reductions in
+   * FP64.  A matrix whose non-zeros span more than 2^99, or a run whose
+   * ||2^-k A x||^2 leaves [2^-100, 2^100], runs the FP64 kernel instead. */
   int precision;
   /* Equilibration with the paper's row and column 2-norm scaling (rows
    * first, then the columns of D_r^-1 A), each factor rounded to the nearest
@@ -90,7 +97,13 @@ typedef struct {
    * sigmas, kappa, products and the transpose all refer to A_hat (the
    * paper's kappa of the scaled system). */
   int equilibrate;
-  int engine;       /* GRID: cooperative grid with timed software barriers;
+  int engine;       /* GRID: cooperative grid with timed software barriers
+                       and three phases per iteration (product, transposed
+                       product with Adam, update of x; two full barriers);
+                       MERGED: the same grid with the update of x folded
+                       into the next product (one full grid barrier per
+                       iteration) -- what PA_DF64 always runs, opt-in for
+                       FP64;
                        CLUSTER: one thread-block cluster (<= 16 CTAs) with
                        the hardware cluster barrier (plain FP64 only);
                        AUTO: CLUSTER when the grid would use <= 16 CTAs    */
@@ -271,6 +284,19 @@ pa_status pa_get_equilibration(pa_handle h, double* d_row, double* d_col);
  * nanoseconds of the GPU's global timer.  Host outputs. */
 pa_status pa_last_run_profile(pa_handle h, int* grid, double* busy_ns);
 
+/* Facts about the handle's latest single-vector run (pa_estimate, pa_run),
+ * into out[4] (host):
+ *   out[0] kernel: 0 the three-phase grid kernel, 1 the merged-phase grid
+ *          kernel in FP64, 2 the merged-phase grid kernel in double-float
+ *          (PA_DF64), 3 the cluster kernel; -1 before any run;
+ *   out[1] iterations of the merged-phase kernel that multiplied x itself
+ *          instead of folding the update of x into the product (see the
+ *          engine option);
+ *   out[2] PA_DF64 runs that left the double-float range and were redone in
+ *          FP64, since the handle was created;
+ *   out[3] CTAs of the run's grid. */
+pa_status pa_last_run_info(pa_handle h, int64_t* out);
+
 /* Launches of this library's kernels since the handle was created (a
  * counter kept by the host code at every launch). */
 int64_t pa_kernel_launches(pa_handle h);
@@ -282,7 +308,9 @@ int64_t pa_kernel_launches(pa_handle h);
  * because cudaMalloc's implicit device-wide synchronisation is not
  * acceptable there.)
  *   row_ptr (n_rows+1 int32), col_idx and vals (nnz int32 / float64), x
- *   (n_cols float64): device pointers, read only; the CSR is not validated.
+ *   (n_cols float64): device pointers, read only, none of them NULL (for a
+ *   matrix without entries pass any valid device address as col_idx and
+ *   vals); the CSR is not validated.
  *   sigma: device pointer to one float64, written by the call's kernels.
  *   cuda_stream: cudaStream_t (NULL = legacy default stream); the call only
  *   enqueues work and returns without synchronising.
@@ -290,7 +318,9 @@ int64_t pa_kernel_launches(pa_handle h);
  * on every GPU that loads it until the process exits) limits
  * max(n_rows, n_cols) to 2,097,152; larger sizes give PA_ERR_INVALID_ARG.
  * The first call on a device looks up that array's address (once per
- * device); make that first call before any stream capture.  All calls share
+ * device) and keeps it for the process: calls must run in the device's
+ * primary context (the CUDA runtime's), and a cudaDeviceReset between calls
+ * is not supported.  Make that first call before any stream capture.  All calls share
  * the array: calls whose kernels may overlap on the GPU race and must be
  * ordered by the caller (same stream or events).  Errors: PA_ERR_INVALID_ARG,
  * PA_ERR_CUDA, PA_ERR_UNSUPPORTED (device index 64 or above). */

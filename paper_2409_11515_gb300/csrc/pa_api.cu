@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <climits>
 #include <string>
 #include <chrono>
 #include <map>
@@ -131,6 +132,18 @@ struct pa_ctx {
   float *X0f = nullptr, *X1f = nullptr, *X2f = nullptr, *Wf = nullptr;
   float *mf = nullptr, *vf = nullptr, *yf = nullptr, *dxf = nullptr;
   int64_t a_entries = 0, t_entries = 0;  // padded entries of the sliced copies
+
+  // PA_DF64: values of 2^-df_k P A Q^T and its transpose as (hi, lo) float
+  // pairs, the vectors in the same form, and the bias table as pairs
+  bool df_ok = false;     // the matrix's exponent range fits the variant
+  int df_k = 0;
+  float2 *a_val2 = nullptr, *t_val2 = nullptr;
+  float2 *XD0 = nullptr, *XD1 = nullptr, *XD2 = nullptr;
+  float2 *ud = nullptr, *md = nullptr, *vd = nullptr, *yd = nullptr;
+  float4* bias2 = nullptr;
+  int df_fallbacks = 0;   // double-float runs redone in FP64 (range)
+  int last_kernel = -1;   // kernel of the latest single-vector run (pa_last_run_info)
+  int last_refreshes = 0;
 };
 
 static void* dev_alloc(pa_ctx* h, size_t bytes) {
@@ -308,8 +321,10 @@ extern "C" pa_status pa_create(pa_handle* out, int32_t n_rows, int32_t n_cols, i
   if (o.barrier_timeout_ns <= 0) o.barrier_timeout_ns = 2000000000LL;
   if (o.loss != PA_LOSS_LOGRATIO && o.loss != PA_LOSS_QUADRATIC)
     return fail(PA_ERR_INVALID_ARG, "unknown loss %d", o.loss);
-  if (o.precision != PA_FP64 && o.precision != PA_MIXED)
+  if (o.precision != PA_FP64 && o.precision != PA_MIXED && o.precision != PA_DF64)
     return fail(PA_ERR_INVALID_ARG, "unknown precision mode %d", o.precision);
+  if (o.engine < PA_ENGINE_AUTO || o.engine > PA_ENGINE_MERGED)
+    return fail(PA_ERR_INVALID_ARG, "unknown engine %d", o.engine);
   if (o.equilibrate != PA_EQ_NONE && o.equilibrate != PA_EQ_STORAGE &&
       o.equilibrate != PA_EQ_TARGET)
     return fail(PA_ERR_INVALID_ARG, "unknown equilibration mode %d", o.equilibrate);
@@ -408,6 +423,47 @@ extern "C" pa_status pa_create(pa_handle* out, int32_t n_rows, int32_t n_cols, i
 
 // ------------------------------------------------------------- runs --
 
+// PA_DF64 set-up: the binary exponent range of the sliced values decides
+// whether the double-float variant applies (2^-k A with max |a| in [1/2, 1)
+// must keep every non-zero above 2^-100, so that its low part stays a normal
+// float); if so, the (hi, lo) copies of both sliced matrices and the vectors.
+static pa_status build_df(pa_ctx* h) {
+  pa_status st;
+  int* rng = nullptr;
+  if ((st = alloc_n(h, &rng, 2, "exponent range"))) return st;
+  const int init[2] = {INT_MIN, INT_MAX};
+  int got[2] = {0, 0};
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(rng, init, sizeof init, cudaMemcpyHostToDevice, h->stream)) ||
+      (e = launch_exp_range(h->a_entries, h->sa.val, rng, h->stream, &h->launches)) ||
+      (e = cudaMemcpyAsync(got, rng, sizeof got, cudaMemcpyDeviceToHost, h->stream)) ||
+      (e = cudaStreamSynchronize(h->stream)))
+    return cuda_fail(e, "measuring the value range");
+  dev_free(h, rng);
+  h->df_ok = false;
+  if (h->opt.loss != PA_LOSS_LOGRATIO || got[0] == INT_MIN || got[0] >= 2047 || got[1] < 1 ||
+      got[0] - got[1] > 99)
+    return PA_OK;  // runs use the FP64 kernel
+  h->df_k = got[0] - 1022;  // 2^-k max|a| lies in [1/2, 1)
+  if (h->df_k < -400 || h->df_k > 400) return PA_OK;
+  const size_t n = (size_t)std::max(h->n_rows, h->n_cols);
+  if ((st = alloc_n(h, &h->a_val2, (size_t)h->a_entries + 32, "values (double-float)")) ||
+      (st = alloc_n(h, &h->t_val2, (size_t)h->t_entries + 32, "values (double-float)")) ||
+      (st = alloc_n(h, &h->XD0, n, "iterate (double-float)")) ||
+      (st = alloc_n(h, &h->XD1, n, "iterate (double-float)")) ||
+      (st = alloc_n(h, &h->XD2, n, "iterate (double-float)")) ||
+      (st = alloc_n(h, &h->ud, n, "u (double-float)")) ||
+      (st = alloc_n(h, &h->md, n, "first moment (double-float)")) ||
+      (st = alloc_n(h, &h->vd, n, "second moment (double-float)")) ||
+      (st = alloc_n(h, &h->yd, (size_t)std::max(h->n_rows, 1), "A x (double-float)")))
+    return st;
+  if ((e = launch_split_df(h->a_entries, h->sa.val, h->df_k, h->a_val2, h->stream, &h->launches)) ||
+      (e = launch_split_df(h->t_entries, h->sq.val, h->df_k, h->t_val2, h->stream, &h->launches)))
+    return cuda_fail(e, "splitting the values");
+  h->df_ok = true;
+  return PA_OK;
+}
+
 static pa_status ensure_run_buffers(pa_ctx* h) {
   if (h->run_ready) return PA_OK;
   const size_t n = (size_t)std::max(h->n_rows, h->n_cols);
@@ -431,6 +487,7 @@ static pa_status ensure_run_buffers(pa_ctx* h) {
        (st = alloc_n(h, &h->yf, (size_t)h->n_rows, "A x (FP32)")) ||
        (st = alloc_n(h, &h->dxf, n, "step (FP32)"))))
     return st;
+  if (h->opt.precision == PA_DF64 && (st = build_df(h))) return st;
   h->run_ready = true;
   return PA_OK;
 }
@@ -438,6 +495,8 @@ static pa_status ensure_run_buffers(pa_ctx* h) {
 static int choose_grid(pa_ctx* h, int* maxG_out) {
   int per = 0;
   int maxG = persistent_max_blocks(h->opt.loss, false, &per);
+  maxG = std::min(maxG, merged_max_blocks(h->opt.loss, false));
+  if (h->df_ok) maxG = std::min(maxG, merged_max_blocks(PA_LOSS_LOGRATIO, true));
   if (h->opt.precision == PA_MIXED) {
     maxG = std::min(maxG, persistent_max_blocks(h->opt.loss, true, &per));
     maxG = std::min(maxG, persistent32_max_blocks(&per));
@@ -593,6 +652,22 @@ static pa_status ensure_bias(pa_ctx* h, int iters, double lr, double b1, double 
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // tab is pageable host memory
     if (e != cudaSuccess) return cuda_fail(e, "uploading the bias corrections");
   }
+  if (h->df_ok && iters > 0) {
+    // the same constants as double-word pairs: hi = float(K), lo = float(K - hi)
+    std::vector<float4> t2((size_t)iters);
+    for (int t = 0; t < iters; ++t) {
+      const float k1 = (float)tab[t].x, k2 = (float)tab[t].y;
+      t2[t] = make_float4(k1, (float)(tab[t].x - (double)k1), k2, (float)(tab[t].y - (double)k2));
+    }
+    if (h->bias2) dev_free(h, h->bias2);
+    h->bias2 = nullptr;
+    pa_status st;
+    if ((st = alloc_n(h, &h->bias2, (size_t)iters, "bias table (double-float)"))) return st;
+    cudaError_t e = cudaMemcpyAsync(h->bias2, t2.data(), sizeof(float4) * iters,
+                                    cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "uploading the bias corrections");
+  }
   return PA_OK;
 }
 
@@ -618,7 +693,10 @@ static pa_status status_error(const RunState* rs) {
 // from.  Then sigma of the tracked minimiser; the run state comes back in *out.
 static pa_status fp64_run(pa_ctx* h, pa_mode mode, int iters, int t0, bool fresh_state, bool dd,
                           double b1, double b2, double eps, int G, int maxG, double* L_trace_dev,
-                          double* x_trace_dev, int n_trace, RunState* out, bool cluster = false) {
+                          double* x_trace_dev, int n_trace, RunState* out, bool cluster = false,
+                          int kernel = 0) {
+  // kernel: 0 = the three-phase k_persistent, 1 = the merged-phase kernel in
+  // FP64, 2 = the merged-phase kernel in double-float
   const size_t n = (size_t)h->n_cols;
   cudaError_t e = cudaSuccess;
   if (fresh_state &&
@@ -657,17 +735,53 @@ static pa_status fp64_run(pa_ctx* h, pa_mode mode, int iters, int t0, bool fresh
   p.w2 = (1.0 - b2) / ((1.0 - b1) * (1.0 - b1));
   p.timeout_ns = h->opt.barrier_timeout_ns;
   p.skip_arrival = h->opt.debug_skip_arrival;
-  e = cluster ? launch_persistent_cluster(p, h->opt.loss, G, h->stream, &h->launches)
-              : launch_persistent(p, h->opt.loss, dd, G, h->stream, &h->launches);
+  p.u = h->dx;
+  p.s_scale = 1.0;
+  if (kernel == 2) {
+    p.a_val2 = h->a_val2; p.t_val2 = h->t_val2;
+    p.XD0 = h->XD0; p.XD1 = h->XD1; p.XD2 = h->XD2;
+    p.ud = h->ud; p.md = h->md; p.vd = h->vd; p.yd = h->yd;
+    p.bias2 = h->bias2;
+    p.s_scale = ldexp(1.0, 2 * h->df_k);
+    if (!fresh_state) return fail(PA_ERR_UNSUPPORTED, "double-float runs start from x_init");
+    if ((e = launch_split_df((int64_t)n, h->X0, 0, h->XD0, h->stream, &h->launches)) ||
+        (e = cudaMemsetAsync(h->md, 0, sizeof(float2) * n, h->stream)) ||
+        (e = cudaMemsetAsync(h->vd, 0, sizeof(float2) * n, h->stream)))
+      return cuda_fail(e, "preparing the run");
+  }
+  if (cluster) e = launch_persistent_cluster(p, h->opt.loss, G, h->stream, &h->launches);
+  else if (kernel == 0) e = launch_persistent(p, h->opt.loss, dd, G, h->stream, &h->launches);
+  else e = launch_merged(p, h->opt.loss, kernel == 2, G, h->stream, &h->launches);
   if (e == cudaErrorCooperativeLaunchTooLarge)
     return fail(PA_ERR_LAUNCH, "cooperative grid of %d CTAs does not fit (max %d)", G, maxG);
   if (e != cudaSuccess) return cuda_fail(e, "launching the persistent kernel");
+  if (kernel == 2) {
+    // x_min and the last iterate back to FP64 in the buffers the rest reads
+    RunState rs{};
+    if ((e = cudaMemcpyAsync(&rs, h->st, sizeof(RunState), cudaMemcpyDeviceToHost, h->stream)) ||
+        (e = cudaStreamSynchronize(h->stream)))
+      return cuda_fail(e, "running Projected Adam");
+    if (rs.status == kStatusDfRange) {  // outside the variant's range: the run again in FP64
+      ++h->df_fallbacks;
+      if ((e = cudaMemcpyAsync(h->X0, h->Xinit, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream)))
+        return cuda_fail(e, "preparing the run");
+      return fp64_run(h, mode, iters, t0, fresh_state, dd, b1, b2, eps, G, maxG, L_trace_dev,
+                      x_trace_dev, n_trace, out, false, 1);
+    }
+    float2* xd[3] = {h->XD0, h->XD1, h->XD2};
+    double* x64[3] = {h->X0, h->X1, h->X2};
+    for (int k : {rs.minb, rs.cur})
+      if (k >= 0 && k < 3 && (e = launch_join_df((int64_t)n, xd[k], x64[k], h->stream, &h->launches)))
+        return cuda_fail(e, "converting the iterates");
+  }
   if ((e = launch_sigma(h->sa, h->n_cols, h->X0, h->X1, h->X2, 1, h->st, h->blockpart, dd,
                         h->stream, &h->launches)))
     return cuda_fail(e, "launching the sigma kernel");
   if ((e = cudaMemcpyAsync(out, h->st, sizeof(RunState), cudaMemcpyDeviceToHost, h->stream)) ||
       (e = cudaStreamSynchronize(h->stream)))
     return cuda_fail(e, "running Projected Adam");
+  h->last_kernel = cluster ? 3 : kernel;
+  h->last_refreshes = (kernel == 1 || kernel == 2) ? out->refreshes : 0;
   return PA_OK;
 }
 
@@ -782,8 +896,9 @@ static pa_status run_one(pa_ctx* h, pa_mode mode, int iters, double lr, double b
   // the cluster engine: one thread-block cluster with hardware barriers, for
   // plain FP64 runs of matrices that would use at most 16 CTAs anyway
   bool cluster = false;
-  if (!mixed && h->opt.engine != PA_ENGINE_GRID && h->opt.debug_skip_arrival == 0 &&
-      (h->opt.engine == PA_ENGINE_CLUSTER || G <= 16)) {
+  const bool df = h->opt.precision == PA_DF64 && h->df_ok;
+  if (!mixed && !df && h->opt.engine != PA_ENGINE_GRID && h->opt.engine != PA_ENGINE_MERGED &&
+      h->opt.debug_skip_arrival == 0 && (h->opt.engine == PA_ENGINE_CLUSTER || G <= 16)) {
     const int cmax = persistent_cluster_max(h->opt.loss);
     const int slices = std::max(1, std::min(h->sa.n_slices, h->sq.n_slices));
     int Gc = std::min(std::min(cmax, 16), slices);
@@ -806,8 +921,15 @@ static pa_status run_one(pa_ctx* h, pa_mode mode, int iters, double lr, double b
         if (!ev && (e = cudaEventCreate(&ev))) return cuda_fail(e, "creating the tuner's events");
       if ((e = cudaEventRecord(h->tune_ev[0], h->stream))) return cuda_fail(e, "timing the run");
     }
+    // the merged-phase kernel in double-float for PA_DF64 (when the matrix
+    // fits it) and in FP64 on request; otherwise the three-phase kernel
+    int kernel = 0;
+    if (!cluster && !mixed) {
+      if (h->opt.precision == PA_DF64 && h->df_ok) kernel = 2;
+      else if (h->opt.engine == PA_ENGINE_MERGED) kernel = 1;
+    }
     if ((st = fp64_run(h, mode, iters, 0, true, mixed, b1, b2, eps, G, maxG, L_trace_dev,
-                       x_trace_dev, n_trace, out, cluster)))
+                       x_trace_dev, n_trace, out, cluster, kernel)))
       return st;
     if (tuning) {
       float ms = 0.f;
@@ -1250,6 +1372,16 @@ extern "C" pa_status pa_get_transpose(pa_handle h, int32_t* row_ptr_t, int32_t* 
   return PA_OK;
 }
 
+extern "C" pa_status pa_last_run_info(pa_handle h, int64_t* out) {
+  g_err.clear();
+  if (!h || !out) return fail(PA_ERR_INVALID_ARG, "NULL argument");
+  out[0] = h->last_kernel;
+  out[1] = h->last_refreshes;
+  out[2] = h->df_fallbacks;
+  out[3] = h->last_G;
+  return PA_OK;
+}
+
 extern "C" pa_status pa_last_run_profile(pa_handle h, int* grid, double* busy_ns) {
   g_err.clear();
   if (!h || !grid) return fail(PA_ERR_INVALID_ARG, "NULL argument");
@@ -1510,10 +1642,13 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
       if ((err = cudaMemsetAsync(rs_d, 0, sizeof(RunState), s))) return err;
       for (int i = 0; i < m; ++i) {
         const size_t nx = (size_t)items[i].n_cols * K;
+        // the sigma_max pass clears all three status slots, so no slot that
+        // the host combines below is ever read unwritten
+        const size_t n_status = md == PA_SIGMA_MAX || !(mode & PA_SIGMA_MAX) ? 3 : 1;
         if ((err = cudaMemsetAsync(items[i].M, 0, sizeof(double) * nx, s)) ||
             (err = cudaMemsetAsync(items[i].V, 0, sizeof(double) * nx, s)) ||
             (err = cudaMemsetAsync(items[i].barrier, 0, sizeof(unsigned), s)) ||
-            (err = cudaMemsetAsync(items[i].status, 0, sizeof(int), s)))
+            (err = cudaMemsetAsync(items[i].status, 0, sizeof(int) * n_status, s)))
           return err;
       }
       BatchParams q = bp;
@@ -1537,7 +1672,14 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
         if ((err = launch_batch_sigma(items_d, m, K, blk_item_d, blk_row0_d, nb, 256, blockpart,
                                       item_blk0_d, sig + (size_t)2 * m * K, false, s, L)))
           return err;
-        if (tail == 0) continue;
+        if (tail == 0) {  // the FP32 stage was all of sigma_max: keep its status
+          if (mode & PA_SIGMA_MIN)
+            for (int i = 0; i < m; ++i)
+              if ((err = cudaMemcpyAsync(items[i].status + 2, items[i].status, sizeof(int),
+                                         cudaMemcpyDeviceToDevice, s)))
+                return err;
+          continue;
+        }
         // the FP64 tail continues from the last FP32 iterate and moments
         for (int i = 0; i < m; ++i) {
           const size_t nx = (size_t)items[i].n_cols * K;

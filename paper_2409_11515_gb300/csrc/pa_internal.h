@@ -29,7 +29,8 @@ struct RunState {
   unsigned int barrier;  // monotonically increasing arrival counter
   unsigned int abort;    // set by the first CTA that gives up
   double sigma;        // ||A x_min|| / ||x_min||, written by the sigma kernel
-  double pad;
+  int refreshes;       // merged-phase kernel: iterations that multiplied x itself
+  int pad;
 };
 
 // A row- and column-permuted copy P A Q^T of a matrix in sliced ELL form:
@@ -79,6 +80,16 @@ struct IterParams {
   double w2;      // (1 - beta2) / (1 - beta1)^2
   long long timeout_ns;
   int skip_arrival;
+  // ---- the merged-phase kernel (k_merged) ----
+  double* u;                           // u_t = x_{t-1} - dx_t (FP64 variant)
+  // double-float variant (PA_DF64): values of 2^-k P A Q^T and of its
+  // transpose as (hi, lo) float pairs, and the vectors in the same form
+  const float2* a_val2; const float2* t_val2;
+  float2 *XD0, *XD1, *XD2;             // iterate buffers
+  float2 *ud, *md, *vd, *yd;           // u, Adam moments, y = 2^-k A x
+  const float4* bias2;                 // [iters]: K1 and K2 of `bias` as (hi, lo) pairs
+  double s_scale;                      // 4^k: ||A x||^2 = s_scale ||2^-k A x||^2
+  int win_slices;                      // slices per CTA whose products wait in shared memory
 };
 
 // The mixed-precision sigma_max iteration (FP32 products and Adam state on
@@ -363,5 +374,24 @@ cudaError_t launch_persistent_cluster(const IterParams& p, int loss, int G, cuda
                                       int64_t* launches);
 cudaError_t launch_persistent(const IterParams& p, int loss, bool dd, int G, cudaStream_t s,
                               int64_t* launches);
+
+// The merged-phase persistent kernel: the normalisation of iteration t is
+// folded into the product of iteration t+1 (one full grid barrier and one
+// split barrier per iteration).  df selects the double-float variant
+// (log-ratio loss only).  Internal status for a double-float run whose
+// scalars left the range the variant supports (the caller reruns in FP64):
+constexpr int kStatusDfRange = -100;
+int merged_max_blocks(int loss, bool df);
+cudaError_t launch_merged(const IterParams& p, int loss, bool df, int G, cudaStream_t s,
+                          int64_t* launches);
+// Double-float set-up: the largest and smallest non-zero binary exponents
+// of |vals| (out[0] = max, out[1] = min; out must hold {INT_MIN, INT_MAX}),
+// the split of 2^-k vals into (hi, lo) pairs, and vector conversions.
+cudaError_t launch_exp_range(int64_t n, const double* vals, int* out, cudaStream_t s,
+                             int64_t* launches);
+cudaError_t launch_split_df(int64_t n, const double* in, int k, float2* out, cudaStream_t s,
+                            int64_t* launches);
+cudaError_t launch_join_df(int64_t n, const float2* in, double* out, cudaStream_t s,
+                           int64_t* launches);
 
 }  // namespace pa

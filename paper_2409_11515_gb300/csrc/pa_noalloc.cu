@@ -41,7 +41,10 @@ std::mutex g_mu;
 double* g_scratch_ptr[kMaxDevices] = {};
 
 // Host code cannot use g_sigma_scratch's name as a device address; look the
-// address up once per device, with that device current.
+// address up once per device, with that device current.  The cached address
+// belongs to the device's primary context (the one the CUDA runtime uses):
+// after a cudaDeviceReset, or from a context created through the driver API,
+// it is stale, which the header states as a condition of use.
 cudaError_t scratch_address(int dev, double** out) {
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_scratch_ptr[dev]) {
@@ -89,7 +92,7 @@ extern "C" pa_status pa_sigma_noalloc(int32_t n_rows, int32_t n_cols, const int3
                                       double* sigma, void* cuda_stream) {
   const int64_t n = n_rows > n_cols ? n_rows : n_cols;
   const int64_t max_n = (int64_t)kNoAllocThreads * kNoAllocMaxBlocks;
-  if (n_rows <= 0 || n_cols <= 0 || !row_ptr || !x || !sigma)
+  if (n_rows <= 0 || n_cols <= 0 || !row_ptr || !col_idx || !vals || !x || !sigma)
     return pa::set_error(PA_ERR_INVALID_ARG, "pa_sigma_noalloc: empty matrix or NULL pointer");
   if (n > max_n)
     return pa::set_error(PA_ERR_INVALID_ARG,

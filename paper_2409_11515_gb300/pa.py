@@ -24,9 +24,9 @@ LIB_PATH = _PKG / "_build" / "libpa.so"
 SIGMA_MAX, SIGMA_MIN, BOTH, SIGMA_MIN_LU, BOTH_LU = 1, 2, 3, 4, 5
 HOST, DEVICE = 0, 1
 LOSS_LOGRATIO, LOSS_QUADRATIC = 0, 1
-FP64, MIXED = 0, 1
+FP64, MIXED, DF64 = 0, 1, 2
 EQ_NONE, EQ_STORAGE, EQ_TARGET = 0, 1, 2
-ENGINE_AUTO, ENGINE_GRID, ENGINE_CLUSTER = 0, 1, 2
+ENGINE_AUTO, ENGINE_GRID, ENGINE_CLUSTER, ENGINE_MERGED = 0, 1, 2, 3
 ABLATE_NO_TANGENT, ABLATE_NO_NORMALISE = 1, 2
 
 OK, WARN_SINGULAR = 0, 1
@@ -38,7 +38,7 @@ STATUS_NAMES = {0: "PA_OK", 1: "PA_WARN_SINGULAR", -1: "PA_ERR_INVALID_ARG",
 EXPORTS = ("pa_options_default", "pa_create", "pa_estimate", "pa_run", "pa_estimate_batched",
            "pa_get_vector", "pa_spmv", "pa_spmv_t", "pa_get_transpose", "pa_get_equilibration",
            "pa_kernel_launches", "pa_destroy", "pa_last_error", "pa_set_allocator",
-           "pa_last_run_profile", "pa_sigma_noalloc", "pa_last_batch_graph", "pa_error_bounds", "pa_attach_lu")
+           "pa_last_run_profile", "pa_last_run_info", "pa_sigma_noalloc", "pa_last_batch_graph", "pa_error_bounds", "pa_attach_lu")
 
 ERROR_BOUND_KEYS = ("residual_norm", "b_norm", "x_hat_norm", "thm1_lower", "thm1_upper",
                     "thm2_lower", "thm2_upper", "thm3_upper", "thm4_rounding", "singular")
@@ -113,6 +113,8 @@ def _declare(L):
     L.pa_attach_lu.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, C.c_int]
     L.pa_error_bounds.restype = C.c_int
     L.pa_error_bounds.argtypes = [vp, vp, vp, C.c_int, d, d, d, vp]
+    L.pa_last_run_info.restype = C.c_int
+    L.pa_last_run_info.argtypes = [vp, vp]
     L.pa_last_run_profile.restype = C.c_int
     L.pa_last_run_profile.argtypes = [vp, C.POINTER(C.c_int), vp]
     L.pa_last_batch_graph.restype = C.c_int
@@ -295,6 +297,15 @@ class Handle:
         t = np.zeros((max(g.value, 1), 2))
         _check(load().pa_last_run_profile(self._h, C.byref(g), t.ctypes.data))
         return g.value, t[:g.value]
+
+    def last_run_info(self):
+        """pa_last_run_info: {kernel, refreshes, df_fallbacks, grid} of the
+        latest single-vector run (kernel 0 three-phase grid, 1 merged FP64,
+        2 merged double-float, 3 cluster)."""
+        out = np.zeros(4, dtype=np.int64)
+        _check(load().pa_last_run_info(self._h, out.ctypes.data))
+        return dict(kernel=int(out[0]), refreshes=int(out[1]), df_fallbacks=int(out[2]),
+                    grid=int(out[3]))
 
     def attach_lu(self, L, U, p=None, q=None):
         """pa_attach_lu: P A Q = L U (L lower, U upper triangular, CSR given as
