@@ -5,9 +5,21 @@ Workload: the 401 x 401-cell hydro-mechanical operator (964,806 rows, six
 unknowns per cell, 8 inclusions, viscosity 1e18..1e24 Pa s, seed 2), FP64
 throughout, one seeded start vector; one step = one kappa_2 estimate =
 5000 Projected Adam iterations for sigma_max plus 20000 for sigma_min.
-Metric: Projected Adam iterations per second (whole job).
+Metric: Projected Adam iterations per second (whole job), with the FP64-pipe
+and HBM rooflines of the iteration kernel, the relative error of each sigma
+against the stored full-length CPU-oracle run, the oracle timed on one host
+core and on all host cores (OpenMP build), and an end-to-end figure through
+the C ABI with host buffers.
+
+The same line carries bounded runs of the other configurations under
+"sub_results" (skip them with --no-sub): the headline workload in PA_DF64
+(double-float), the 21 x 21 operator on the cluster engine, 64 operators x 8
+restarts in one batched SpMM launch, and the 1001 x 1001 operator in FP64,
+PA_DF64 and mixed precision -- each with its roofline, its CPU-oracle
+baseline and its errors against the oracle.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload hydro401|hydro21|batched|mixed1001|stress2001|lu64]
 
 --impl reference times the CPU oracle (the plain serial FP64 program under
 oracle/) on a bounded sample of the same workload.  Under torchrun with N > 1
@@ -18,6 +30,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -40,11 +53,46 @@ START_SEED = 1
 
 
 def _peaks():
+    """HBM copy bandwidth (GB/s) measured on the GB300s, or the
+    fallback figure when the measured file is absent."""
     p = ROOT / "MEASURED_PEAKS.json"
     if p.exists():
         d = json.loads(p.read_text())
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def _sm_count():
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+
+
+def fp64_peak_tflops(sm_mhz):
+    """GB300's FP64 pipe: 2 FMA lanes per SM per clock (ncu's dfma peak), 2
+    flops each, times the SM count and the median SM clock under load."""
+    return 2 * 2 * _sm_count() * sm_mhz * 1e6 / 1e12
+
+
+def host_cpu():
+    """Core count and CPU model of this host (the oracle's baseline machine)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.TimeoutExpired):
+        pass
+    if not model:
+        try:
+            for ln in Path("/proc/cpuinfo").read_text().splitlines():
+                if ln.lower().startswith(("model name", "cpu part")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "model": model or "unknown", "arch": platform.machine()}
 
 
 class ClockSampler:
@@ -141,27 +189,31 @@ def flops_per_iteration(n_rows, n_cols, nnz):
     return 4 * nnz + 26 * n_cols
 
 
-def kernel_source_hash():
+KERNEL_SOURCES = {
+    "k_persistent": ("pa_iter.cu", "pa_device.cuh", "pa_internal.h"),
+    "k_merged_df64": ("pa_iter2.cu", "pa_df.cuh", "pa_device.cuh", "pa_internal.h"),
+}
+TRAFFIC_FILE = ROOT / "profiles" / "dram_traffic.json"
+
+
+def kernel_source_hash(kernel="k_persistent"):
     import hashlib
     h = hashlib.sha256()
-    for f in ("pa_iter.cu", "pa_device.cuh", "pa_internal.h"):
+    for f in KERNEL_SOURCES[kernel]:
         h.update((ROOT / "paper_2409_11515_gb300" / "csrc" / f).read_bytes())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic_per_iteration():
-    """DRAM bytes per iteration of k_persistent from the committed ncu summary,
-    or None when the kernel source changed since that capture."""
-    prof = ROOT / "profiles" / "k_persistent_hydro401.md"
-    if not prof.exists():
+def profiled_traffic_per_iteration(kernel="k_persistent", workload="hydro401"):
+    """DRAM bytes per iteration of `kernel` on `workload` from the ncu capture
+    recorded in profiles/dram_traffic.json, or None when the kernel's sources
+    changed since that capture."""
+    if not TRAFFIC_FILE.exists():
         return None
-    src = dram = None
-    for line in prof.read_text().splitlines():
-        if line.startswith("kernel source sha256[:16]:"):
-            src = line.rsplit(":", 1)[1].strip()
-        if line.startswith("dram bytes per iteration:"):
-            dram = float(line.split(":", 1)[1].strip())
-    return dram if (src == kernel_source_hash() and dram) else None
+    rec = json.loads(TRAFFIC_FILE.read_text()).get(f"{kernel}@{workload}")
+    if not rec or rec.get("source_sha16") != kernel_source_hash(kernel):
+        return None
+    return float(rec["dram_bytes_per_iteration"])
 
 
 def bytes_per_iteration(n_rows, n_cols, nnz):
@@ -214,17 +266,35 @@ def _config(A):
             "l2": "working set larger than L2 (A + A^T + 9 vectors of 964806 rows = 231 MB > 129 MB)"}
 
 
-def cpu_baseline(A, x0):
+def cpu_baseline(A, x0, it=150):
+    """The serial oracle on one host core (the contract's baseline) and the
+    OpenMP build of the same source on every host core, `it` sigma_max +
+    `it` sigma_min iterations of the operator each."""
     import oracle
     oracle.build()
-    it = 150
     t0 = time.perf_counter()
     oracle.projected_adam(A, oracle.SIGMA_MAX, it, x_init=x0, **HYPER)
     oracle.projected_adam(A, oracle.SIGMA_MIN, it, x_init=x0, **HYPER)
     dt = time.perf_counter() - t0
-    return {"value": 2 * it / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    cpu = host_cpu()
+    base = {"value": 2 * it / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{it} sigma_max + {it} sigma_min iterations of the same operator "
-                      "(serial C oracle, one host core)"}
+                      "(serial C oracle, one host core)", "host": cpu}
+    try:
+        L = oracle.load_openmp()
+        with oracle.using(L):
+            oracle.projected_adam(A, oracle.SIGMA_MAX, 2, x_init=x0, **HYPER)  # thread start-up
+            t0 = time.perf_counter()
+            oracle.projected_adam(A, oracle.SIGMA_MAX, it, x_init=x0, **HYPER)
+            oracle.projected_adam(A, oracle.SIGMA_MIN, it, x_init=x0, **HYPER)
+            dt = time.perf_counter() - t0
+        all_cores = {"value": 2 * it / dt, "unit": UNIT,
+                     "cores": int(os.environ.get("OMP_NUM_THREADS", cpu["nproc"] or 1)),
+                     "kind": "oracle (OpenMP build of the same source, timing only)",
+                     "sample": base["sample"].replace("one host core", "all host cores")}
+    except (OSError, subprocess.CalledProcessError) as e:
+        all_cores = {"unavailable": f"OpenMP build failed: {e}"}
+    return base, all_cores
 
 
 def oracle_iteration_rate(A, iters, x0):
@@ -250,6 +320,223 @@ def oracle_estimate_baseline(A, iters):
                       f"extrapolated to {EST_ITERS[0]} + {EST_ITERS[1]}"}
 
 
+def _oracle_run(name):
+    """The stored full-length oracle run of a workload (tests/golden), or None."""
+    sys.path.insert(0, str(ROOT / "tests" / "golden"))
+    try:
+        import make_oracle_runs
+        return make_oracle_runs.lookup(name)
+    except Exception:  # no stored run for the current generator and oracle
+        return None
+
+
+def _rel_err(got, ref, key):
+    return None if ref is None else abs(got / ref[key] - 1)
+
+
+def _timed_events(stream, fn):
+    """fn() bracketed by CUDA events on `stream`; (result, seconds)."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    r = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return r, e0.elapsed_time(e1) / 1e3
+
+
+KAPPA_NOTE = ("sigma_min by the direct route (||A x|| / ||x|| minimised on the sphere): on "
+              "these operators it stays far above the true sigma_min, so this kappa is not "
+              "kappa_2(A); the paper's route to kappa_2 is Algorithm 2 (PA_SIGMA_MIN_LU)")
+
+
+def sub_c2_df64(A, stream, it_max, it_min, hbm_peak, ref):
+    """The headline workload in PA_DF64 (double-float merged kernel): one full
+    estimate timed, its roofline against HBM, its errors against the oracle."""
+    from paper_2409_11515_gb300 import pa
+    with pa.create(A, stream=stream, precision=pa.DF64, autotune=4) as h:
+        for _ in range(2):  # warm-up and two tuner rounds each
+            h.estimate(pa.SIGMA_MAX, 500, seed=START_SEED, **HYPER)
+            h.estimate(pa.SIGMA_MIN, 500, seed=START_SEED, **HYPER)
+        rM, tM = _timed_events(stream, lambda: h.estimate(pa.SIGMA_MAX, it_max, seed=START_SEED, **HYPER))
+        infoM = h.last_run_info()
+        rm, tm = _timed_events(stream, lambda: h.estimate(pa.SIGMA_MIN, it_min, seed=START_SEED, **HYPER))
+        infom = h.last_run_info()
+    B = bytes_per_iteration(A.n_rows, A.n_cols, A.nnz)
+    its = it_max + it_min
+    ach = B * its / (tM + tm) / 1e9
+    tpi = profiled_traffic_per_iteration("k_merged_df64")
+    return {
+        "iterations_per_s": its / (tM + tm), "kappa_estimates_per_s": 1.0 / (tM + tm),
+        "precision": "PA_DF64: FP64 input and final sigma; sliced 2^-k A and the vectors as "
+                     "double-float pairs (about 48 significant bits), products and Adam on the "
+                     "FP32 pipe, reductions in FP64; parity-tested to the FP64 bars",
+        "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": ach / hbm_peak, "bytes_per_iteration": B,
+                     "traffic": tpi * its / 2 if tpi else None,
+                     "kernel": "k_merged<0, true, 2> (per-launch CUDA events)"},
+        "result": {"sigma_max": rM["sigma_max"], "sigma_min_direct": rm["sigma_min"],
+                   "kappa_direct": rM["sigma_max"] / rm["sigma_min"],
+                   "rel_err_vs_oracle": {"sigma_max": _rel_err(rM["sigma_max"], ref, "sigma_max"),
+                                         "sigma_min": _rel_err(rm["sigma_min"], ref, "sigma_min")}},
+        "run_info": {"sigma_max": infoM, "sigma_min": infom},
+    }
+
+
+def sub_c1(stream, steps):
+    """C1: the 21 x 21 operator (2,646 rows) on the thread-block-cluster
+    engine, 2000 + 2000 iterations per estimate; errors against the oracle's
+    same-seed run, which also gives the CPU baseline."""
+    import oracle
+    from paper_2409_11515_gb300 import pa, synth
+    A = synth.hydro_operator(21, seed=1)
+    it = 2000
+    with pa.create(A, stream=stream, engine=pa.ENGINE_CLUSTER) as h:
+        h.estimate(pa.BOTH, 100, seed=START_SEED, **HYPER)
+        ts = []
+        for _ in range(max(1, steps)):
+            r, dt = _timed_events(stream, lambda: h.estimate(pa.BOTH, it, seed=START_SEED, **HYPER))
+            ts.append(dt)
+        info = h.last_run_info()
+    t = sum(ts) / len(ts)
+    oracle.build()
+    t0 = time.perf_counter()
+    ro = oracle.estimate(A, it, it, seed=START_SEED, **HYPER)
+    t_cpu = time.perf_counter() - t0
+    B = bytes_per_iteration(A.n_rows, A.n_cols, A.nnz)
+    F = flops_per_iteration(A.n_rows, A.n_cols, A.nnz)
+    return {
+        "workload": "hydro 21x21 cells, 2,646 rows, 2000 + 2000 iterations, cluster engine "
+                    f"({info['grid']} CTAs)",
+        "iterations_per_s": 2 * it / t, "us_per_iteration": 1e6 * t / (2 * it),
+        "roofline": {"bound": "alu", "achieved": F * 2 * it / t / 1e12, "unit": "TFLOP/s",
+                     "algorithmic_GBps": B * 2 * it / t / 1e9,
+                     "note": "working set (0.6 MB) inside L2: latency- and barrier-bound"},
+        "result": {"sigma_max": r["sigma_max"], "sigma_min_direct": r["sigma_min"],
+                   "rel_err_vs_oracle": {"sigma_max": abs(r["sigma_max"] / ro["sigma_max"] - 1),
+                                         "sigma_min": abs(r["sigma_min"] / ro["sigma_min"] - 1)}},
+        "cpu_baseline": {"value": 2 * it / t_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "the same 2000 + 2000 iterations (serial C oracle)"},
+    }
+
+
+def sub_c3(stream, it=(300, 300)):
+    """C3: 64 operators (sides U[51, 301], seed 3) x 8 restarts in one
+    pa_estimate_batched call (SpMM blocks of k = 8, CUDA graph), a bounded
+    run of `it` iterations extrapolated to one estimate; errors of sampled
+    items against the oracle from the same start vectors and iterations."""
+    import oracle
+    from paper_2409_11515_gb300 import pa, synth
+    n_mat, k = 64, 8
+    mats = synth.hydro_batch(n_mat, 51, 301, seed=3)
+    hs = [pa.create(A, stream=stream, autotune=1 if i == 0 else 0) for i, A in enumerate(mats)]
+    try:
+        pa.estimate_batched(hs, pa.BOTH, k, (5, 5), seed=3, **HYPER)
+        rb, tb = _timed_events(stream, lambda: pa.estimate_batched(hs, pa.BOTH, k, it, seed=3, **HYPER))
+    finally:
+        for h in hs:
+            h.destroy()
+    full_T = EST_ITERS[0] + EST_ITERS[1]
+    K = 8
+    B = sum(2 * (12 * A.nnz + 4 * (A.n_rows + 1)) + 72 * A.n_cols * K for A in mats)  # per batch iteration
+    F = sum(flops_per_iteration(A.n_rows, A.n_cols, A.nnz) * K for A in mats)
+    batch_its = (it[0] + it[1])  # each advances all n_mat x K vectors by one iteration
+    hbm_peak, kind = _peaks()
+    ach = B * batch_its / tb / 1e9
+    oracle.build()
+    errs = []
+    t_cpu, rows_cpu = 0.0, 0
+    for i in (0, 32):
+        A = mats[i]
+        x0 = oracle.start_vector(A.n_cols, oracle.splitmix64_at(3, i * k + 0))
+        t0 = time.perf_counter()
+        rM = oracle.projected_adam(A, oracle.SIGMA_MAX, it[0], x_init=x0, **HYPER)
+        rm = oracle.projected_adam(A, oracle.SIGMA_MIN, it[1], x_init=x0, **HYPER)
+        t_cpu += time.perf_counter() - t0
+        rows_cpu += A.n_rows
+        errs.append({"item": i, "restart": 0, "rows": int(A.n_rows),
+                     "sigma_max": abs(rb["sigma_max"][i, 0] / rM.sigma - 1),
+                     "sigma_min": abs(rb["sigma_min"][i, 0] / rm.sigma - 1)})
+    rows = sum(A.n_rows for A in mats)
+    # the oracle's seconds per row-iteration, scaled to one estimate of every item
+    est_cpu = (t_cpu / (rows_cpu * (it[0] + it[1]))) * rows * k * full_T
+    return {
+        "workload": "64 hydro operators, sides U[51,301] (seed 3), 8 restarts each, one "
+                    "persistent SpMM launch per sigma mode (k = 8) in a CUDA graph",
+        "rows_total": int(rows), "nnz_total": int(sum(A.nnz for A in mats)),
+        "iters_timed": list(it), "cuda_graph": rb["cuda_graph"],
+        "vector_iterations_per_s": n_mat * k * batch_its / tb,
+        "kappa_estimates_per_s": n_mat * k / (tb * full_T / batch_its),
+        "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": ach / hbm_peak, "bytes_per_batch_iteration": B,
+                     "fp64_pipe_TFLOPs": F * batch_its / tb / 1e12},
+        "rel_err_vs_oracle_sampled": errs,
+        "cpu_baseline": {"value": n_mat * k / est_cpu, "unit": "estimates/s", "cores": 1,
+                         "kind": "oracle",
+                         "sample": f"items 0 and 32, restart 0, {it[0]} + {it[1]} iterations "
+                                   "(serial C oracle), row-weighted and extrapolated to one "
+                                   "estimate of all 512 items"},
+        "note": "estimates/s extrapolate the timed iterations to 5000 + 20000 per estimate",
+    }
+
+
+def sub_c4(stream, hbm_peak, dd_iters=1000):
+    """C4: the 1001 x 1001 operator (6,012,006 rows): one full FP64 estimate,
+    one full PA_DF64 estimate, the MIXED sigma_max (FP32 stage + FP64 tail,
+    full length) and a bounded run of the MIXED Dot2 sigma_min; errors of the
+    full runs against the stored full-length oracle run."""
+    import oracle
+    from paper_2409_11515_gb300 import pa, synth
+    A = synth.hydro_operator(1001, n_incl=8, eta_lo=1e18, eta_hi=1e24, seed=4)
+    ref = _oracle_run("hydro1001")
+    B = bytes_per_iteration(A.n_rows, A.n_cols, A.nnz)
+    its = EST_ITERS[0] + EST_ITERS[1]
+    out = {"workload": "hydro 1001x1001 cells, 6,012,006 rows, 5000 + 20000 iterations",
+           "n_rows": int(A.n_rows), "nnz": int(A.nnz), "bytes_per_iteration": B,
+           "oracle_reference": "stored full-length run (tests/golden/oracle_runs.json)"
+                               if ref else "no stored full-length oracle run for this build"}
+    for name, opt in (("fp64", {}), ("df64", dict(precision=pa.DF64))):
+        with pa.create(A, stream=stream, **opt) as h:
+            h.estimate(pa.SIGMA_MAX, 50, seed=START_SEED, **HYPER)
+            rM, tM = _timed_events(stream, lambda: h.estimate(pa.SIGMA_MAX, EST_ITERS[0], seed=START_SEED, **HYPER))
+            rm, tm = _timed_events(stream, lambda: h.estimate(pa.SIGMA_MIN, EST_ITERS[1], seed=START_SEED, **HYPER))
+            info = h.last_run_info()
+        ach = B * its / (tM + tm) / 1e9
+        out[name] = {"iterations_per_s": its / (tM + tm), "kappa_estimates_per_s": 1 / (tM + tm),
+                     "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                                  "frac": ach / hbm_peak},
+                     "sigma_max": rM["sigma_max"], "sigma_min_direct": rm["sigma_min"],
+                     "rel_err_vs_oracle": {"sigma_max": _rel_err(rM["sigma_max"], ref, "sigma_max"),
+                                           "sigma_min": _rel_err(rm["sigma_min"], ref, "sigma_min")},
+                     "kernel": info["kernel"]}
+    with pa.create(A, stream=stream, precision=pa.MIXED) as h:
+        h.estimate(pa.SIGMA_MAX, 50, seed=START_SEED, **HYPER)
+        rM, tM = _timed_events(stream, lambda: h.estimate(pa.SIGMA_MAX, EST_ITERS[0], seed=START_SEED, **HYPER))
+        rm, tm = _timed_events(stream, lambda: h.estimate(pa.SIGMA_MIN, dd_iters, seed=START_SEED, **HYPER))
+    Bm = 2 * (8 * A.nnz + 4 * (A.n_rows + 1)) + 56 * A.n_cols  # FP32 values/vectors, FP64 m, v
+    out["mixed"] = {
+        "sigma_max_iterations_per_s": EST_ITERS[0] / tM,
+        "sigma_max_roofline": {"bound": "hbm", "achieved": Bm * EST_ITERS[0] / tM / 1e9,
+                               "peak": hbm_peak, "unit": "GB/s",
+                               "frac": Bm * EST_ITERS[0] / tM / 1e9 / hbm_peak},
+        "sigma_max": rM["sigma_max"],
+        "sigma_max_rel_err_vs_oracle": _rel_err(rM["sigma_max"], ref, "sigma_max"),
+        "dot2_sigma_min_iterations_per_s": dd_iters / tm,
+        "kappa_estimates_per_s": 1.0 / (tM + EST_ITERS[1] * tm / dd_iters),
+        "note": f"sigma_min (Dot2 products) timed over {dd_iters} iterations and extrapolated"}
+    oracle.build()
+    t0 = time.perf_counter()
+    x0 = oracle.start_vector(A.n_cols, START_SEED)
+    oracle.projected_adam(A, oracle.SIGMA_MAX, 5, x_init=x0, **HYPER)
+    oracle.projected_adam(A, oracle.SIGMA_MIN, 5, x_init=x0, **HYPER)
+    rate = 10 / (time.perf_counter() - t0)
+    out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                           "sample": "5 + 5 iterations of the same operator (serial C oracle)",
+                           "kappa_estimates_per_s": rate / its}
+    return out
+
+
 def run_ours(args):
     ws, rank, local = _dist()
     import torch
@@ -267,7 +554,9 @@ def run_ours(args):
                              seed=WORKLOAD["seed"])
     stream = torch.cuda.Stream()
     tune_rounds = min(args.autotune, 2 * args.warmup)  # all of them inside the warm-up
-    h = pa.create(A, stream=stream, autotune=tune_rounds)
+    df = args.precision == "df64"
+    prec = pa.DF64 if df else pa.FP64
+    h = pa.create(A, stream=stream, autotune=tune_rounds, precision=prec)
     it_per_step = ITERS_MAX + ITERS_MIN
 
     def step(handle):
@@ -297,42 +586,9 @@ def run_ours(args):
     value = whole_job_value(it_per_step * args.steps, ms / 1e3, ws)
     # ---- roofline of the persistent kernel: per-launch time on its own stream
     kms = []
-    r_fp64 = None
     for iters, mode in ((ITERS_MAX, pa.SIGMA_MAX), (ITERS_MIN, pa.SIGMA_MIN)):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        rr = h.estimate(mode, iters, seed=START_SEED, **HYPER)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        kms.append((iters, e0.elapsed_time(e1)))
-        r_fp64 = rr
-    # ---- mixed precision on the same workload (PA_MIXED): FP32 sigma_max with
-    # an FP64 tail, compensated sigma_min; errors against this run's FP64 sigmas
-    variants = None
-    if not args.no_variants:
-        with pa.create(A, stream=stream, precision=pa.MIXED) as hm:
-            hm.estimate(pa.SIGMA_MAX, 50, seed=START_SEED, **HYPER)  # warm-up
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            rm = hm.estimate(pa.SIGMA_MAX, ITERS_MAX, seed=START_SEED, **HYPER)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            t_max = e0.elapsed_time(e1) / 1e3
-            it_dd = max(1, ITERS_MIN // 10)
-            e0.record(stream)
-            rd = hm.estimate(pa.SIGMA_MIN, it_dd, seed=START_SEED, **HYPER)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            t_dd = e0.elapsed_time(e1) / 1e3
-        variants = {
-            "mixed_sigma_max": {"iterations_per_s": ITERS_MAX / t_max, "iters": ITERS_MAX,
-                                "sigma_max": rm["sigma_max"],
-                                "rel_err_vs_fp64": abs(rm["sigma_max"] / r_fp64["sigma_max"] - 1),
-                                "precision": "FP32 products and Adam state on D_r^-1 A D_c^-1, "
-                                             "FP64 norms, last iters/10 in FP64"},
-            "compensated_sigma_min": {"iterations_per_s": it_dd / t_dd, "iters": it_dd,
-                                      "precision": "FP64 with double-double (Dot2) products"},
-        }
+        _, dt = _timed_events(stream, lambda: h.estimate(mode, iters, seed=START_SEED, **HYPER))
+        kms.append((iters, dt * 1e3))
     B = bytes_per_iteration(A.n_rows, A.n_cols, A.nnz)
     F = flops_per_iteration(A.n_rows, A.n_cols, A.nnz)
     tot_it = sum(i for i, _ in kms)
@@ -341,18 +597,27 @@ def run_ours(args):
     achieved_f = F * tot_it / (tot_ms / 1e3) / 1e12
     peak, peak_kind = _peaks()
     clk = clocks.get("sm_mhz") or 2070.0
-    # FP64 pipe: 2 FMA lanes per SM per clock (ncu: dfma peak 2/cycle/SM), 152 SMs
-    fp64_peak = 2 * 2 * 152 * clk * 1e6 / 1e12
-    tpi = profiled_traffic_per_iteration()
+    fp64_peak = fp64_peak_tflops(clk)
+    kname = "k_merged_df64" if df else "k_persistent"
+    tpi = profiled_traffic_per_iteration(kname)
     launch_iters = tot_it / len(kms)
     h.destroy()
+    ref = _oracle_run("hydro401") if (ITERS_MAX, ITERS_MIN) == EST_ITERS else None
+    # ---- the other configurations, each on a bounded sample (rank 0 only)
+    subs = None
+    if rank == 0 and not args.no_sub and not df:
+        subs = {}
+        subs["c2_df64"] = sub_c2_df64(A, stream, ITERS_MAX, ITERS_MIN, peak, ref)
+        subs["c1_hydro21_cluster"] = sub_c1(stream, args.steps if args.steps <= 3 else 3)
+        subs["c3_batched64"] = sub_c3(stream)
+        subs["c4_hydro1001"] = sub_c4(stream, peak)
     # ---- end to end through the C ABI with host buffers
     e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 2))
     torch.cuda.synchronize()
     _barrier(ws)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        with pa.create(A, stream=stream, autotune=tune_rounds) as he:
+        with pa.create(A, stream=stream, autotune=tune_rounds, precision=prec) as he:
             he.estimate(pa.SIGMA_MAX, ITERS_MAX, seed=START_SEED, **HYPER)
             re = he.estimate(pa.SIGMA_MIN, ITERS_MIN, seed=START_SEED, **HYPER)
     torch.cuda.synchronize()
@@ -364,33 +629,43 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": "df64 (2xf32)" if df else "f64",
             "data": "synthetic (seeded hydro-mechanical operator generator)",
             "config": dict(_config(A), parallelism=f"replicas{ws}" if ws > 1 else "single_gpu",
+                           precision="PA_DF64" if df else "fp64",
                            partition=(f"measured-cost tuner, {tune_rounds} rounds in warm-up"
                                       if tune_rounds > 0 else "fixed cost model")),
             "kappa_estimates_per_s": ws * args.steps / (ms / 1e3),
-            "result": {"sigma_max": r["sigma_max"], "sigma_min": r["sigma_min"],
-                       "kappa": r["kappa"], "status": r["status"]},
+            "result": {"sigma_max": r["sigma_max"], "sigma_min_direct": r["sigma_min"],
+                       "kappa_direct": r["kappa"], "kappa_note": KAPPA_NOTE,
+                       "status": r["status"],
+                       "rel_err_vs_oracle": {"sigma_max": _rel_err(r["sigma_max"], ref, "sigma_max"),
+                                             "sigma_min": _rel_err(r["sigma_min"], ref, "sigma_min"),
+                                             "reference": "stored full-length oracle run "
+                                                          "(tests/golden/oracle_runs.json)"
+                                                          if ref else None}},
             "roofline": {"bound": "alu", "achieved": achieved_f, "peak": fp64_peak,
                          "unit": "TFLOP/s", "frac": achieved_f / fp64_peak, "traffic": traffic,
-                         "kernel": "k_persistent, FP64 (per-launch CUDA events on its stream)",
-                         "peak_source": "FP64 pipe: 2 FMA lanes/SM/clock x 152 SMs x 2 flops "
-                                        "x median SM clock under load",
+                         "kernel": ("k_merged<0, true, 2>, double-float" if df else
+                                    "k_persistent<0, 0, 0>, FP64") +
+                                   " (per-launch CUDA events on its stream)",
+                         "peak_source": f"FP64 pipe: 2 FMA lanes/SM/clock x {_sm_count()} SMs x 2 "
+                                        "flops x median SM clock under load (derived)",
                          "flops_per_iteration": F, "iterations_per_launch": launch_iters,
-                         "traffic_source": "ncu dram bytes per iteration x iterations per launch "
-                                           "(profiles/k_persistent_hydro401.md)"},
+                         "traffic_source": "ncu dram bytes per iteration (profiles/dram_traffic.json) "
+                                           "x iterations per launch"},
             "roofline_hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "bytes_per_iteration": B,
                              "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json)"},
-            "variants_same_workload": variants,
+            "sub_results": subs,
             "clocks": clocks,
             "gpu_launches": launches,
             "e2e": {"value": whole_job_value(it_per_step * e2e_steps, e2e_s, ws), "unit": UNIT,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         }
         if ws == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(A, _start_vector_host(A.n_cols))
+            line["cpu_baseline"], line["cpu_baseline_all_cores"] = cpu_baseline(
+                A, _start_vector_host(A.n_cols))
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
@@ -776,7 +1051,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
-    ap.add_argument("--no-variants", action="store_true", help="skip the mixed-precision leg")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="skip the bounded runs of the other configurations (C1, C3, C4, DF64)")
     ap.add_argument("--workload", choices=["hydro401", "hydro21", "batched", "mixed1001",
                                            "stress2001", "lu64"],
                     default="hydro401",
@@ -784,8 +1060,9 @@ def main():
                          "engine, LU route); batched: 64 operators x 8 restarts; "
                          "mixed1001: 1001x1001 mixed vs FP64; stress2001: 2001x1001, 32 restarts; "
                          "lu64: 64 small operators, kappa through the LU route")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
-                    help="batched workload: the handles' precision mode")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "df64"], default="fp64",
+                    help="the handles' precision mode: the default workload takes fp64 "
+                         "(the benchmark line) or df64; the batched workload fp64 or mixed")
     ap.add_argument("--iters-max", type=int, default=None,
                     help="sigma_max iterations per estimate (short runs for profiling); "
                          "default 5000, stress2001 200, batched 500 (timed, then extrapolated)")

@@ -24,6 +24,7 @@ _HERE = Path(__file__).resolve().parent
 _SRC = _HERE / "pa_oracle.c"
 _BUILD = _HERE / "_build"
 _LIB_PATH = _BUILD / "liboracle.so"
+_OMP_PATH = _BUILD / "liboracle_omp.so"
 _lock = threading.Lock()
 _lib = None
 
@@ -34,17 +35,25 @@ OK, SINGULAR, NONFINITE = 0, 1, -4
 
 
 def build(force: bool = False, openmp: bool = False) -> Path:
-    """Compile pa_oracle.c into oracle/_build/liboracle.so (gcc, -O2, no FMA contraction)."""
+    """Compile pa_oracle.c into oracle/_build/liboracle.so (gcc, -O2, no FMA
+    contraction).  openmp=True builds liboracle_omp.so from the same source
+    with -fopenmp: the same arithmetic with the loops on all host cores and
+    per-thread partial sums -- for timing the oracle only, never as checker."""
     _BUILD.mkdir(exist_ok=True)
-    out = _LIB_PATH
+    out = _OMP_PATH if openmp else _LIB_PATH
     if not force and out.exists() and out.stat().st_mtime >= _SRC.stat().st_mtime:
         return out
     tmp = out.with_suffix(f".{os.getpid()}.tmp.so")
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-shared", "-fPIC",
-           str(_SRC), "-o", str(tmp), "-lm"]
+           *(["-fopenmp"] if openmp else []), str(_SRC), "-o", str(tmp), "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out
+
+
+def load_openmp() -> C.CDLL:
+    """The OpenMP timing build (see build); use it through `using(...)`."""
+    return load(build(openmp=True))
 
 
 def load(path) -> C.CDLL:

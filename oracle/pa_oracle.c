@@ -31,6 +31,13 @@
  *                         (triangular solves with given L, U factors):
  *                         sigma_min(A) = 1 / ||A^{-1}||_2.
  *
+ * Timing build: compiled with -fopenmp (oracle.build(openmp=True)), the
+ * "#pragma omp" lines below run the row loops and the element loops on all
+ * host cores and reduce the sums (dot products, the transposed scatter) per
+ * thread.  That changes the summation order, so the OpenMP build only times
+ * the oracle on many cores; the checker is always the serial build, where
+ * the pragmas are ignored.
+ *
  * Readings where the paper is silent (all stated again in the design notes):
  *   - sigma_min: minimise L(x) = log||Ax|| - log||x|| on the sphere with the
  *     same Algorithm 1 (the negated loss of Eq. nabla_loss), not the LU route
@@ -94,6 +101,7 @@ void po_start_vector(int64_t n, uint64_t seed, double* x) {
 
 void po_spmv(int32_t n_rows, const int32_t* row_ptr, const int32_t* col, const double* val,
              const double* x, double* y) {
+#pragma omp parallel for schedule(static)
   for (int32_t i = 0; i < n_rows; ++i) {
     double acc = 0.0;
     for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) acc = acc + val[k] * x[col[k]];
@@ -106,6 +114,7 @@ void po_spmv(int32_t n_rows, const int32_t* row_ptr, const int32_t* col, const d
 void po_spmv_t(int32_t n_rows, int32_t n_cols, const int32_t* row_ptr, const int32_t* col,
                const double* val, const double* y, double* z) {
   for (int32_t j = 0; j < n_cols; ++j) z[j] = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : z[:n_cols])
   for (int32_t i = 0; i < n_rows; ++i)
     for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) z[col[k]] = z[col[k]] + val[k] * y[i];
 }
@@ -178,6 +187,7 @@ void po_spmv_t_dd(int32_t n_rows, int32_t n_cols, const int32_t* row_ptr, const 
 
 static double po_dot(int64_t n, const double* a, const double* b) {
   double acc = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : acc)
   for (int64_t i = 0; i < n; ++i) acc = acc + a[i] * b[i];
   return acc;
 }
@@ -193,6 +203,7 @@ static double po_loss(int mode, int loss, double s, double q) {
  * q = ||x||^2; negated for sigma_min.  Quadratic reading: -2z / +2z. */
 static void po_grad_from(int mode, int loss, int64_t n, const double* x, const double* z,
                          double s, double q, double* g) {
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     double gi;
     if (loss == PO_LOSS_LOGRATIO)
@@ -299,6 +310,7 @@ int po_projected_adam(int32_t n_rows, int32_t n_cols, const int32_t* row_ptr, co
     /* biased moments, bias correction, update */
     double bc1 = 1.0 - pow(beta1, (double)t);
     double bc2 = 1.0 - pow(beta2, (double)t);
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
       m[i] = beta1 * m[i] + (1.0 - beta1) * g[i];
       v[i] = beta2 * v[i] + (1.0 - beta2) * (g[i] * g[i]);
@@ -309,12 +321,15 @@ int po_projected_adam(int32_t n_rows, int32_t n_cols, const int32_t* row_ptr, co
     /* project the update onto the tangent space of the sphere at x */
     if (!(flags & PO_FLAG_NO_TANGENT)) {
       double c = po_dot(n, x, dx);
+#pragma omp parallel for schedule(static)
       for (int64_t i = 0; i < n; ++i) dx[i] = dx[i] - c * x[i];
     }
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) x[i] = x[i] - dx[i];
     /* back onto the unit sphere */
     if (!(flags & PO_FLAG_NO_NORMALISE)) {
       double nrm = sqrt(po_dot(n, x, x));
+#pragma omp parallel for schedule(static)
       for (int64_t i = 0; i < n; ++i) x[i] = x[i] / nrm;
     }
     t_done = t;

@@ -1,7 +1,8 @@
-"""bench.py's roofline traffic comes from the committed ncu summary of the
-FP64 iteration kernel, and only while the kernel sources hash to the value
-recorded there (host logic only, no GPU)."""
+"""bench.py's roofline traffic comes from the ncu captures recorded in
+profiles/dram_traffic.json, and only while the captured kernel's sources hash
+to the value recorded there (host logic only, no GPU)."""
 import importlib.util
+import json
 from pathlib import Path
 
 ROOT = Path(__file__).resolve().parents[1]
@@ -14,14 +15,24 @@ def _bench():
     return mod
 
 
-def test_profiled_traffic_follows_the_recorded_hash():
+def test_profiled_traffic_follows_the_recorded_hash(tmp_path, monkeypatch):
     b = _bench()
-    text = (ROOT / "profiles" / "k_persistent_hydro401.md").read_text().splitlines()
-    rec = [l.rsplit(":", 1)[1].strip() for l in text if l.startswith("kernel source sha256[:16]:")]
-    dram = [float(l.split(":", 1)[1]) for l in text if l.startswith("dram bytes per iteration:")]
-    assert len(rec) == 1 and len(dram) == 1 and len(rec[0]) == 16
-    got = b.profiled_traffic_per_iteration()
-    if rec[0] == b.kernel_source_hash():
-        assert got == dram[0]
-    else:
-        assert got is None
+    recs = json.loads((ROOT / "profiles" / "dram_traffic.json").read_text())
+    assert recs, "no capture recorded"
+    for key, rec in recs.items():
+        kernel, workload = key.split("@")
+        assert kernel in b.KERNEL_SOURCES and len(rec["source_sha16"]) == 16
+        assert rec["dram_bytes_per_iteration"] > 0 and rec["summary"].startswith("profiles/")
+        assert (ROOT / rec["summary"]).exists()
+        got = b.profiled_traffic_per_iteration(kernel, workload)
+        if rec["source_sha16"] == b.kernel_source_hash(kernel):
+            assert got == rec["dram_bytes_per_iteration"]
+        else:
+            assert got is None
+    # a record whose hash no longer matches the sources gives no traffic
+    fake = tmp_path / "dram_traffic.json"
+    fake.write_text(json.dumps({"k_persistent@hydro401": {
+        "source_sha16": "0" * 16, "dram_bytes_per_iteration": 1.0,
+        "summary": "profiles/k_persistent_hydro401.md"}}))
+    monkeypatch.setattr(b, "TRAFFIC_FILE", fake)
+    assert b.profiled_traffic_per_iteration("k_persistent", "hydro401") is None
