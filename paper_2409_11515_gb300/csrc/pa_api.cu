@@ -100,6 +100,11 @@ struct pa_ctx {
   // Algorithm 2: the attached factors in level-scheduled form
   bool have_lu = false, have_min_lu = false, have_min_direct = false;
   TriSys lu_sys[4] = {};          // L, U, U^T, L^T
+  TriRows lu_rows[4] = {};        // the same systems in row form (the grid kernel)
+  double* lu_y4 = nullptr;        // the grid kernel's four solve vectors [4][n]
+  double* lu_part = nullptr;      // its per-CTA partial sums
+  int lu_part_G = 0;
+  int lu_last_kernel = -1;        // 0: one CTA (level steps), 1: the grid (row waits)
   int32_t* lu_p = nullptr;        // row permutation (null = identity)
   std::vector<void*> lu_bufs;     // device arrays of the factors
   double* xmin_lu = nullptr;      // x_min of the latest LU-route run (source order)
@@ -993,6 +998,18 @@ static pa_status to_host(pa_ctx* h, const T* src, size_t count, int kind, std::v
   return e == cudaSuccess ? PA_OK : cuda_fail(e, "reading the LU factors");
 }
 
+static pa_status upload_rows(pa_ctx* h, const TriRowsHost& t, TriRows* out) {
+  int32_t *rp, *ci, *order;
+  double *va, *dinv;
+  pa_status st;
+  if ((st = upload(h, t.rp, &rp, "LU rows")) || (st = upload(h, t.ci, &ci, "LU rows")) ||
+      (st = upload(h, t.va, &va, "LU rows")) || (st = upload(h, t.dinv, &dinv, "LU rows")) ||
+      (st = upload(h, t.order, &order, "LU rows")))
+    return st;
+  *out = TriRows{rp, ci, va, dinv, order};
+  return PA_OK;
+}
+
 static pa_status upload_tri(pa_ctx* h, const TriHost& t, TriSys* out) {
   double *dinv, *va;
   int4 *linfo, *items;
@@ -1072,6 +1089,18 @@ extern "C" pa_status pa_attach_lu(pa_handle h, const int32_t* l_row_ptr, const i
       (st = upload_tri(h, tut, &h->lu_sys[2])) || (st = upload_tri(h, tlt, &h->lu_sys[3])) ||
       (p && (st = upload(h, pp, &h->lu_p, "LU permutation"))))
     return (free_lu(h), st);
+  {  // the row form for the grid kernel
+    TriRowsHost r;
+    const int32_t* rps[4] = {lrp.data(), urp.data(), utrp.data(), ltrp.data()};
+    const int32_t* cis[4] = {lci.data(), uci.data(), utci.data(), ltci.data()};
+    const double* vas[4] = {lva.data(), uva.data(), utva.data(), ltva.data()};
+    for (int k = 0; k < 4; ++k) {
+      tri_rows_host(n, rps[k], cis[k], vas[k], k % 2 == 0, &r);
+      if ((st = upload_rows(h, r, &h->lu_rows[k]))) return (free_lu(h), st);
+    }
+    if ((st = alloc_n(h, &h->lu_y4, (size_t)4 * n, "LU solve vectors"))) return (free_lu(h), st);
+    h->lu_bufs.push_back(h->lu_y4);
+  }
   if (!h->xmin_lu &&
       ((st = alloc_n(h, &h->xmin_lu, (size_t)n, "x_min")) ||
        (st = alloc_n(h, &h->lu_w, (size_t)n, "LU vectors")) ||
@@ -1121,19 +1150,57 @@ static pa_status lu_run(pa_ctx* h, const double* x0, int iters, double lr, doubl
   p.beta1 = b1;
   p.beta2 = b2;
   const size_t smem = lu_layout(&p);
-  if (!h->lu_params && (st = alloc_n(h, &h->lu_params, 1, "LU run parameters"))) return st;
-  if ((e = cudaMemcpyAsync(h->lu_params, &p, sizeof(LuParams), cudaMemcpyHostToDevice, h->stream)) ||
-      (e = cudaStreamSynchronize(h->stream)) ||  // p lives on this stack frame
-      (e = launch_lu_iter(h->lu_params, 1, smem, p.smem_mode == 1, h->stream, &h->launches)) ||
-      (e = cudaMemcpyAsync(out, h->st, sizeof(RunState), cudaMemcpyDeviceToHost, h->stream)) ||
-      (e = cudaStreamSynchronize(h->stream)))
-    return cuda_fail(e, "running the LU route");
+  // one CTA stepping through the levels while the solve vector fits in its
+  // shared memory; past that, the whole grid with per-row waits (engine
+  // GRID / CLUSTER force one or the other)
+  const bool grid = h->opt.engine == PA_ENGINE_GRID ||
+                    (h->opt.engine != PA_ENGINE_CLUSTER && p.smem_mode == 0);
+  h->lu_last_kernel = grid ? 1 : 0;
+  if (grid) {
+    const int G = lu_grid_max_blocks();
+    if (G <= 0) return fail(PA_ERR_LAUNCH, "the LU grid kernel does not fit on this GPU");
+    if (h->lu_part_G < G) {
+      if (h->lu_part) dev_free(h, h->lu_part);
+      h->lu_part = nullptr;
+      if ((st = alloc_n(h, &h->lu_part, (size_t)4 * G, "LU partials"))) return st;
+      h->lu_part_G = G;
+    }
+    LuGridParams g{};
+    g.n = p.n;
+    for (int k = 0; k < 4; ++k) {
+      g.sys[k] = h->lu_rows[k];
+      g.y[k] = h->lu_y4 + (size_t)k * p.n;
+    }
+    g.p = p.p;
+    g.x = p.x; g.xmin = p.xmin; g.m = p.m; g.v = p.v; g.dx = p.dx; g.w = p.w;
+    g.partials = h->lu_part;
+    g.bias = p.bias;
+    g.L_trace = p.L_trace; g.x_trace = p.x_trace; g.n_trace = p.n_trace;
+    g.st = p.st;
+    g.iters = p.iters; g.t0 = p.t0;
+    g.beta1 = p.beta1; g.beta2 = p.beta2;
+    g.timeout_ns = h->opt.barrier_timeout_ns;
+    if ((e = launch_lu_grid(g, G, h->stream, &h->launches)) ||
+        (e = cudaMemcpyAsync(out, h->st, sizeof(RunState), cudaMemcpyDeviceToHost, h->stream)) ||
+        (e = cudaStreamSynchronize(h->stream)))
+      return cuda_fail(e, "running the LU route on the grid");
+  } else {
+    if (!h->lu_params && (st = alloc_n(h, &h->lu_params, 1, "LU run parameters"))) return st;
+    if ((e = cudaMemcpyAsync(h->lu_params, &p, sizeof(LuParams), cudaMemcpyHostToDevice, h->stream)) ||
+        (e = cudaStreamSynchronize(h->stream)) ||  // p lives on this stack frame
+        (e = launch_lu_iter(h->lu_params, 1, smem, p.smem_mode == 1, h->stream, &h->launches)) ||
+        (e = cudaMemcpyAsync(out, h->st, sizeof(RunState), cudaMemcpyDeviceToHost, h->stream)) ||
+        (e = cudaStreamSynchronize(h->stream)))
+      return cuda_fail(e, "running the LU route");
+  }
   if ((st = status_error(out))) return st;
   const double sig_inv = out->sigma;  // ||A^{-1} x_min|| / ||x_min||
   out->sigma = 1.0 / sig_inv;
   h->sigma_min = out->sigma;
   h->have_min = true;
   h->have_min_lu = true;
+  h->last_kernel = grid ? 5 : 4;
+  h->last_refreshes = 0;
   return (pa_status)out->status;
 }
 

@@ -318,6 +318,43 @@ size_t lu_layout(LuParams* p);
 // (else all items run with their solve vector in global memory).
 cudaError_t launch_lu_iter(const LuParams* items_dev, int n_items, size_t smem, bool all_smem,
                            cudaStream_t s, int64_t* launches);
+// ---- Algorithm 2 on the whole grid (pa_lu_grid.cu), for large factors ----
+// One triangular system in row form: row i's off-diagonal entries
+// ci/va[rp[i] .. rp[i+1]) with va_ij = -T_ij / T_ii, and dinv_i = 1 / T_ii.
+// order: the rows sorted by level (lower: row i depends on j < i; upper: on
+// j > i), the sequence the grid kernel's warps take them in.
+struct TriRows {
+  const int32_t* rp;
+  const int32_t* ci;
+  const double* va;
+  const double* dinv;
+  const int32_t* order;
+};
+struct TriRowsHost {
+  std::vector<int32_t> rp, ci, order;
+  std::vector<double> va, dinv;
+};
+// Row form of a triangular CSR whose diagonal entries are present and non-zero
+// (tri_analyse checks that first).
+void tri_rows_host(int32_t n, const int32_t* rp, const int32_t* ci, const double* va, bool lower,
+                   TriRowsHost* out);
+struct LuGridParams {
+  int32_t n;
+  TriRows sys[4];            // L, U, U^T, L^T (lower, upper, lower, upper)
+  const int32_t* p;          // row permutation of P A = L U Q^T (null = identity)
+  double *x, *xmin, *m, *v, *dx, *w;
+  double* y[4];              // the four solve vectors
+  double* partials;          // [G][4]
+  const double2* bias;
+  double* L_trace; double* x_trace; int n_trace;
+  RunState* st;
+  int iters, t0;
+  double beta1, beta2;
+  long long timeout_ns;
+};
+int lu_grid_max_blocks();
+cudaError_t launch_lu_grid(const LuGridParams& p, int G, cudaStream_t s, int64_t* launches);
+
 // Host analysis for TriSys: checks triangularity and non-zero diagonals,
 // computes the levels and builds the step lists.  lower: row i depends on
 // columns j < i; else on j > i.  Returns an empty string or the reason the

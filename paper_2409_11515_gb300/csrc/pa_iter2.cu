@@ -50,7 +50,6 @@
 // the per-iteration scalars stay in FP64.  A run whose ||y||^2 leaves
 // [2^-100, 2^100] ends with kStatusDfRange and the host reruns it in FP64.
 #include <math.h>
-#include <stdlib.h>
 
 #include <algorithm>
 #include <climits>
@@ -656,18 +655,12 @@ int conv_blocks(int64_t n) { return (int)std::min<int64_t>(4096, (n + 255) / 256
 
 }  // namespace
 
-// The double-float variant is built for two CTAs of 512 threads per SM (64
-// registers, a few bytes of spill), which measured faster than one CTA with
-// its full register set; PA_DF_CTAS_PER_SM=1 selects the latter.
+// The double-float variant runs two CTAs of 512 threads per SM (64
+// registers, no spills): measured faster than one CTA per SM with its full
+// register set (77.7 against 97.5 us per iteration on the 401 x 401
+// operator), the memory latency of the products needing the warps.
 static void* merged_fn(int loss, bool df) {
-  if (df) {
-    static const int per_sm = [] {
-      const char* e = getenv("PA_DF_CTAS_PER_SM");
-      return e && atoi(e) == 1 ? 1 : 2;
-    }();
-    return per_sm == 2 ? (void*)k_merged<PA_LOSS_LOGRATIO, true, 2>
-                       : (void*)k_merged<PA_LOSS_LOGRATIO, true, 1>;
-  }
+  if (df) return (void*)k_merged<PA_LOSS_LOGRATIO, true, 2>;
   return loss == PA_LOSS_QUADRATIC ? (void*)k_merged<PA_LOSS_QUADRATIC, false, kMinBlocksPerSM>
                                    : (void*)k_merged<PA_LOSS_LOGRATIO, false, kMinBlocksPerSM>;
 }

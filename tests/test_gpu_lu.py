@@ -47,17 +47,22 @@ CASES = {
 }
 
 
+# engine AUTO runs these small factors on one CTA (level steps, kernel 4);
+# engine GRID forces the grid kernel with per-row waits (kernel 5)
+@pytest.mark.parametrize("engine,kernel", [(pa.ENGINE_AUTO, 4), (pa.ENGINE_GRID, 5)],
+                         ids=["one_cta", "grid"])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_lu_route_iterates_match_oracle(name):
+def test_lu_route_iterates_match_oracle(name, engine, kernel):
     A = CASES[name]()
     Lf, Uf, p, q = lu_factors(A)
     T = 100
     x0 = oracle.start_vector(A.n_cols, 7)
     ro = oracle.projected_adam_lu(Lf, Uf, p, q, T, x0, n_trace=T, trace_L=True, **HYPER)
-    with pa.create(A) as h:
+    with pa.create(A, engine=engine) as h:
         h.attach_lu(Lf, Uf, p, q)
         rg = h.run(pa.SIGMA_MIN_LU, T, x0, trace_L=True, n_trace=T, **HYPER)
         xv = h.get_vector(pa.SIGMA_MIN_LU)
+        assert h.last_run_info()["kernel"] == kernel
     assert rg["status"] == ro.status == 0
     err_x = np.linalg.norm(rg["x_trace"] - ro.x_trace, axis=1)
     err_L = np.abs(rg["L_trace"] - ro.L_trace) / np.maximum(1.0, np.abs(ro.L_trace))
@@ -69,8 +74,9 @@ def test_lu_route_iterates_match_oracle(name):
     assert np.linalg.norm(rg["x_min"] - ro.x_min) <= 1e-10
 
 
+@pytest.mark.parametrize("engine", [pa.ENGINE_AUTO, pa.ENGINE_GRID], ids=["auto", "grid"])
 @pytest.mark.parametrize("name", ["hydro13", "hydro21"])
-def test_lu_route_kappa_matches_dense_inverse(name):
+def test_lu_route_kappa_matches_dense_inverse(name, engine):
     """kappa ~ 1e22: Algorithm 2's sigma_min against 1 / sigma_max of the
     dense LU inverse; sigma_max of Algorithm 1 against the dense SVD."""
     A = CASES[name]()
@@ -78,7 +84,7 @@ def test_lu_route_kappa_matches_dense_inverse(name):
     D = synth.csr_to_dense(A)
     smin_ref = 1.0 / np.linalg.svd(np.linalg.inv(D), compute_uv=False)[0]
     smax_ref = np.linalg.svd(D, compute_uv=False)[0]
-    with pa.create(A) as h:
+    with pa.create(A, engine=engine) as h:
         h.attach_lu(Lf, Uf, p, q)
         r = h.estimate(pa.BOTH_LU, 1000, seed=1, **HYPER)
     assert r["status"] == 0
@@ -181,3 +187,29 @@ def test_batched_lu_needs_factors_on_every_handle():
     finally:
         for h in hs:
             h.destroy()
+
+
+def test_lu_grid_route_100k_rows_matches_oracle():
+    """The 129 x 129 operator (99,846 rows; COLAMD factors with about 27M
+    non-zeros and 5,400 levels per system): the solve vector no longer fits
+    in one CTA's shared memory, so the grid kernel runs (per-row waits).
+    Iterates and L_t for t <= 10 and sigma after 10 iterations against the
+    oracle; the run is reproducible."""
+    A = synth.hydro_operator(129, seed=7)
+    Lf, Uf, p, q = lu_factors(A)
+    T = 10
+    x0 = oracle.start_vector(A.n_cols, 1)
+    ro = oracle.projected_adam_lu(Lf, Uf, p, q, T, x0, n_trace=T, trace_L=True, **HYPER)
+    with pa.create(A) as h:
+        h.attach_lu(Lf, Uf, p, q)
+        rg = h.run(pa.SIGMA_MIN_LU, T, x0, trace_L=True, n_trace=T, **HYPER)
+        assert h.last_run_info()["kernel"] == 5
+        rg2 = h.run(pa.SIGMA_MIN_LU, T, x0, **HYPER)
+    assert rg["status"] == ro.status == 0
+    err_x = np.linalg.norm(rg["x_trace"] - ro.x_trace, axis=1)
+    err_L = np.abs(rg["L_trace"] - ro.L_trace) / np.maximum(1.0, np.abs(ro.L_trace))
+    assert np.max(err_x) <= 1e-10, np.max(err_x)
+    assert np.max(err_L) <= 1e-10
+    assert rg["t_min"] == ro.t_min
+    assert abs(rg["sigma"] / ro.sigma_min - 1) <= 1e-12
+    assert np.array_equal(rg2["x_last"], rg["x_last"])
