@@ -907,6 +907,13 @@ def run_stress2001(args):
                                                               seed=START_SEED, **HYPER))
     out["mixed_k1_vector_iterations_per_s"] = (it[0] + it[1]) / (tmx + tmn)
     out["mixed_k32_vector_iterations_per_s"] = 32 * (it[0] + it[1]) / tbm
+    # PA_DF64 (double-float iteration held to the FP64 parity bars), k = 1
+    with pa.create(A, stream=stream, precision=pa.DF64) as hd:
+        hd.estimate(pa.SIGMA_MAX, 50, seed=START_SEED, **HYPER)
+        rd, td = _timed(stream, lambda: (hd.estimate(pa.SIGMA_MAX, it[0], seed=START_SEED, **HYPER),
+                                         hd.estimate(pa.SIGMA_MIN, it[1], seed=START_SEED, **HYPER)))
+        df_info = hd.last_run_info()
+    out["df64_k1_vector_iterations_per_s"] = (it[0] + it[1]) / td
     kappa = rf[0]["sigma_max"] / rf[1]["sigma_min"]
     est_k32 = 32 * (it[0] + it[1]) / tbm / full_T
     line = {
@@ -919,6 +926,9 @@ def run_stress2001(args):
                    "nnz": int(A.nnz), "iters_timed": list(it), "estimate_iters": list(EST_ITERS)},
         "fp64_k1_estimates_per_s": out["fp64_k1_vector_iterations_per_s"] / full_T,
         "fp64_k32_estimates_per_s": out["fp64_k32_vector_iterations_per_s"] / full_T,
+        "df64_k1_estimates_per_s": out["df64_k1_vector_iterations_per_s"] / full_T,
+        "df64_run_info": df_info,
+        "df64_short_run_sigmas": [rd[0]["sigma_max"], rd[1]["sigma_min"]],
         "throughput": out,
         "kappa_fp64_full_estimate": kappa,
         "sigma_fp64": [rf[0]["sigma_max"], rf[1]["sigma_min"]],
