@@ -284,11 +284,29 @@ pa_status pa_get_equilibration(pa_handle h, double* d_row, double* d_col);
  * nanoseconds of the GPU's global timer.  Host outputs. */
 pa_status pa_last_run_profile(pa_handle h, int* grid, double* busy_ns);
 
+/* Checkpoint/resume: continue the handle's latest single-vector run for
+ * `iters` more iterations of Algorithm 1, from the state that run left on the
+ * device (its last iterate x_T, Adam's moments m and v, the iteration count
+ * for the bias corrections, and the tracked minimum L_min with x_min).  The
+ * run being continued must be a successful PA_FP64 pa_estimate / pa_run of
+ * PA_SIGMA_MAX or PA_SIGMA_MIN on the three-phase grid or the cluster kernel,
+ * or an earlier pa_continue, with the same hyperparameters (else
+ * PA_ERR_INVALID_ARG).  A run of T1 iterations continued for T2 gives the
+ * same bits as one run of T1 + T2 (same partition: autotune 0 or finished):
+ * x_min, the returned sigma, x_last and L_min.  Host outputs, each may be
+ * NULL: sigma (||A x_min|| / ||x_min|| for the continued mode), x_last
+ * (n_cols float64, source order), info[4] = {L_min, t_min, L_last,
+ * iterations run in total}.  Also updates the sigma pa_estimate reports for
+ * that mode. */
+pa_status pa_continue(pa_handle h, int iters, double lr, double beta1, double beta2, double eps,
+                      double* sigma, double* x_last, double* info);
+
 /* Facts about the handle's latest single-vector run (pa_estimate, pa_run),
  * into out[4] (host):
  *   out[0] kernel: 0 the three-phase grid kernel, 1 the merged-phase grid
  *          kernel in FP64, 2 the merged-phase grid kernel in double-float
- *          (PA_DF64), 3 the cluster kernel; -1 before any run;
+ *          (PA_DF64), 3 the cluster kernel, 4 the LU route on one CTA, 5 the
+ *          LU route on the grid; -1 before any run;
  *   out[1] iterations of the merged-phase kernel that multiplied x itself
  *          instead of folding the update of x into the product (see the
  *          engine option);

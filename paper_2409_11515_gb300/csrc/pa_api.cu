@@ -2,6 +2,7 @@
 // validation, device memory, the start vector, launch orchestration of the
 // persistent Projected Adam kernel, and result read-back.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -18,6 +19,18 @@
 #include "pa_internal.h"
 
 using namespace pa;
+
+// NVTX range around each entry point (visible in Nsight timelines; free when
+// no tool is attached: the header-only NVTX loads its injection library only
+// when a profiler asks for it).
+namespace {
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace
 
 // ------------------------------------------------------------ errors --
 
@@ -149,6 +162,14 @@ struct pa_ctx {
   int df_fallbacks = 0;   // double-float runs redone in FP64 (range)
   int last_kernel = -1;   // kernel of the latest single-vector run (pa_last_run_info)
   int last_refreshes = 0;
+  // the state pa_continue resumes: the latest FP64 run of the three-phase or
+  // cluster kernel (x_T in X[cur], x_min in X[minb], m, v, the tracked minimum)
+  struct Cont {
+    bool valid = false;
+    int mode = 0, t_done = 0, t_min = 0, have_best = 0, cur = 0, minb = 0, G = 0;
+    bool cluster = false;
+    double best_s = 0, best_q = 0, lr = 0, b1 = 0, b2 = 0, eps = 0;
+  } cont;
 };
 
 static void* dev_alloc(pa_ctx* h, size_t bytes) {
@@ -307,6 +328,7 @@ static pa_status build_equilibration(pa_ctx* h, bool fp32_copies) {
 extern "C" pa_status pa_create(pa_handle* out, int32_t n_rows, int32_t n_cols, int64_t nnz,
                                const int32_t* row_ptr, const int32_t* col_idx, const double* vals,
                                int ptr_kind, const pa_options* opt, void* cuda_stream) {
+  NvtxRange nvtx_range("pa_create");
   g_err.clear();
   if (!out) return fail(PA_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
@@ -699,7 +721,7 @@ static pa_status status_error(const RunState* rs) {
 static pa_status fp64_run(pa_ctx* h, pa_mode mode, int iters, int t0, bool fresh_state, bool dd,
                           double b1, double b2, double eps, int G, int maxG, double* L_trace_dev,
                           double* x_trace_dev, int n_trace, RunState* out, bool cluster = false,
-                          int kernel = 0) {
+                          int kernel = 0, const pa_ctx::Cont* cont = nullptr) {
   // kernel: 0 = the three-phase k_persistent, 1 = the merged-phase kernel in
   // FP64, 2 = the merged-phase kernel in double-float
   const size_t n = (size_t)h->n_cols;
@@ -742,6 +764,14 @@ static pa_status fp64_run(pa_ctx* h, pa_mode mode, int iters, int t0, bool fresh
   p.skip_arrival = h->opt.debug_skip_arrival;
   p.u = h->dx;
   p.s_scale = 1.0;
+  if (cont) {  // continue a run: x_T in X0, x_min in X1, m and v as left
+    p.init_have_best = cont->have_best;
+    p.init_best_s = cont->best_s;
+    p.init_best_q = cont->best_q;
+    p.init_t_min = cont->t_min;
+    p.init_minb = 1;
+    p.t_min_base = cont->t_done;
+  }
   if (kernel == 2) {
     p.a_val2 = h->a_val2; p.t_val2 = h->t_val2;
     p.XD0 = h->XD0; p.XD1 = h->XD1; p.XD2 = h->XD2;
@@ -916,6 +946,7 @@ static pa_status run_one(pa_ctx* h, pa_mode mode, int iters, double lr, double b
   pa_status st;
   if ((st = ensure_partitions(h, G)) || (st = ensure_bias(h, iters, lr, b1, b2, eps))) return st;
   if (mixed && mode == PA_SIGMA_MAX) {
+    h->cont.valid = false;
     if ((st = mixed_max_run(h, iters, b1, b2, eps, G, maxG, L_trace_dev, out)) < 0) return st;
   } else {
     const bool tuning = !cluster && !mixed && h->opt.autotune > 0 &&
@@ -948,7 +979,23 @@ static pa_status run_one(pa_ctx* h, pa_mode mode, int iters, double lr, double b
     e = launch_unpermute(h->n_cols, 1, h->sq.pos, pick64h(h, out->minb), keep, h->stream,
                          &h->launches);
     if (e != cudaSuccess) return cuda_fail(e, "keeping x_min");
+    h->cont.valid = false;
     if ((st = status_error(out))) return st;
+    if (kernel == 0 && !mixed && out->status == PA_OK) {
+      pa_ctx::Cont& c = h->cont;
+      c.valid = true;
+      c.mode = mode;
+      c.t_done = out->iters_run;
+      c.t_min = out->t_min;
+      c.have_best = out->have_best;
+      c.best_s = out->best_s;
+      c.best_q = out->best_q;
+      c.cur = out->cur;
+      c.minb = out->minb;
+      c.G = G;
+      c.cluster = cluster;
+      c.lr = lr; c.b1 = b1; c.b2 = b2; c.eps = eps;
+    }
   }
   if (mode == PA_SIGMA_MAX) { h->sigma_max = out->sigma; h->have_max = true; }
   else { h->sigma_min = out->sigma; h->have_min = true; h->have_min_direct = true; }
@@ -1036,6 +1083,7 @@ extern "C" pa_status pa_attach_lu(pa_handle h, const int32_t* l_row_ptr, const i
                                   const double* l_val, const int32_t* u_row_ptr,
                                   const int32_t* u_col, const double* u_val, const int32_t* p,
                                   const int32_t* q, int ptr_kind) {
+  NvtxRange nvtx_range("pa_attach_lu");
   g_err.clear();
   if (!h || !l_row_ptr || !u_row_ptr) return fail(PA_ERR_INVALID_ARG, "NULL handle or row_ptr");
   if (h->n_rows != h->n_cols)
@@ -1116,6 +1164,7 @@ static pa_status lu_run(pa_ctx* h, const double* x0, int iters, double lr, doubl
                         double eps, double* L_trace_dev, double* x_trace_dev, int n_trace,
                         RunState* out) {
   if (!h->have_lu) return fail(PA_ERR_INVALID_ARG, "no LU factors attached (pa_attach_lu)");
+  h->cont.valid = false;  // the LU route reuses the iterate and moment buffers
   pa_status st;
   if ((st = ensure_bias(h, iters, lr, b1, b2, eps))) return st;
   const size_t n = (size_t)h->n_cols;
@@ -1252,6 +1301,7 @@ extern "C" pa_status pa_run(pa_handle h, pa_mode mode, int iters, double lr, dou
                             double beta2, double eps, const double* x_init, int x_kind,
                             double* x_min, double* x_last, double* info, double* L_trace,
                             double* x_trace, int n_trace, double* sigma) {
+  NvtxRange nvtx_range("pa_run");
   g_err.clear();
   if (!h) return fail(PA_ERR_INVALID_ARG, "NULL handle");
   if (mode != PA_SIGMA_MAX && mode != PA_SIGMA_MIN && mode != PA_SIGMA_MIN_LU)
@@ -1321,9 +1371,77 @@ extern "C" pa_status pa_run(pa_handle h, pa_mode mode, int iters, double lr, dou
   return rst;
 }
 
+extern "C" pa_status pa_continue(pa_handle h, int iters, double lr, double beta1, double beta2,
+                                 double eps, double* sigma, double* x_last, double* info) {
+  NvtxRange nvtx_range("pa_continue");
+  g_err.clear();
+  if (!h) return fail(PA_ERR_INVALID_ARG, "NULL handle");
+  pa_ctx::Cont& c = h->cont;
+  if (!c.valid)
+    return fail(PA_ERR_INVALID_ARG,
+                "nothing to continue: the handle's latest run was not a successful FP64 run "
+                "of the three-phase or cluster kernel");
+  if (lr != c.lr || beta1 != c.b1 || beta2 != c.b2 || eps != c.eps)
+    return fail(PA_ERR_INVALID_ARG, "pa_continue needs the hyperparameters of the run it continues");
+  pa_status st;
+  if ((st = check_hyper(iters, lr, beta1, beta2, eps))) return st;
+  if ((long long)c.t_done + iters > INT_MAX) return fail(PA_ERR_INVALID_ARG, "too many iterations");
+  if ((st = ensure_bias(h, c.t_done + iters, lr, beta1, beta2, eps))) return st;
+  // x_T to X0, x_min to X1 (through the step buffer, so that no copy
+  // overwrites the other's source)
+  const size_t n = (size_t)h->n_cols;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(h->dx, pick64h(h, c.cur), sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream)) ||
+      (c.minb != 1 &&
+       (e = cudaMemcpyAsync(h->X1, pick64h(h, c.minb), sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream))) ||
+      (e = cudaMemcpyAsync(h->X0, h->dx, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream)))
+    return cuda_fail(e, "preparing the continued run");
+  const int maxG = c.G;
+  RunState rs{};
+  const pa_ctx::Cont prev = c;
+  c.valid = false;
+  if ((st = fp64_run(h, (pa_mode)prev.mode, iters, prev.t_done, false, false, beta1, beta2, eps,
+                     prev.G, maxG, nullptr, nullptr, 0, &rs, prev.cluster, 0, &prev)))
+    return st;
+  double* keep = prev.mode == PA_SIGMA_MAX ? h->xmin_max : h->xmin_min;
+  if ((e = launch_unpermute(h->n_cols, 1, h->sq.pos, pick64h(h, rs.minb), keep, h->stream,
+                            &h->launches)))
+    return cuda_fail(e, "keeping x_min");
+  if ((st = status_error(&rs))) return st;
+  if (rs.status == PA_OK) {
+    c = prev;
+    c.valid = true;
+    c.t_done = prev.t_done + rs.iters_run;
+    c.t_min = rs.t_min;
+    c.have_best = rs.have_best;
+    c.best_s = rs.best_s;
+    c.best_q = rs.best_q;
+    c.cur = rs.cur;
+    c.minb = rs.minb;
+  }
+  if (prev.mode == PA_SIGMA_MAX) { h->sigma_max = rs.sigma; h->have_max = true; }
+  else { h->sigma_min = rs.sigma; h->have_min = true; h->have_min_direct = true; }
+  if (x_last) {
+    if ((e = launch_unpermute(h->n_cols, 1, h->sq.pos, pick64h(h, rs.cur), h->dx, h->stream,
+                              &h->launches)) ||
+        (e = cudaMemcpyAsync(x_last, h->dx, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream)))
+      return cuda_fail(e, "reading x_last");
+  }
+  if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(e, "reading results");
+  if (sigma) *sigma = rs.sigma;
+  if (info) {
+    info[0] = rs.L_min;
+    info[1] = rs.t_min;
+    info[2] = rs.L_last;
+    info[3] = prev.t_done + rs.iters_run;
+  }
+  return (pa_status)rs.status;
+}
+
 extern "C" pa_status pa_estimate(pa_handle h, pa_mode mode, int iters, double lr, double beta1,
                                  double beta2, double eps, uint64_t seed, double* sigma_max,
                                  double* sigma_min, double* kappa) {
+  NvtxRange nvtx_range("pa_estimate");
   g_err.clear();
   if (!h) return fail(PA_ERR_INVALID_ARG, "NULL handle");
   if (mode != PA_SIGMA_MAX && mode != PA_SIGMA_MIN && mode != PA_BOTH &&
@@ -1416,10 +1534,12 @@ static pa_status product(pa_handle h, bool transposed, const double* in, double*
 }
 
 extern "C" pa_status pa_spmv(pa_handle h, const double* x, double* y, int ptr_kind) {
+  NvtxRange nvtx_range("pa_spmv");
   return product(h, false, x, y, ptr_kind);
 }
 
 extern "C" pa_status pa_spmv_t(pa_handle h, const double* y, double* z, int ptr_kind) {
+  NvtxRange nvtx_range("pa_spmv_t");
   return product(h, true, y, z, ptr_kind);
 }
 
@@ -1466,6 +1586,7 @@ extern "C" pa_status pa_last_run_profile(pa_handle h, int* grid, double* busy_ns
 extern "C" pa_status pa_error_bounds(pa_handle h, const double* x_hat, const double* b,
                                      int ptr_kind, double kappa, double norm_a, double u,
                                      double* out) {
+  NvtxRange nvtx_range("pa_error_bounds");
   g_err.clear();
   if (!h || !x_hat || !b || !out) return fail(PA_ERR_INVALID_ARG, "NULL handle or pointer");
   if (ptr_kind != PA_HOST && ptr_kind != PA_DEVICE)
@@ -1988,6 +2109,7 @@ extern "C" pa_status pa_estimate_batched(int n_mat, const pa_handle* handles, pa
                                          int k_restarts, const int* iters, double lr, double beta1,
                                          double beta2, double eps, uint64_t seed, double* out,
                                          pa_status* item_status) {
+  NvtxRange nvtx_range("pa_estimate_batched");
   g_err.clear();
   if (n_mat <= 0 || !handles || !iters || !out || k_restarts <= 0)
     return fail(PA_ERR_INVALID_ARG, "invalid batched arguments");

@@ -30,7 +30,8 @@ struct RunState {
   unsigned int abort;    // set by the first CTA that gives up
   double sigma;        // ||A x_min|| / ||x_min||, written by the sigma kernel
   int refreshes;       // merged-phase kernel: iterations that multiplied x itself
-  int pad;
+  int have_best;       // three-phase kernel: the tracked minimum at the end of
+  double best_s, best_q;  // the run (for a continued run): ||y||^2, ||x||^2
 };
 
 // A row- and column-permuted copy P A Q^T of a matrix in sliced ELL form:
@@ -80,6 +81,11 @@ struct IterParams {
   double w2;      // (1 - beta2) / (1 - beta1)^2
   long long timeout_ns;
   int skip_arrival;
+  // ---- continued runs of k_persistent (pa_continue): the tracked state of
+  // the run being continued; all zero for a fresh run ----
+  int init_have_best, init_t_min, init_minb;
+  double init_best_s, init_best_q;
+  int t_min_base;                      // iteration numbers of this run start after it
   // ---- the merged-phase kernel (k_merged) ----
   double* u;                           // u_t = x_{t-1} - dx_t (FP64 variant)
   // double-float variant (PA_DF64): values of 2^-k P A Q^T and of its

@@ -97,11 +97,13 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
   if (tid == 0) {
     sh.cur = 0;
     sh.brk = 0;
-    sh.minb = 0;
-    sh.t_min = 0;
+    sh.minb = p.init_minb;   // a continued run starts with the tracked state
+    sh.t_min = p.init_t_min; // of the run it continues (zeros for a fresh run)
     sh.iters_run = 0;
     sh.status = PA_OK;
-    sh.have_best = 0;
+    sh.have_best = p.init_have_best;
+    sh.best_s = p.init_best_s;
+    sh.best_q = p.init_best_q;
     sh.have_last = 0;
     sh.busy_a = sh.busy_b = 0;
     sh.lat_a = 0;
@@ -195,7 +197,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
               sh.best_s = s_;
               sh.best_q = q;
               sh.have_best = 1;
-              sh.t_min = t - 1;
+              sh.t_min = p.t_min_base + t - 1;
               sh.minb = cur;
             }
             sh.last_s = s_;
@@ -335,6 +337,9 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
     st->L_min = sh.have_best ? loss_value(p.mode, LOSS, sh.best_s, sh.best_q) : INFINITY;
     st->L_last = sh.have_last ? loss_value(p.mode, LOSS, sh.last_s, sh.last_q) : NAN;
     st->iters_run = sh.iters_run;
+    st->best_s = sh.best_s;
+    st->best_q = sh.best_q;
+    st->have_best = sh.have_best;
   }
 }
 

@@ -38,7 +38,7 @@ STATUS_NAMES = {0: "PA_OK", 1: "PA_WARN_SINGULAR", -1: "PA_ERR_INVALID_ARG",
 EXPORTS = ("pa_options_default", "pa_create", "pa_estimate", "pa_run", "pa_estimate_batched",
            "pa_get_vector", "pa_spmv", "pa_spmv_t", "pa_get_transpose", "pa_get_equilibration",
            "pa_kernel_launches", "pa_destroy", "pa_last_error", "pa_set_allocator",
-           "pa_last_run_profile", "pa_last_run_info", "pa_sigma_noalloc", "pa_last_batch_graph", "pa_error_bounds", "pa_attach_lu")
+           "pa_last_run_profile", "pa_last_run_info", "pa_continue", "pa_sigma_noalloc", "pa_last_batch_graph", "pa_error_bounds", "pa_attach_lu")
 
 ERROR_BOUND_KEYS = ("residual_norm", "b_norm", "x_hat_norm", "thm1_lower", "thm1_upper",
                     "thm2_lower", "thm2_upper", "thm3_upper", "thm4_rounding", "singular")
@@ -113,6 +113,8 @@ def _declare(L):
     L.pa_attach_lu.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, C.c_int]
     L.pa_error_bounds.restype = C.c_int
     L.pa_error_bounds.argtypes = [vp, vp, vp, C.c_int, d, d, d, vp]
+    L.pa_continue.restype = C.c_int
+    L.pa_continue.argtypes = [vp, C.c_int, d, d, d, d, vp, vp, vp]
     L.pa_last_run_info.restype = C.c_int
     L.pa_last_run_info.argtypes = [vp, vp]
     L.pa_last_run_profile.restype = C.c_int
@@ -297,6 +299,17 @@ class Handle:
         t = np.zeros((max(g.value, 1), 2))
         _check(load().pa_last_run_profile(self._h, C.byref(g), t.ctypes.data))
         return g.value, t[:g.value]
+
+    def continue_run(self, iters, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-12):
+        """pa_continue: the latest FP64 run continued for `iters` iterations;
+        {status, sigma, x_last, L_min, t_min, L_last, iters_total}."""
+        sig = C.c_double()
+        x_last = np.empty(self.n_cols)
+        info = np.empty(4)
+        st = _check(load().pa_continue(self._h, int(iters), lr, beta1, beta2, eps, C.byref(sig),
+                                       x_last.ctypes.data, info.ctypes.data))
+        return {"status": st, "sigma": sig.value, "x_last": x_last, "L_min": info[0],
+                "t_min": int(info[1]), "L_last": info[2], "iters_total": int(info[3])}
 
     def last_run_info(self):
         """pa_last_run_info: {kernel, refreshes, df_fallbacks, grid} of the
