@@ -127,6 +127,10 @@ struct pa_ctx {
   RunState* st = nullptr;
   int G = 0;
   int32_t *part_a = nullptr, *part_t = nullptr, *dep = nullptr;
+  // each CTA's slices dealt to its warps by cost, longest first to the least
+  // loaded warp: warp w of CTA b takes list[woff[b (NW+1) + w] .. woff[.. + 1])
+  int32_t *a_list = nullptr, *a_woff = nullptr, *t_list = nullptr, *t_woff = nullptr;
+  std::vector<int32_t> wpa_h, wpt_h;  // host copies of the slice pointers
   unsigned* ready = nullptr;
   unsigned long long* cta_ns = nullptr;  // [2G] per-CTA busy time of the last run
   unsigned long long* cta_lat = nullptr; // [G] per-CTA phase-A completion latency
@@ -538,6 +542,90 @@ static int choose_grid(pa_ctx* h, int* maxG_out) {
   return (int)std::min<int64_t>(want, maxG);
 }
 
+// Deal each CTA's slices [part[b], part[b+1]) to its NW warps: slices by
+// decreasing cost 32 (width + row_weight), each to the warp with the least
+// cost so far (ties: the lower warp); every warp then takes its slices in
+// increasing order.  Deterministic, so the per-thread partial sums keep a
+// fixed order.  Round-robin dealing left the slowest warp of a CTA with
+// 1.2-1.3x the mean work on the hydro operators (rows of 1, 3, 6 and 11
+// entries sorted within windows).
+static void deal_slices(const std::vector<int32_t>& part, const std::vector<int32_t>& wp,
+                        int row_weight, int NW, std::vector<int32_t>* list,
+                        std::vector<int32_t>* woff) {
+  const int G = (int)part.size() - 1;
+  list->assign((size_t)part[G], 0);
+  woff->assign((size_t)G * (NW + 1), 0);
+  std::vector<int32_t> idx;
+  std::vector<std::vector<int32_t>> per(NW);
+  std::vector<long long> load(NW);
+  for (int b = 0; b < G; ++b) {
+    idx.clear();
+    for (int32_t sl = part[b]; sl < part[b + 1]; ++sl) idx.push_back(sl);
+    std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) {
+      return wp[x + 1] - wp[x] > wp[y + 1] - wp[y];
+    });
+    for (int w = 0; w < NW; ++w) {
+      per[w].clear();
+      load[w] = 0;
+    }
+    for (int32_t sl : idx) {
+      int best = 0;
+      for (int w = 1; w < NW; ++w)
+        if (load[w] < load[best]) best = w;
+      per[best].push_back(sl);
+      load[best] += 32ll * (wp[sl + 1] - wp[sl] + row_weight);
+    }
+    int32_t pos = part[b];
+    for (int w = 0; w < NW; ++w) {
+      std::sort(per[w].begin(), per[w].end());
+      (*woff)[(size_t)b * (NW + 1) + w] = pos;
+      for (int32_t sl : per[w]) (*list)[pos++] = sl;
+    }
+    (*woff)[(size_t)b * (NW + 1) + NW] = pos;
+  }
+}
+
+// The warp slice lists of the current partitions (after ensure_partitions
+// or a tuner round).
+static pa_status build_warp_lists(pa_ctx* h) {
+  const int G = h->G, NW = kBlock / 32;
+  cudaError_t e;
+  if (h->wpa_h.empty()) {
+    h->wpa_h.resize((size_t)h->sa.n_slices + 1);
+    h->wpt_h.resize((size_t)h->sq.n_slices + 1);
+    if ((e = cudaMemcpyAsync(h->wpa_h.data(), h->sa.wp, sizeof(int32_t) * h->wpa_h.size(), cudaMemcpyDeviceToHost, h->stream)) ||
+        (e = cudaMemcpyAsync(h->wpt_h.data(), h->sq.wp, sizeof(int32_t) * h->wpt_h.size(), cudaMemcpyDeviceToHost, h->stream)))
+      return cuda_fail(e, "reading the slice pointers");
+  }
+  std::vector<int32_t> pa_((size_t)G + 1), pt_((size_t)G + 1);
+  if ((e = cudaMemcpyAsync(pa_.data(), h->part_a, sizeof(int32_t) * pa_.size(), cudaMemcpyDeviceToHost, h->stream)) ||
+      (e = cudaMemcpyAsync(pt_.data(), h->part_t, sizeof(int32_t) * pt_.size(), cudaMemcpyDeviceToHost, h->stream)) ||
+      (e = cudaStreamSynchronize(h->stream)))
+    return cuda_fail(e, "reading the partitions");
+  std::vector<int32_t> la, wa, lt, wt;
+  deal_slices(pa_, h->wpa_h, 2, NW, &la, &wa);
+  deal_slices(pt_, h->wpt_h, 30, NW, &lt, &wt);
+  pa_status st;
+  if (!h->a_list) {
+    if ((st = alloc_n(h, &h->a_list, std::max<size_t>(la.size(), 1), "warp slice lists")) ||
+        (st = alloc_n(h, &h->t_list, std::max<size_t>(lt.size(), 1), "warp slice lists")))
+      return st;
+  }
+  if (h->a_woff) dev_free(h, h->a_woff);
+  if (h->t_woff) dev_free(h, h->t_woff);
+  h->a_woff = h->t_woff = nullptr;
+  if ((st = alloc_n(h, &h->a_woff, wa.size(), "warp slice lists")) ||
+      (st = alloc_n(h, &h->t_woff, wt.size(), "warp slice lists")))
+    return st;
+  if ((!la.empty() && (e = cudaMemcpyAsync(h->a_list, la.data(), sizeof(int32_t) * la.size(), cudaMemcpyHostToDevice, h->stream))) ||
+      (!lt.empty() && (e = cudaMemcpyAsync(h->t_list, lt.data(), sizeof(int32_t) * lt.size(), cudaMemcpyHostToDevice, h->stream))) ||
+      (e = cudaMemcpyAsync(h->a_woff, wa.data(), sizeof(int32_t) * wa.size(), cudaMemcpyHostToDevice, h->stream)) ||
+      (e = cudaMemcpyAsync(h->t_woff, wt.data(), sizeof(int32_t) * wt.size(), cudaMemcpyHostToDevice, h->stream)) ||
+      (e = cudaStreamSynchronize(h->stream)))  // the host vectors are pageable
+    return cuda_fail(e, "uploading the warp slice lists");
+  return PA_OK;
+}
+
 static pa_status ensure_partitions(pa_ctx* h, int G) {
   if (h->G == G && h->part_a) return PA_OK;
   if (h->part_a) dev_free(h, h->part_a);
@@ -573,7 +661,7 @@ static pa_status ensure_partitions(pa_ctx* h, int G) {
   h->G = G;
   h->tuned_rounds = 0;
   h->tune_best = INFINITY;
-  return PA_OK;
+  return build_warp_lists(h);
 }
 
 // Re-split one partition at equal measured cost.  CTA b spent busy[b] on
@@ -654,7 +742,7 @@ static pa_status tune_partitions(pa_ctx* h, double t_iter) {
                                h->stream, &h->launches)) ||
       (e = cudaStreamSynchronize(h->stream)))
     return cuda_fail(e, "applying the tuned partition");
-  return PA_OK;
+  return build_warp_lists(h);
 }
 
 // Per-iteration Adam scalars: the step lr m_hat / (sqrt(v_hat) + eps) with
@@ -740,6 +828,7 @@ static pa_status fp64_run(pa_ctx* h, pa_mode mode, int iters, int t0, bool fresh
   p.a_wp = h->sa.wp; p.a_col = h->sa.col; p.a_val = h->sa.val;
   p.t_wp = h->sq.wp; p.t_col = h->sq.col; p.t_val = h->sq.val;
   p.part_a = h->part_a; p.part_t = h->part_t;
+  p.a_list = h->a_list; p.a_woff = h->a_woff; p.t_list = h->t_list; p.t_woff = h->t_woff;
   p.X0 = h->X0; p.X1 = h->X1; p.X2 = h->X2;
   p.m = h->m; p.v = h->v; p.y = h->y; p.ylo = h->ylo; p.dx = h->dx;
   p.partials = h->partials;

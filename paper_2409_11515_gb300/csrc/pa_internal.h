@@ -57,6 +57,10 @@ struct IterParams {
   const int32_t* t_wp; const int32_t* t_col; const double* t_val;  // Q A^T P^T
   const int32_t* part_a;   // [G+1] slice ranges of P A Q^T per CTA
   const int32_t* part_t;   // [G+1] slice ranges of Q A^T P^T per CTA (own x rows)
+  // each CTA's slices dealt to its kBlock/32 warps: warp w of CTA b takes
+  // a_list[a_woff[b (NW+1) + w] .. a_woff[b (NW+1) + w + 1]) (t_*: A^T)
+  const int32_t* a_list; const int32_t* a_woff;
+  const int32_t* t_list; const int32_t* t_woff;
   double* X0; double* X1; double* X2;  // three iterate buffers
   double* m; double* v;                // Adam moments
   double* y; double* ylo;              // y = A x (ylo: low part, compensated mode)

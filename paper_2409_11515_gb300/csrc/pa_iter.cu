@@ -9,7 +9,9 @@
 //
 // One launch runs every iteration without returning to the host.  CTA b owns
 // a contiguous range of slices of P A Q^T (phase A) and of Q A^T P^T (phases
-// B and C); the ranges are balanced by padded entries plus a per-row weight.
+// B and C); the ranges are balanced by padded entries plus a per-row weight,
+// and inside a CTA the host deals the slices to the warps by the same cost
+// (longest first to the least loaded warp).
 // Per iteration t:
 //
 //   A  y = A x_{t-1} (own rows); partials s = sum y_i^2, q = ||x||^2 | grid barrier
@@ -111,7 +113,9 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
   }
 
   const int dlo = p.dep[2 * b], dhi = p.dep[2 * b + 1];
-
+  // every thread reads sh.cur at t = 1: shared memory starts with whatever
+  // the SM's previous launch left there
+  __syncthreads();
 
   // per-thread partial of ||x||^2 over the own rows, carried into phase A
   double qloc = 0.0;
@@ -134,8 +138,10 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
     // ---- phase A: y = A x, partials ||y||^2 and ||x||^2
     {
       double v[2] = {0.0, qloc};
-      for (int s = sa0 + warp; s < sa1; s += NW) {
-        if (s + NW < sa1) prefetch_slice_l2(p.a_wp, p.a_col, p.a_val, s + NW, lane);
+      const int k0 = p.a_woff[b * (NW + 1) + warp], k1 = p.a_woff[b * (NW + 1) + warp + 1];
+      for (int k = k0; k < k1; ++k) {  // this warp's share of the CTA's slices
+        const int s = __ldg(p.a_list + k);
+        if (k + 1 < k1) prefetch_slice_l2(p.a_wp, p.a_col, p.a_val, __ldg(p.a_list + k + 1), lane);
         const int r = 32 * s + lane;
         double yr;
         if (DD) {
@@ -243,8 +249,10 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
       const double b1 = p.beta1, b2 = p.beta2;
       const double w2 = p.w2;  // (1 - beta2) g^2 = w2 g'^2 with g' = (1 - beta1) g
       double v[2] = {0.0, 0.0};
-      for (int s = st0 + warp; s < st1; s += NW) {
-        if (!DD && s + NW < st1) prefetch_slice_l2(p.t_wp, p.t_col, p.t_val, s + NW, lane);
+      const int k0 = p.t_woff[b * (NW + 1) + warp], k1 = p.t_woff[b * (NW + 1) + warp + 1];
+      for (int k = k0; k < k1; ++k) {
+        const int s = __ldg(p.t_list + k);
+        if (!DD && k + 1 < k1) prefetch_slice_l2(p.t_wp, p.t_col, p.t_val, __ldg(p.t_list + k + 1), lane);
         const double z = DD ? slice_dot_dd2(p.t_wp, p.t_col, p.t_val, s, lane, p.y, p.ylo)
                             : slice_dot(p.t_wp, p.t_col, p.t_val, s, lane, p.y);
         const int j = 32 * s + lane;

@@ -226,12 +226,16 @@ __global__ void __launch_bounds__(kBlock, MINB) k_merged(const IterParams p) {
     }
     if (tid == 0) sh.tmark = globaltimer_ns();
     const int cur = sh.cur;  // x_{t-2} (t > 1) or x_0
-    // products of the loop below: slice sl of P A Q^T times u_{t-1} (from < 0)
-    // or times iterate buffer `from`
-    auto product = [&](int sl, int from) -> W {
-      if (sl + NW < sa1) {
-        if (DF) prefetch_slice_l2(p.a_wp, p.a_col, p.a_val2, sl + NW, lane);
-        else prefetch_slice_l2(p.a_wp, p.a_col, p.a_val, sl + NW, lane);
+    // products of the loops below: the slice at entry k of this warp's list
+    // times u_{t-1} (from < 0) or times iterate buffer `from`;
+    // this warp's share of the CTA's slices of P A Q^T: a_list[ka0 .. ka1)
+    const int ka0 = p.a_woff[b * (NW + 1) + warp], ka1 = p.a_woff[b * (NW + 1) + warp + 1];
+    auto product = [&](int k, int from) -> W {
+      const int sl = __ldg(p.a_list + k);
+      if (k + 1 < ka1) {
+        const int nx = __ldg(p.a_list + k + 1);
+        if (DF) prefetch_slice_l2(p.a_wp, p.a_col, p.a_val2, nx, lane);
+        else prefetch_slice_l2(p.a_wp, p.a_col, p.a_val, nx, lane);
       }
       if constexpr (DF)
         return slice_dot_df(p.a_wp, p.a_col, p.a_val2, sl, lane, from < 0 ? p.ud : X32(from));
@@ -245,7 +249,10 @@ __global__ void __launch_bounds__(kBlock, MINB) k_merged(const IterParams p) {
     const bool spec = t > 1 && !sh.prev_refresh;
     const int swin = spec ? min(sa1, sa0 + p.win_slices) : sa0;
     if (spec)
-      for (int sl = sa0 + warp; sl < swin; sl += NW) wbuf[32 * (sl - sa0) + lane] = product(sl, -1);
+      for (int k = ka0; k < ka1; ++k) {
+        const int sl = __ldg(p.a_list + k);
+        if (sl < swin) wbuf[32 * (sl - sa0) + lane] = product(k, -1);
+      }
     if (t > 1) {  // what the row passes below read: y_{t-2}, x_{t-2} and u_{t-1} rows
       const int ra = 32 * sa0, rb = min(32 * sa1, p.n_rows);
       if (rb > ra) prefetch_range_l2(DF ? (const void*)(p.yd + ra) : (const void*)(p.y + ra),
@@ -339,11 +346,12 @@ __global__ void __launch_bounds__(kBlock, MINB) k_merged(const IterParams p) {
         }
       };
       // slice sl's row of this lane, multiplied now (y_{t-2} loaded first)
-      auto multiply_finish = [&](int sl, int from, bool direct) {
-        const int r = 32 * sl + lane;
+      // entry k of this warp's list, multiplied now (y_{t-2} loaded first)
+      auto multiply_finish = [&](int k, int from, bool direct) {
+        const int r = 32 * __ldg(p.a_list + k) + lane;
         S yo{};
         if (!direct && r < p.n_rows) yo = ybuf[r];
-        const W wv = product(sl, from);
+        const W wv = product(k, from);
         if (r < p.n_rows) finish_row(r, wv, yo, direct);
       };
       // own x rows: x_{t-1} (written into buffer xb for t > 1) and ||x||^2
@@ -399,7 +407,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_merged(const IterParams p) {
           status = PA_ERR_TIMEOUT;
           break;
         }
-        for (int sl = sa0 + warp; sl < sa1; sl += NW) multiply_finish(sl, xb, true);
+        for (int k = ka0; k < ka1; ++k) multiply_finish(k, xb, true);
       } else {
         // the speculative rows from shared memory (all threads, coalesced),
         // then the remaining slices multiplied and finished at once
@@ -415,8 +423,8 @@ __global__ void __launch_bounds__(kBlock, MINB) k_merged(const IterParams p) {
             if (i0 + k * kBlock < rw)
               finish_row(rbase + i0 + k * kBlock, wbuf[i0 + k * kBlock], yo[k], false);
         }
-        for (int sl = swin + warp; sl < sa1; sl += NW)
-          multiply_finish(sl, t == 1 ? cur : -1, t == 1);
+        for (int k = ka0; k < ka1; ++k)
+          if (__ldg(p.a_list + k) >= swin) multiply_finish(k, t == 1 ? cur : -1, t == 1);
         finish_x();
       }
       if (DF) {
@@ -529,8 +537,10 @@ __global__ void __launch_bounds__(kBlock, MINB) k_merged(const IterParams p) {
         const df K1{bq.x, bq.y}, K2{bq.z, bq.w};
         DfAcc a1, a2;
         const float2* xs = X32(xc);
-        for (int sl = st0 + warp; sl < st1; sl += NW) {
-          if (sl + NW < st1) prefetch_slice_l2(p.t_wp, p.t_col, p.t_val2, sl + NW, lane);
+        const int kt0 = p.t_woff[b * (NW + 1) + warp], kt1 = p.t_woff[b * (NW + 1) + warp + 1];
+        for (int k = kt0; k < kt1; ++k) {
+          const int sl = __ldg(p.t_list + k);
+          if (k + 1 < kt1) prefetch_slice_l2(p.t_wp, p.t_col, p.t_val2, __ldg(p.t_list + k + 1), lane);
           const int j = 32 * sl + lane;
           const df z = slice_dot_df(p.t_wp, p.t_col, p.t_val2, sl, lane, p.yd);
           if (j < n) {
@@ -554,8 +564,10 @@ __global__ void __launch_bounds__(kBlock, MINB) k_merged(const IterParams p) {
         const double2 bc = p.bias[p.t0 + t - 1];
         const double b1 = p.beta1, b2 = p.beta2, w2 = p.w2;
         const double* xs = X64(xc);
-        for (int sl = st0 + warp; sl < st1; sl += NW) {
-          if (sl + NW < st1) prefetch_slice_l2(p.t_wp, p.t_col, p.t_val, sl + NW, lane);
+        const int kt0 = p.t_woff[b * (NW + 1) + warp], kt1 = p.t_woff[b * (NW + 1) + warp + 1];
+        for (int k = kt0; k < kt1; ++k) {
+          const int sl = __ldg(p.t_list + k);
+          if (k + 1 < kt1) prefetch_slice_l2(p.t_wp, p.t_col, p.t_val, __ldg(p.t_list + k + 1), lane);
           const int j = 32 * sl + lane;
           const double z = slice_dot(p.t_wp, p.t_col, p.t_val, sl, lane, p.y);
           if (j < n) {

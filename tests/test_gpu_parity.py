@@ -338,6 +338,24 @@ def test_deterministic_and_device_pointers():
         assert h.launches() > 0
 
 
+@pytest.mark.parametrize("engine", ["auto", "cluster", "grid"])
+def test_repeated_runs_bit_identical(engine):
+    """Ten runs on one handle, each after the previous launch has left its
+    own shared-memory state on the SMs: every run equals the first bit for
+    bit and the oracle within the iterate bar."""
+    A = synth.hydro_operator(31, seed=4)
+    x0 = oracle.start_vector(A.n_cols, 1)
+    ro = oracle.projected_adam(A, pa.SIGMA_MAX, 200, x_init=x0, lr=1e-2, beta1=0.9,
+                               beta2=0.999, eps=1e-12)
+    kw = {"auto": {}, "cluster": dict(engine=pa.ENGINE_CLUSTER),
+          "grid": dict(engine=pa.ENGINE_GRID, grid_blocks=16, autotune=0)}[engine]
+    with pa.create(A, **kw) as h:
+        runs = [h.run(pa.SIGMA_MAX, 200, x0)["x_last"] for _ in range(10)]
+    for k, x in enumerate(runs[1:], 1):
+        assert np.array_equal(x, runs[0]), f"run {k} differs from run 0"
+    assert np.linalg.norm(runs[0] - ro.x_last) < 1e-12
+
+
 def test_torch_allocator_hook():
     pytest.importorskip("torch")
     pa.use_torch_allocator()
