@@ -64,7 +64,8 @@ enum { PA_HOST = 0, PA_DEVICE = 1 };                   /* pointer kinds        *
 enum { PA_LOSS_LOGRATIO = 0, PA_LOSS_QUADRATIC = 1 };  /* loss forms           */
 enum { PA_FP64 = 0, PA_MIXED = 1, PA_DF64 = 2 };       /* precision modes      */
 enum { PA_EQ_NONE = 0, PA_EQ_STORAGE = 1, PA_EQ_TARGET = 2 }; /* equilibration */
-enum { PA_ENGINE_AUTO = 0, PA_ENGINE_GRID = 1, PA_ENGINE_CLUSTER = 2, PA_ENGINE_MERGED = 3 };
+enum { PA_ENGINE_AUTO = 0, PA_ENGINE_GRID = 1, PA_ENGINE_CLUSTER = 2, PA_ENGINE_MERGED = 3,
+       PA_ENGINE_SINGLE = 4 };
 enum { PA_ABLATE_NO_TANGENT = 1, PA_ABLATE_NO_NORMALISE = 2 };
 
 typedef struct {
@@ -106,6 +107,12 @@ typedef struct {
                        FP64;
                        CLUSTER: one thread-block cluster (<= 16 CTAs) with
                        the hardware cluster barrier (plain FP64 only);
+                       SINGLE: the grid reading A once per iteration with
+                       no transposed copy: each CTA owns a block of rows
+                       and the same x positions, sums A^T y over its rows'
+                       column window and the owners add the overlapping
+                       windows in CTA order (FP64, square matrices, rows of
+                       at most 255 entries; PA_ERR_UNSUPPORTED otherwise);
                        AUTO: CLUSTER when the grid would use <= 16 CTAs    */
   int ablation;     /* PA_ABLATE_* bits: drop the tangent projection and/or
                        the normalisation of Algorithm 1 (the paper's vanilla
@@ -301,12 +308,28 @@ pa_status pa_last_run_profile(pa_handle h, int* grid, double* busy_ns);
 pa_status pa_continue(pa_handle h, int iters, double lr, double beta1, double beta2, double eps,
                       double* sigma, double* x_last, double* info);
 
+/* z = A^T (A x) (Eq. nabla_loss's A^T A v term) through the single-pass
+ * engine's per-CTA window plans, without the transposed copy: y = A x over
+ * each CTA's row block, each CTA's window sums of A^T y in row order, and the
+ * owners of the positions add the overlapping windows in CTA order (so the
+ * result is reproducible bit for bit).  x and z have n_cols float64 entries
+ * (source order), host or device memory per ptr_kind; the caller owns both.
+ * Builds the plans on first use (square matrices with rows of at most 255
+ * entries; PA_ERR_UNSUPPORTED otherwise). */
+pa_status pa_spmv_ata(pa_handle h, const double* x, double* z, int ptr_kind);
+
+/* The single-pass engine's plan sizes, into out[5] (host): CTAs it was built
+ * for (0 before first use), window columns over all CTAs (halo slots), plan
+ * entries (one per non-zero), plan slots (entries plus the padding of the
+ * 32-column groups) and padded entries of the sliced copy of A. */
+pa_status pa_single_pass_info(pa_handle h, int64_t* out);
+
 /* Facts about the handle's latest single-vector run (pa_estimate, pa_run),
  * into out[4] (host):
  *   out[0] kernel: 0 the three-phase grid kernel, 1 the merged-phase grid
  *          kernel in FP64, 2 the merged-phase grid kernel in double-float
  *          (PA_DF64), 3 the cluster kernel, 4 the LU route on one CTA, 5 the
- *          LU route on the grid; -1 before any run;
+ *          LU route on the grid, 6 the single-pass kernel; -1 before any run;
  *   out[1] iterations of the merged-phase kernel that multiplied x itself
  *          instead of folding the update of x into the product (see the
  *          engine option);

@@ -174,6 +174,18 @@ struct pa_ctx {
     bool cluster = false;
     double best_s = 0, best_q = 0, lr = 0, b1 = 0, b2 = 0, eps = 0;
   } cont;
+  // the single-pass engine (PA_ENGINE_SINGLE): its partition (rows and x
+  // positions alike), the owners of each window's columns (sp_dep), the CTAs
+  // whose windows meet each CTA's positions (sp_rdep), its warp lists and the
+  // per-CTA window plans, built for sp_G CTAs
+  int sp_G = 0;
+  int32_t *sp_part = nullptr, *sp_dep = nullptr, *sp_rdep = nullptr;
+  int32_t *sp_list = nullptr, *sp_lwoff = nullptr;
+  int32_t *sp_cmin = nullptr, *sp_woff = nullptr, *sp_goff = nullptr, *sp_gp = nullptr;
+  int32_t* sp_gcol = nullptr;
+  uint32_t* sp_ent = nullptr;
+  double* sp_halo = nullptr;
+  int64_t sp_window_cols = 0, sp_plan_entries = 0, sp_plan_slots = 0;
 };
 
 static void* dev_alloc(pa_ctx* h, size_t bytes) {
@@ -354,7 +366,7 @@ extern "C" pa_status pa_create(pa_handle* out, int32_t n_rows, int32_t n_cols, i
     return fail(PA_ERR_INVALID_ARG, "unknown loss %d", o.loss);
   if (o.precision != PA_FP64 && o.precision != PA_MIXED && o.precision != PA_DF64)
     return fail(PA_ERR_INVALID_ARG, "unknown precision mode %d", o.precision);
-  if (o.engine < PA_ENGINE_AUTO || o.engine > PA_ENGINE_MERGED)
+  if (o.engine < PA_ENGINE_AUTO || o.engine > PA_ENGINE_SINGLE)
     return fail(PA_ERR_INVALID_ARG, "unknown engine %d", o.engine);
   if (o.equilibrate != PA_EQ_NONE && o.equilibrate != PA_EQ_STORAGE &&
       o.equilibrate != PA_EQ_TARGET)
@@ -745,6 +757,196 @@ static pa_status tune_partitions(pa_ctx* h, double t_iter) {
   return build_warp_lists(h);
 }
 
+// The single-pass engine's structures for G CTAs.  The partition cuts the
+// slices of P A Q^T at equal cost 32 (w(s) + 15) (each entry is used twice:
+// y = A x and its column's window sum; the 15 stands for the per-position
+// Adam work), and CTA b owns rows and x positions [32 part[b], 32 part[b+1]).
+// The plan of CTA b lists, for each column c of its window [cmin_b, cmax_b]
+// (the columns its rows touch), the block's entries in column c by
+// increasing row, each as (row - 32 part[b]) << 8 | slot k of the entry in
+// its row.  The columns with entries are sorted by entry count (stable) and
+// cut into groups of 32, one column per lane, stored column-major like the
+// slices of the matrix, so a warp's lanes take columns of equal length.
+// Built on the host from the sliced copy, so it is deterministic.
+static pa_status ensure_single(pa_ctx* h, int G) {
+  if (h->sp_G == G && h->sp_part) return PA_OK;
+  if (h->n_rows != h->n_cols)
+    return fail(PA_ERR_UNSUPPORTED, "the single-pass engine needs a square matrix (%d x %d)",
+                h->n_rows, h->n_cols);
+  for (void* q : {(void*)h->sp_part, (void*)h->sp_dep, (void*)h->sp_rdep, (void*)h->sp_list,
+                  (void*)h->sp_lwoff, (void*)h->sp_cmin, (void*)h->sp_woff, (void*)h->sp_goff,
+                  (void*)h->sp_gp, (void*)h->sp_gcol, (void*)h->sp_ent, (void*)h->sp_halo})
+    if (q) dev_free(h, q);
+  h->sp_part = h->sp_dep = h->sp_rdep = h->sp_list = h->sp_lwoff = nullptr;
+  h->sp_cmin = h->sp_woff = h->sp_goff = h->sp_gp = h->sp_gcol = nullptr;
+  h->sp_ent = nullptr;
+  h->sp_halo = nullptr;
+  h->sp_G = 0;
+  const int ns = h->sa.n_slices, n = h->n_cols;
+  pa_status st;
+  if ((st = alloc_n(h, &h->sp_part, (size_t)G + 1, "single-pass partition")) ||
+      (st = alloc_n(h, &h->sp_dep, (size_t)2 * G, "single-pass partition")))
+    return st;
+  cudaError_t e;
+  if ((e = launch_partition(h->sa.wp, ns, G, 15, h->sp_part, h->stream, &h->launches)) ||
+      (e = launch_dependencies(h->sa.wp, h->sa.col, h->sa.val, h->sp_part, h->sp_part, G,
+                               h->sp_dep, h->stream, &h->launches)))
+    return cuda_fail(e, "partitioning for the single-pass engine");
+  // the sliced copy on the host
+  if (h->wpa_h.empty()) {
+    h->wpa_h.resize((size_t)ns + 1);
+    h->wpt_h.resize((size_t)h->sq.n_slices + 1);
+    if ((e = cudaMemcpyAsync(h->wpa_h.data(), h->sa.wp, sizeof(int32_t) * h->wpa_h.size(), cudaMemcpyDeviceToHost, h->stream)) ||
+        (e = cudaMemcpyAsync(h->wpt_h.data(), h->sq.wp, sizeof(int32_t) * h->wpt_h.size(), cudaMemcpyDeviceToHost, h->stream)))
+      return cuda_fail(e, "reading the slice pointers");
+  }
+  const std::vector<int32_t>& wp = h->wpa_h;
+  const size_t total = (size_t)32 * wp[ns];
+  std::vector<int32_t> part((size_t)G + 1), col(total);
+  std::vector<double> val(total);
+  if ((e = cudaMemcpyAsync(part.data(), h->sp_part, sizeof(int32_t) * part.size(), cudaMemcpyDeviceToHost, h->stream)) ||
+      (total && (e = cudaMemcpyAsync(col.data(), h->sa.col, sizeof(int32_t) * total, cudaMemcpyDeviceToHost, h->stream))) ||
+      (total && (e = cudaMemcpyAsync(val.data(), h->sa.val, sizeof(double) * total, cudaMemcpyDeviceToHost, h->stream))) ||
+      (e = cudaStreamSynchronize(h->stream)))
+    return cuda_fail(e, "reading the sliced matrix");
+  for (int s = 0; s < ns; ++s)
+    if (wp[s + 1] - wp[s] > 255)
+      return fail(PA_ERR_UNSUPPORTED, "the single-pass engine takes rows of at most 255 entries");
+  // windows
+  std::vector<int32_t> cmin((size_t)G), woff((size_t)G + 1, 0), rdep((size_t)2 * G);
+  for (int b = 0; b < G; ++b) {
+    int32_t lo = INT32_MAX, hi = -1;
+    for (int s = part[b]; s < part[b + 1]; ++s)
+      for (size_t e2 = (size_t)32 * wp[s]; e2 < (size_t)32 * wp[s + 1]; ++e2)
+        if (val[e2] != 0.0) {
+          lo = std::min(lo, col[e2]);
+          hi = std::max(hi, col[e2]);
+        }
+    cmin[b] = hi < 0 ? 0 : lo;
+    const int64_t w = hi < 0 ? 0 : (int64_t)hi - lo + 1;
+    if ((int64_t)woff[b] + w > INT32_MAX - 1)
+      return fail(PA_ERR_UNSUPPORTED, "single-pass windows exceed 2^31 columns");
+    woff[b + 1] = woff[b] + (int32_t)w;
+  }
+  const size_t nwin = (size_t)woff[G];
+  // entries per window column, then the entries in row order
+  std::vector<int32_t> cptr(nwin + 1, 0);
+  for (int b = 0; b < G; ++b)
+    for (int s = part[b]; s < part[b + 1]; ++s)
+      for (size_t e2 = (size_t)32 * wp[s]; e2 < (size_t)32 * wp[s + 1]; ++e2)
+        if (val[e2] != 0.0) ++cptr[(size_t)woff[b] + (col[e2] - cmin[b]) + 1];
+  for (size_t w = 0; w < nwin; ++w) cptr[w + 1] += cptr[w];
+  const size_t nent = (size_t)cptr[nwin];
+  std::vector<uint32_t> bucket(std::max<size_t>(nent, 1));
+  {
+    std::vector<int32_t> fill(cptr.begin(), cptr.end() - 1);
+    for (int b = 0; b < G; ++b)
+      for (int s = part[b]; s < part[b + 1]; ++s) {
+        const int w = wp[s + 1] - wp[s];
+        for (int l = 0; l < 32; ++l)  // rows of the slice in order, each row's entries in order
+          for (int k = 0; k < w; ++k) {
+            const size_t e2 = (size_t)32 * (wp[s] + k) + l;
+            if (val[e2] == 0.0) continue;
+            const uint32_t rl = (uint32_t)(32 * (s - part[b]) + l);
+            bucket[(size_t)fill[(size_t)woff[b] + (col[e2] - cmin[b])]++] = (rl << 8) | (uint32_t)k;
+          }
+      }
+  }
+  // per CTA: the window columns that have entries, by decreasing count
+  // (stable), in groups of 32 stored column-major and padded with kPlanPad
+  std::vector<int32_t> goff((size_t)G + 1, 0), gp(1, 0), gcol;
+  std::vector<uint32_t> ent;
+  std::vector<int32_t> order;
+  for (int b = 0; b < G; ++b) {
+    const int32_t W = woff[b + 1] - woff[b];
+    auto cnt = [&](int32_t w) { return cptr[(size_t)woff[b] + w + 1] - cptr[(size_t)woff[b] + w]; };
+    order.clear();
+    for (int32_t w = 0; w < W; ++w)
+      if (cnt(w) > 0) order.push_back(w);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return cnt(x) > cnt(y); });
+    for (size_t g0 = 0; g0 < order.size(); g0 += 32) {
+      const int width = cnt(order[g0]);
+      const size_t base = ent.size();
+      ent.resize(base + (size_t)32 * width, kPlanPad);
+      for (int l = 0; l < 32; ++l) {
+        if (g0 + l >= order.size()) {
+          gcol.push_back(-1);
+          continue;
+        }
+        const int32_t w = order[g0 + l];
+        gcol.push_back(w);
+        const size_t c0 = (size_t)cptr[(size_t)woff[b] + w];
+        for (int k = 0; k < cnt(w); ++k) ent[base + (size_t)32 * k + l] = bucket[c0 + k];
+      }
+      gp.push_back(gp.back() + width);
+    }
+    goff[b + 1] = (int32_t)(gp.size() - 1);
+  }
+  if (ent.empty()) ent.push_back(kPlanPad);
+  if (gcol.empty()) gcol.push_back(-1);
+  // the CTAs whose windows meet each CTA's own positions
+  for (int c = 0; c < G; ++c) {
+    const int64_t p0 = std::min<int64_t>(32ll * part[c], n), p1 = std::min<int64_t>(32ll * part[c + 1], n);
+    int lo = 1, hi = 0;
+    for (int b = 0; b < G && p0 < p1; ++b) {
+      const int64_t w0 = cmin[b], w1 = (int64_t)cmin[b] + (woff[b + 1] - woff[b]);
+      if (w0 < p1 && p0 < w1) {
+        if (lo > hi) lo = b;
+        hi = b;
+      }
+    }
+    rdep[2 * c] = lo;
+    rdep[2 * c + 1] = hi;
+  }
+  std::vector<int32_t> list, lwoff;
+  deal_slices(part, wp, 15, kBlock / 32, &list, &lwoff);
+  if ((st = alloc_n(h, &h->sp_rdep, rdep.size(), "single-pass plan")) ||
+      (st = alloc_n(h, &h->sp_list, std::max<size_t>(list.size(), 1), "single-pass plan")) ||
+      (st = alloc_n(h, &h->sp_lwoff, lwoff.size(), "single-pass plan")) ||
+      (st = alloc_n(h, &h->sp_cmin, cmin.size(), "single-pass plan")) ||
+      (st = alloc_n(h, &h->sp_woff, woff.size(), "single-pass plan")) ||
+      (st = alloc_n(h, &h->sp_goff, goff.size(), "single-pass plan")) ||
+      (st = alloc_n(h, &h->sp_gp, gp.size(), "single-pass plan")) ||
+      (st = alloc_n(h, &h->sp_gcol, gcol.size(), "single-pass plan")) ||
+      (st = alloc_n(h, &h->sp_ent, ent.size(), "single-pass plan")) ||
+      (st = alloc_n(h, &h->sp_halo, std::max<size_t>(nwin, 1), "single-pass halo")))
+    return st;
+  if ((e = cudaMemcpyAsync(h->sp_rdep, rdep.data(), sizeof(int32_t) * rdep.size(), cudaMemcpyHostToDevice, h->stream)) ||
+      (!list.empty() && (e = cudaMemcpyAsync(h->sp_list, list.data(), sizeof(int32_t) * list.size(), cudaMemcpyHostToDevice, h->stream))) ||
+      (e = cudaMemcpyAsync(h->sp_lwoff, lwoff.data(), sizeof(int32_t) * lwoff.size(), cudaMemcpyHostToDevice, h->stream)) ||
+      (e = cudaMemcpyAsync(h->sp_cmin, cmin.data(), sizeof(int32_t) * cmin.size(), cudaMemcpyHostToDevice, h->stream)) ||
+      (e = cudaMemcpyAsync(h->sp_woff, woff.data(), sizeof(int32_t) * woff.size(), cudaMemcpyHostToDevice, h->stream)) ||
+      (e = cudaMemcpyAsync(h->sp_goff, goff.data(), sizeof(int32_t) * goff.size(), cudaMemcpyHostToDevice, h->stream)) ||
+      (e = cudaMemcpyAsync(h->sp_gp, gp.data(), sizeof(int32_t) * gp.size(), cudaMemcpyHostToDevice, h->stream)) ||
+      (e = cudaMemcpyAsync(h->sp_gcol, gcol.data(), sizeof(int32_t) * gcol.size(), cudaMemcpyHostToDevice, h->stream)) ||
+      (e = cudaMemsetAsync(h->sp_halo, 0, sizeof(double) * std::max<size_t>(nwin, 1), h->stream)) ||
+      (e = cudaMemcpyAsync(h->sp_ent, ent.data(), sizeof(uint32_t) * ent.size(), cudaMemcpyHostToDevice, h->stream)) ||
+      (e = cudaStreamSynchronize(h->stream)))  // the host vectors are pageable
+    return cuda_fail(e, "uploading the single-pass plan");
+  h->sp_window_cols = (int64_t)nwin;
+  h->sp_plan_entries = (int64_t)nent;
+  h->sp_plan_slots = (int64_t)ent.size();
+  h->sp_G = G;
+  return PA_OK;
+}
+
+// The single-pass engine's fields of IterParams.
+static void single_params(pa_ctx* h, IterParams* p) {
+  p->part_a = h->sp_part;
+  p->part_t = h->sp_part;
+  p->dep = h->sp_dep;
+  p->a_list = h->sp_list;
+  p->a_woff = h->sp_lwoff;
+  p->sp_cmin = h->sp_cmin;
+  p->sp_woff = h->sp_woff;
+  p->sp_goff = h->sp_goff;
+  p->sp_gp = h->sp_gp;
+  p->sp_gcol = h->sp_gcol;
+  p->sp_ent = h->sp_ent;
+  p->sp_halo = h->sp_halo;
+  p->sp_rdep = h->sp_rdep;
+}
+
 // Per-iteration Adam scalars: the step lr m_hat / (sqrt(v_hat) + eps) with
 // m_hat = m / (1 - b1^t), v_hat = v / (1 - b2^t) equals K1 m / (sqrt(v) + K2)
 // with K1 = lr sqrt(1 - b2^t) / (1 - b1^t) and K2 = eps sqrt(1 - b2^t).
@@ -811,7 +1013,8 @@ static pa_status fp64_run(pa_ctx* h, pa_mode mode, int iters, int t0, bool fresh
                           double* x_trace_dev, int n_trace, RunState* out, bool cluster = false,
                           int kernel = 0, const pa_ctx::Cont* cont = nullptr) {
   // kernel: 0 = the three-phase k_persistent, 1 = the merged-phase kernel in
-  // FP64, 2 = the merged-phase kernel in double-float
+  // FP64, 2 = the merged-phase kernel in double-float, 6 = the single-pass
+  // kernel (k_single)
   const size_t n = (size_t)h->n_cols;
   cudaError_t e = cudaSuccess;
   if (fresh_state &&
@@ -873,8 +1076,10 @@ static pa_status fp64_run(pa_ctx* h, pa_mode mode, int iters, int t0, bool fresh
         (e = cudaMemsetAsync(h->vd, 0, sizeof(float2) * n, h->stream)))
       return cuda_fail(e, "preparing the run");
   }
+  if (kernel == 6) single_params(h, &p);
   if (cluster) e = launch_persistent_cluster(p, h->opt.loss, G, h->stream, &h->launches);
   else if (kernel == 0) e = launch_persistent(p, h->opt.loss, dd, G, h->stream, &h->launches);
+  else if (kernel == 6) e = launch_single(p, h->opt.loss, G, h->stream, &h->launches);
   else e = launch_merged(p, h->opt.loss, kernel == 2, G, h->stream, &h->launches);
   if (e == cudaErrorCooperativeLaunchTooLarge)
     return fail(PA_ERR_LAUNCH, "cooperative grid of %d CTAs does not fit (max %d)", G, maxG);
@@ -1021,7 +1226,16 @@ static pa_status run_one(pa_ctx* h, pa_mode mode, int iters, double lr, double b
   // plain FP64 runs of matrices that would use at most 16 CTAs anyway
   bool cluster = false;
   const bool df = h->opt.precision == PA_DF64 && h->df_ok;
-  if (!mixed && !df && h->opt.engine != PA_ENGINE_GRID && h->opt.engine != PA_ENGINE_MERGED &&
+  const bool single = h->opt.engine == PA_ENGINE_SINGLE;
+  if (single) {
+    if (h->opt.precision != PA_FP64)
+      return fail(PA_ERR_UNSUPPORTED, "the single-pass engine runs in FP64 only");
+    const int gs = single_max_blocks(h->opt.loss);
+    if (gs <= 0) return fail(PA_ERR_LAUNCH, "the single-pass kernel does not fit on this GPU");
+    G = std::min(G, gs);
+    maxG = std::min(maxG, gs);
+  }
+  if (!mixed && !df && !single && h->opt.engine != PA_ENGINE_GRID && h->opt.engine != PA_ENGINE_MERGED &&
       h->opt.debug_skip_arrival == 0 && (h->opt.engine == PA_ENGINE_CLUSTER || G <= 16)) {
     const int cmax = persistent_cluster_max(h->opt.loss);
     const int slices = std::max(1, std::min(h->sa.n_slices, h->sq.n_slices));
@@ -1034,11 +1248,12 @@ static pa_status run_one(pa_ctx* h, pa_mode mode, int iters, double lr, double b
   }
   pa_status st;
   if ((st = ensure_partitions(h, G)) || (st = ensure_bias(h, iters, lr, b1, b2, eps))) return st;
+  if (single && (st = ensure_single(h, G))) return st;
   if (mixed && mode == PA_SIGMA_MAX) {
     h->cont.valid = false;
     if ((st = mixed_max_run(h, iters, b1, b2, eps, G, maxG, L_trace_dev, out)) < 0) return st;
   } else {
-    const bool tuning = !cluster && !mixed && h->opt.autotune > 0 &&
+    const bool tuning = !cluster && !mixed && !single && h->opt.autotune > 0 &&
                         h->tuned_rounds < h->opt.autotune && iters >= 20;
     cudaError_t e;
     if (tuning) {
@@ -1049,7 +1264,8 @@ static pa_status run_one(pa_ctx* h, pa_mode mode, int iters, double lr, double b
     // the merged-phase kernel in double-float for PA_DF64 (when the matrix
     // fits it) and in FP64 on request; otherwise the three-phase kernel
     int kernel = 0;
-    if (!cluster && !mixed) {
+    if (single) kernel = 6;
+    else if (!cluster && !mixed) {
       if (h->opt.precision == PA_DF64 && h->df_ok) kernel = 2;
       else if (h->opt.engine == PA_ENGINE_MERGED) kernel = 1;
     }
@@ -1090,8 +1306,8 @@ static pa_status run_one(pa_ctx* h, pa_mode mode, int iters, double lr, double b
   else { h->sigma_min = out->sigma; h->have_min = true; h->have_min_direct = true; }
   // the partition tuner learns from plain FP64 grid-engine runs long enough
   // to time (the FP32 and compensated kernels have other cost profiles)
-  if (!cluster && !mixed && h->opt.autotune > 0 && h->tuned_rounds < h->opt.autotune && iters >= 20 &&
-      (st = tune_partitions(h, h->last_run_ms / iters)))
+  if (!cluster && !mixed && !single && h->opt.autotune > 0 && h->tuned_rounds < h->opt.autotune &&
+      iters >= 20 && (st = tune_partitions(h, h->last_run_ms / iters)))
     return st;
   return (pa_status)out->status;
 }
@@ -1630,6 +1846,61 @@ extern "C" pa_status pa_spmv(pa_handle h, const double* x, double* y, int ptr_ki
 extern "C" pa_status pa_spmv_t(pa_handle h, const double* y, double* z, int ptr_kind) {
   NvtxRange nvtx_range("pa_spmv_t");
   return product(h, true, y, z, ptr_kind);
+}
+
+extern "C" pa_status pa_spmv_ata(pa_handle h, const double* x, double* z, int ptr_kind) {
+  NvtxRange nvtx_range("pa_spmv_ata");
+  g_err.clear();
+  if (!h || !x || !z) return fail(PA_ERR_INVALID_ARG, "NULL argument");
+  if (ptr_kind != PA_HOST && ptr_kind != PA_DEVICE) return fail(PA_ERR_INVALID_ARG, "bad ptr_kind");
+  pa_status st;
+  if ((st = ensure_run_buffers(h))) return st;
+  int maxG = 0;
+  int G = choose_grid(h, &maxG);
+  if (G <= 0) return fail(PA_ERR_LAUNCH, "the persistent kernel does not fit on this GPU");
+  const int gs = single_max_blocks(h->opt.loss);
+  if (gs > 0) G = std::min(G, gs);
+  if ((st = ensure_single(h, G))) return st;
+  const int32_t n = h->n_cols;
+  double *a = nullptr, *ap = nullptr, *zp = nullptr, *zb = nullptr;
+  if ((st = alloc_n(h, &a, (size_t)n, "product input")) ||
+      (st = alloc_n(h, &ap, (size_t)n, "product input")) ||
+      (st = alloc_n(h, &zp, (size_t)n, "product output")) ||
+      (st = alloc_n(h, &zb, (size_t)n, "product output")))
+    return st;
+  IterParams p{};
+  p.n_rows = h->n_rows;
+  p.n_cols = h->n_cols;
+  p.a_wp = h->sa.wp; p.a_col = h->sa.col; p.a_val = h->sa.val;
+  p.y = h->y;
+  single_params(h, &p);
+  cudaError_t e = cudaMemcpyAsync(a, x, sizeof(double) * n,
+                                  ptr_kind == PA_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                  h->stream);
+  if (e == cudaSuccess) e = launch_permute(n, h->sq.pos, a, ap, h->stream, &h->launches);
+  if (e == cudaSuccess) e = launch_single_product(p, G, ap, zp, h->stream, &h->launches);
+  if (e == cudaSuccess) e = launch_unpermute(n, 1, h->sq.pos, zp, zb, h->stream, &h->launches);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(z, zb, sizeof(double) * n,
+                        ptr_kind == PA_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  dev_free(h, a);
+  dev_free(h, ap);
+  dev_free(h, zp);
+  dev_free(h, zb);
+  if (e != cudaSuccess) return cuda_fail(e, "single-pass product");
+  return PA_OK;
+}
+
+extern "C" pa_status pa_single_pass_info(pa_handle h, int64_t* out) {
+  g_err.clear();
+  if (!h || !out) return fail(PA_ERR_INVALID_ARG, "NULL argument");
+  out[0] = h->sp_G;
+  out[1] = h->sp_window_cols;
+  out[2] = h->sp_plan_entries;
+  out[3] = h->sp_plan_slots;
+  out[4] = h->a_entries;
+  return PA_OK;
 }
 
 extern "C" pa_status pa_get_transpose(pa_handle h, int32_t* row_ptr_t, int32_t* col_t, double* val_t) {

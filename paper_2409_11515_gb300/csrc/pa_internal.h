@@ -100,7 +100,31 @@ struct IterParams {
   const float4* bias2;                 // [iters]: K1 and K2 of `bias` as (hi, lo) pairs
   double s_scale;                      // 4^k: ||A x||^2 = s_scale ||2^-k A x||^2
   int win_slices;                      // slices per CTA whose products wait in shared memory
+  // ---- the single-pass engine (k_single): part_a is its row/position
+  // partition, dep its window's owners, a_list/a_woff its warp lists ----
+  // CTA b's window columns (those its rows touch, sorted by entry count) come
+  // in groups of 32, one per lane: groups [sp_goff[b], sp_goff[b+1]); group
+  // g's entries sit column-major at sp_ent[32 (sp_gp[g] + k) + lane], k <
+  // sp_gp[g+1] - sp_gp[g], each (row - 32 part_a[b]) << 8 | slot in the row,
+  // or kPlanPad; lane l's column is window slot sp_gcol[32 g + l] (-1: none)
+  const int32_t* sp_cmin;   // [G] first x position of CTA b's column window
+  const int32_t* sp_woff;   // [G+1] CTA b's window columns are slots [sp_woff[b], sp_woff[b+1])
+  const int32_t* sp_goff;   // [G+1]
+  const int32_t* sp_gp;     // [groups + 1]
+  const int32_t* sp_gcol;   // [32 groups]
+  const uint32_t* sp_ent;   // [32 sp_gp[groups]]
+  double* sp_halo;          // [sp_woff[G]] CTA b's partial sums of A^T y over its window
+  const int32_t* sp_rdep;   // [2G] CTAs whose windows meet CTA b's own positions: [lo, hi]
 };
+
+constexpr uint32_t kPlanPad = 0xffffffffu;  // a padding slot of a plan group
+// The single-pass engine: Algorithm 1 reading P A Q^T once per iteration
+// (no transposed copy); needs a square matrix, slices at most 255 wide.
+int single_max_blocks(int loss);
+cudaError_t launch_single(const IterParams& p, int loss, int G, cudaStream_t s, int64_t* launches);
+// z = A^T (A x) at positions through the same plan (y is left in p.y).
+cudaError_t launch_single_product(const IterParams& p, int G, const double* x, double* z,
+                                  cudaStream_t s, int64_t* launches);
 
 // The mixed-precision sigma_max iteration (FP32 products and Adam state on
 // the power-of-two-equilibrated matrix, FP64 norms).

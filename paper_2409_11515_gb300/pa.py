@@ -26,7 +26,7 @@ HOST, DEVICE = 0, 1
 LOSS_LOGRATIO, LOSS_QUADRATIC = 0, 1
 FP64, MIXED, DF64 = 0, 1, 2
 EQ_NONE, EQ_STORAGE, EQ_TARGET = 0, 1, 2
-ENGINE_AUTO, ENGINE_GRID, ENGINE_CLUSTER, ENGINE_MERGED = 0, 1, 2, 3
+ENGINE_AUTO, ENGINE_GRID, ENGINE_CLUSTER, ENGINE_MERGED, ENGINE_SINGLE = 0, 1, 2, 3, 4
 ABLATE_NO_TANGENT, ABLATE_NO_NORMALISE = 1, 2
 
 OK, WARN_SINGULAR = 0, 1
@@ -38,7 +38,8 @@ STATUS_NAMES = {0: "PA_OK", 1: "PA_WARN_SINGULAR", -1: "PA_ERR_INVALID_ARG",
 EXPORTS = ("pa_options_default", "pa_create", "pa_estimate", "pa_run", "pa_estimate_batched",
            "pa_get_vector", "pa_spmv", "pa_spmv_t", "pa_get_transpose", "pa_get_equilibration",
            "pa_kernel_launches", "pa_destroy", "pa_last_error", "pa_set_allocator",
-           "pa_last_run_profile", "pa_last_run_info", "pa_continue", "pa_sigma_noalloc", "pa_last_batch_graph", "pa_error_bounds", "pa_attach_lu")
+           "pa_last_run_profile", "pa_last_run_info", "pa_continue", "pa_sigma_noalloc", "pa_last_batch_graph", "pa_error_bounds", "pa_attach_lu",
+           "pa_spmv_ata", "pa_single_pass_info")
 
 ERROR_BOUND_KEYS = ("residual_norm", "b_norm", "x_hat_norm", "thm1_lower", "thm1_upper",
                     "thm2_lower", "thm2_upper", "thm3_upper", "thm4_rounding", "singular")
@@ -105,6 +106,10 @@ def _declare(L):
     L.pa_spmv.argtypes = [vp, vp, vp, C.c_int]
     L.pa_spmv_t.restype = C.c_int
     L.pa_spmv_t.argtypes = [vp, vp, vp, C.c_int]
+    L.pa_spmv_ata.restype = C.c_int
+    L.pa_spmv_ata.argtypes = [vp, vp, vp, C.c_int]
+    L.pa_single_pass_info.restype = C.c_int
+    L.pa_single_pass_info.argtypes = [vp, vp]
     L.pa_get_transpose.restype = C.c_int
     L.pa_get_transpose.argtypes = [vp, vp, vp, vp]
     L.pa_get_equilibration.restype = C.c_int
@@ -285,6 +290,17 @@ class Handle:
     def spmv_t(self, y):
         return self._product(load().pa_spmv_t, y, self.n_cols)
 
+    def spmv_ata(self, x):
+        """pa_spmv_ata: A^T (A x) through the single-pass engine's plans."""
+        return self._product(load().pa_spmv_ata, x, self.n_cols)
+
+    def single_pass_info(self):
+        """pa_single_pass_info: {grid, window_cols, plan_entries, plan_slots, a_entries}."""
+        out = np.zeros(5, dtype=np.int64)
+        _check(load().pa_single_pass_info(self._h, out.ctypes.data))
+        return dict(grid=int(out[0]), window_cols=int(out[1]), plan_entries=int(out[2]),
+                    plan_slots=int(out[3]), a_entries=int(out[4]))
+
     def get_transpose(self):
         rpt = np.empty(self.n_cols + 1, dtype=np.int32)
         cit = np.empty(max(self.nnz, 1), dtype=np.int32)
@@ -314,7 +330,7 @@ class Handle:
     def last_run_info(self):
         """pa_last_run_info: {kernel, refreshes, df_fallbacks, grid} of the
         latest single-vector run (kernel 0 three-phase grid, 1 merged FP64,
-        2 merged double-float, 3 cluster)."""
+        2 merged double-float, 3 cluster, 4/5 LU route, 6 single-pass)."""
         out = np.zeros(4, dtype=np.int64)
         _check(load().pa_last_run_info(self._h, out.ctypes.data))
         return dict(kernel=int(out[0]), refreshes=int(out[1]), df_fallbacks=int(out[2]),
