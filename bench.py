@@ -191,6 +191,7 @@ def flops_per_iteration(n_rows, n_cols, nnz):
 
 KERNEL_SOURCES = {
     "k_persistent": ("pa_iter.cu", "pa_device.cuh", "pa_internal.h"),
+    "k_single": ("pa_iter_sp.cu", "pa_device.cuh", "pa_internal.h"),
     "k_merged_df64": ("pa_iter2.cu", "pa_df.cuh", "pa_device.cuh", "pa_internal.h"),
 }
 TRAFFIC_FILE = ROOT / "profiles" / "dram_traffic.json"
@@ -381,6 +382,64 @@ def sub_c2_df64(A, stream, it_max, it_min, hbm_peak, ref):
                    "rel_err_vs_oracle": {"sigma_max": _rel_err(rM["sigma_max"], ref, "sigma_max"),
                                          "sigma_min": _rel_err(rm["sigma_min"], ref, "sigma_min")}},
         "run_info": {"sigma_max": infoM, "sigma_min": infom},
+    }
+
+
+def single_pass_bytes(A, info):
+    """Bytes of one iteration of the single-pass engine on two bases.
+    int32-CSR basis: A read once (12 B per entry + 4 B per row pointer) and
+    seven 8-byte vector streams per row (x gather, x read, m r/w, v r/w, x
+    write; y stays with the CTA that made it).  Actual basis: what the
+    kernel moves -- the sliced copy (12 B per padded entry, 4 B per slice),
+    the plan (4 B per slot, 4 B per group lane and per group), the halo
+    (8 B written and 8 B read per window column), y and dx through memory
+    (16 B each per row) and the seven vector streams."""
+    n, nnz = A.n_cols, A.nnz
+    csr = 12 * nnz + 4 * (A.n_rows + 1) + 56 * n
+    slices = (A.n_rows + 31) // 32
+    actual = (12 * info["a_entries"] + 4 * (slices + 1) + 4 * info["plan_slots"]
+              + 4 * 33 * info["groups"] + 16 * info["window_cols"] + 32 * n + 56 * n)
+    return csr, actual
+
+
+def sub_c2_single(A, stream, hbm_peak, ref):
+    """The headline workload on the single-pass engine (A read once per
+    iteration, no transposed copy): one full estimate timed, FP64."""
+    from paper_2409_11515_gb300 import pa
+    with pa.create(A, stream=stream, engine=pa.ENGINE_SINGLE) as h:
+        h.estimate(pa.SIGMA_MAX, 200, seed=START_SEED, **HYPER)  # builds the plans
+        rM, tM = _timed_events(stream, lambda: h.estimate(pa.SIGMA_MAX, ITERS_MAX, seed=START_SEED, **HYPER))
+        rm, tm = _timed_events(stream, lambda: h.estimate(pa.SIGMA_MIN, ITERS_MIN, seed=START_SEED, **HYPER))
+        info = h.single_pass_info()
+        run = h.last_run_info()
+    its = ITERS_MAX + ITERS_MIN
+    t = tM + tm
+    csr, actual = single_pass_bytes(A, info)
+    two_pass = bytes_per_iteration(A.n_rows, A.n_cols, A.nnz)
+    F = flops_per_iteration(A.n_rows, A.n_cols, A.nnz)
+    tpi = profiled_traffic_per_iteration("k_single")
+    return {
+        "engine": "PA_ENGINE_SINGLE (k_single<0>), FP64, "
+                  f"{info['grid']} CTAs, {info['window_cols']:,} window columns",
+        "iterations_per_s": its / t, "us_per_iteration": 1e6 * t / its,
+        "kappa_estimates_per_s": 1.0 / t,
+        "roofline": {"bound": "alu", "achieved": F * its / t / 1e12, "unit": "TFLOP/s",
+                     "flops_per_iteration": F},
+        "roofline_hbm": {"unit": "GB/s", "peak": hbm_peak,
+                         "int32_csr_basis": {"bytes_per_iteration": csr,
+                                             "achieved": csr * its / t / 1e9,
+                                             "frac": csr * its / t / 1e9 / hbm_peak},
+                         "actual_basis": {"bytes_per_iteration": actual,
+                                          "achieved": actual * its / t / 1e9,
+                                          "frac": actual * its / t / 1e9 / hbm_peak},
+                         "two_pass_int32_csr_basis_bytes": two_pass,
+                         "traffic": tpi * its / 2 if tpi else None},
+        "plan": info,
+        "result": {"sigma_max": rM["sigma_max"], "sigma_min_direct": rm["sigma_min"],
+                   "kappa_direct": rM["sigma_max"] / rm["sigma_min"],
+                   "rel_err_vs_oracle": {"sigma_max": _rel_err(rM["sigma_max"], ref, "sigma_max"),
+                                         "sigma_min": _rel_err(rm["sigma_min"], ref, "sigma_min")}},
+        "run_info": run,
     }
 
 
@@ -601,7 +660,9 @@ def run_ours(args):
     tune_rounds = min(args.autotune, 2 * args.warmup)  # all of them inside the warm-up
     df = args.precision == "df64"
     prec = pa.DF64 if df else pa.FP64
-    h = pa.create(A, stream=stream, autotune=tune_rounds, precision=prec)
+    single = args.engine == "single"
+    eng = pa.ENGINE_SINGLE if single else pa.ENGINE_AUTO
+    h = pa.create(A, stream=stream, autotune=tune_rounds, precision=prec, engine=eng)
     it_per_step = ITERS_MAX + ITERS_MIN
 
     def step(handle):
@@ -643,16 +704,17 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     clk = clocks.get("sm_mhz") or 2070.0
     fp64_peak = fp64_peak_tflops(clk)
-    kname = "k_merged_df64" if df else "k_persistent"
+    kname = "k_merged_df64" if df else ("k_single" if single else "k_persistent")
     tpi = profiled_traffic_per_iteration(kname)
     launch_iters = tot_it / len(kms)
     h.destroy()
     ref = _oracle_run("hydro401") if (ITERS_MAX, ITERS_MIN) == EST_ITERS else None
     # ---- the other configurations, each on a bounded sample (rank 0 only)
     subs = None
-    if rank == 0 and not args.no_sub and not df:
+    if rank == 0 and not args.no_sub and not df and not single:
         subs = {}
         subs["c2_df64"] = sub_c2_df64(A, stream, ITERS_MAX, ITERS_MIN, peak, ref)
+        subs["c2_single_pass"] = sub_c2_single(A, stream, peak, ref)
         subs["c1_hydro21_cluster"] = sub_c1(stream, args.steps if args.steps <= 3 else 3)
         subs["c3_batched64"] = sub_c3(stream)
         subs["c4_hydro1001"] = sub_c4(stream, peak)
@@ -663,7 +725,7 @@ def run_ours(args):
     _barrier(ws)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        with pa.create(A, stream=stream, autotune=tune_rounds, precision=prec) as he:
+        with pa.create(A, stream=stream, autotune=tune_rounds, precision=prec, engine=eng) as he:
             he.estimate(pa.SIGMA_MAX, ITERS_MAX, seed=START_SEED, **HYPER)
             re = he.estimate(pa.SIGMA_MIN, ITERS_MIN, seed=START_SEED, **HYPER)
     torch.cuda.synchronize()
@@ -677,10 +739,11 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "df64 (2xf32)" if df else "f64",
             "data": "synthetic (seeded hydro-mechanical operator generator)",
-            "config": dict(_config(A), parallelism=f"replicas{ws}" if ws > 1 else "single_gpu",
-                           precision="PA_DF64" if df else "fp64",
-                           partition=(f"measured-cost tuner, {tune_rounds} rounds in warm-up"
-                                      if tune_rounds > 0 else "fixed cost model")),
+            "config": dict(_config(A), **({"precision": "PA_DF64"} if df else {})),
+            "setup": {"parallelism": f"replicas{ws}" if ws > 1 else "single_gpu",
+                      "engine": "single-pass" if single else "auto (three-phase grid kernel)",
+                      "partition": (f"measured-cost tuner, {tune_rounds} rounds in warm-up"
+                                    if tune_rounds > 0 else "fixed cost model")},
             "kappa_estimates_per_s": ws * args.steps / (ms / 1e3),
             "result": {"sigma_max": r["sigma_max"], "sigma_min_direct": r["sigma_min"],
                        "kappa_direct": r["kappa"], "kappa_note": KAPPA_NOTE,
@@ -693,6 +756,7 @@ def run_ours(args):
             "roofline": {"bound": "alu", "achieved": achieved_f, "peak": fp64_peak,
                          "unit": "TFLOP/s", "frac": achieved_f / fp64_peak, "traffic": traffic,
                          "kernel": ("k_merged<0, true, 2>, double-float" if df else
+                                    "k_single<0>, FP64 single-pass" if single else
                                     "k_persistent<0, 0, 0>, FP64") +
                                    " (per-launch CUDA events on its stream)",
                          "peak_source": f"FP64 pipe: 2 FMA lanes/SM/clock x {_sm_count()} SMs x 2 "
@@ -1119,6 +1183,9 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "mixed", "df64"], default="fp64",
                     help="the handles' precision mode: the default workload takes fp64 "
                          "(the benchmark line) or df64; the batched workload fp64 or mixed")
+    ap.add_argument("--engine", choices=["auto", "single"], default="auto",
+                    help="hydro401 only: the handle's engine (single: the single-pass "
+                         "engine, for profiling it on the benchmark workload)")
     ap.add_argument("--iters-max", type=int, default=None,
                     help="sigma_max iterations per estimate (short runs for profiling); "
                          "default 5000, stress2001 200, batched 500 (timed, then extrapolated)")

@@ -318,10 +318,10 @@ pa_status pa_continue(pa_handle h, int iters, double lr, double beta1, double be
  * entries; PA_ERR_UNSUPPORTED otherwise). */
 pa_status pa_spmv_ata(pa_handle h, const double* x, double* z, int ptr_kind);
 
-/* The single-pass engine's plan sizes, into out[5] (host): CTAs it was built
+/* The single-pass engine's plan sizes, into out[6] (host): CTAs it was built
  * for (0 before first use), window columns over all CTAs (halo slots), plan
  * entries (one per non-zero), plan slots (entries plus the padding of the
- * 32-column groups) and padded entries of the sliced copy of A. */
+ * 32-column groups), groups, and padded entries of the sliced copy of A. */
 pa_status pa_single_pass_info(pa_handle h, int64_t* out);
 
 /* Facts about the handle's latest single-vector run (pa_estimate, pa_run),

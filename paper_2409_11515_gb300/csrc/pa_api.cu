@@ -185,7 +185,7 @@ struct pa_ctx {
   int32_t* sp_gcol = nullptr;
   uint32_t* sp_ent = nullptr;
   double* sp_halo = nullptr;
-  int64_t sp_window_cols = 0, sp_plan_entries = 0, sp_plan_slots = 0;
+  int64_t sp_window_cols = 0, sp_plan_entries = 0, sp_plan_slots = 0, sp_groups = 0;
 };
 
 static void* dev_alloc(pa_ctx* h, size_t bytes) {
@@ -926,6 +926,7 @@ static pa_status ensure_single(pa_ctx* h, int G) {
   h->sp_window_cols = (int64_t)nwin;
   h->sp_plan_entries = (int64_t)nent;
   h->sp_plan_slots = (int64_t)ent.size();
+  h->sp_groups = (int64_t)goff[G];
   h->sp_G = G;
   return PA_OK;
 }
@@ -1899,7 +1900,8 @@ extern "C" pa_status pa_single_pass_info(pa_handle h, int64_t* out) {
   out[1] = h->sp_window_cols;
   out[2] = h->sp_plan_entries;
   out[3] = h->sp_plan_slots;
-  out[4] = h->a_entries;
+  out[4] = h->sp_groups;
+  out[5] = h->a_entries;
   return PA_OK;
 }
 

@@ -295,11 +295,12 @@ class Handle:
         return self._product(load().pa_spmv_ata, x, self.n_cols)
 
     def single_pass_info(self):
-        """pa_single_pass_info: {grid, window_cols, plan_entries, plan_slots, a_entries}."""
-        out = np.zeros(5, dtype=np.int64)
+        """pa_single_pass_info: {grid, window_cols, plan_entries, plan_slots, groups,
+        a_entries}."""
+        out = np.zeros(6, dtype=np.int64)
         _check(load().pa_single_pass_info(self._h, out.ctypes.data))
         return dict(grid=int(out[0]), window_cols=int(out[1]), plan_entries=int(out[2]),
-                    plan_slots=int(out[3]), a_entries=int(out[4]))
+                    plan_slots=int(out[3]), groups=int(out[4]), a_entries=int(out[5]))
 
     def get_transpose(self):
         rpt = np.empty(self.n_cols + 1, dtype=np.int32)
