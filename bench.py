@@ -704,9 +704,13 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     clk = clocks.get("sm_mhz") or 2070.0
     fp64_peak = fp64_peak_tflops(clk)
-    kname = "k_merged_df64" if df else ("k_single" if single else "k_persistent")
-    tpi = profiled_traffic_per_iteration(kname)
+    ran = h.last_run_info()["kernel"]  # the launch-shape tuner may pick another kernel
+    kname = {0: "k_persistent", 1: "k_merged_fp64", 2: "k_merged_df64", 6: "k_single"}.get(ran, "?")
+    klabel = {0: "k_persistent<0, 0, 0>, FP64", 1: "k_merged<0, false, 2>, FP64",
+              2: "k_merged<0, true, 2>, double-float", 6: "k_single<0>, FP64 single-pass"}.get(ran, "?")
+    tpi = profiled_traffic_per_iteration(kname) if kname in KERNEL_SOURCES else None
     launch_iters = tot_it / len(kms)
+    choice = h.launch_choice()
     h.destroy()
     ref = _oracle_run("hydro401") if (ITERS_MAX, ITERS_MIN) == EST_ITERS else None
     # ---- the other configurations, each on a bounded sample (rank 0 only)
@@ -743,7 +747,15 @@ def run_ours(args):
             "setup": {"parallelism": f"replicas{ws}" if ws > 1 else "single_gpu",
                       "engine": "single-pass" if single else "auto (three-phase grid kernel)",
                       "partition": (f"measured-cost tuner, {tune_rounds} rounds in warm-up"
-                                    if tune_rounds > 0 else "fixed cost model")},
+                                    if tune_rounds > 0 else "fixed cost model"),
+                      "launch_choice": {
+                          "kernel": klabel, "ctas": choice["grid"],
+                          "source": {0: "not tuned", 1: "timed trials in the warm-up",
+                                     2: "cached for this matrix"}[choice["source"]],
+                          "trials_ms_40_iterations": [
+                              {"kernel": {0: "three-phase", 1: "merged-phase",
+                                          6: "single-pass"}.get(k, str(k)),
+                               "ctas": g, "ms": round(t, 4)} for k, g, t in choice["trials"]]}},
             "kappa_estimates_per_s": ws * args.steps / (ms / 1e3),
             "result": {"sigma_max": r["sigma_max"], "sigma_min_direct": r["sigma_min"],
                        "kappa_direct": r["kappa"], "kappa_note": KAPPA_NOTE,
@@ -755,10 +767,7 @@ def run_ours(args):
                                                           if ref else None}},
             "roofline": {"bound": "alu", "achieved": achieved_f, "peak": fp64_peak,
                          "unit": "TFLOP/s", "frac": achieved_f / fp64_peak, "traffic": traffic,
-                         "kernel": ("k_merged<0, true, 2>, double-float" if df else
-                                    "k_single<0>, FP64 single-pass" if single else
-                                    "k_persistent<0, 0, 0>, FP64") +
-                                   " (per-launch CUDA events on its stream)",
+                         "kernel": klabel + " (per-launch CUDA events on its stream)",
                          "peak_source": f"FP64 pipe: 2 FMA lanes/SM/clock x {_sm_count()} SMs x 2 "
                                         "flops x median SM clock under load (derived)",
                          "flops_per_iteration": F, "iterations_per_launch": launch_iters,

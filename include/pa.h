@@ -131,6 +131,13 @@ typedef struct {
                        equal measured busy time (per-CTA timers of that run),
                        and after run `autotune` keep the fastest of the
                        partitions those runs used (cost-model start included);
+                       before the first FP64 run of at least 20 iterations
+                       on the AUTO engine with more than 16 CTAs and no
+                       explicit grid_blocks, time 40-iteration trials of the
+                       three-phase kernel with two and with one CTA per SM,
+                       the merged-phase kernel and the single-pass kernel,
+                       and keep the fastest (cached per matrix signature for
+                       later handles; see pa_launch_choice);
                        and when this handle is the first of a
                        pa_estimate_batched call, time short trials of the
                        batch with restart blocks of 8, 4 and 2 vectors and
@@ -317,6 +324,14 @@ pa_status pa_continue(pa_handle h, int iters, double lr, double beta1, double be
  * Builds the plans on first use (square matrices with rows of at most 255
  * entries; PA_ERR_UNSUPPORTED otherwise). */
 pa_status pa_spmv_ata(pa_handle h, const double* x, double* z, int ptr_kind);
+
+/* The launch-shape tuner's choice (see the autotune option), into out[4]
+ * (host): kernel (-1 none yet; 0 three-phase, 1 merged-phase, 6 single-pass,
+ * as in pa_last_run_info), CTAs, source (0 none, 1 this handle's trials,
+ * 2 an earlier handle of a matrix with the same signature) and the number of
+ * trial candidates (at most 4).  cand (8 entries, kernel and CTAs per
+ * candidate) and ms (4 entries, each trial's time) may be NULL. */
+pa_status pa_launch_choice(pa_handle h, int64_t* out, int64_t* cand, double* ms);
 
 /* The single-pass engine's plan sizes, into out[6] (host): CTAs it was built
  * for (0 before first use), window columns over all CTAs (halo slots), plan

@@ -9,7 +9,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <climits>
+#include <mutex>
 #include <string>
 #include <chrono>
 #include <map>
@@ -186,6 +188,13 @@ struct pa_ctx {
   uint32_t* sp_ent = nullptr;
   double* sp_halo = nullptr;
   int64_t sp_window_cols = 0, sp_plan_entries = 0, sp_plan_slots = 0, sp_groups = 0;
+  // the launch-shape tuner's choice for plain FP64 runs of the AUTO engine:
+  // kernel (0 three-phase, 1 merged-phase, 6 single-pass) and CTAs; source 1
+  // = this handle's trials, 2 = the cache of an earlier handle of the same
+  // matrix; the trial candidates and their times
+  int launch_kernel = -1, launch_G = 0, launch_source = 0;
+  std::vector<std::array<int, 2>> launch_cands;
+  std::vector<double> launch_ms;
 };
 
 static void* dev_alloc(pa_ctx* h, size_t bytes) {
@@ -1210,6 +1219,81 @@ static pa_status mixed_max_run(pa_ctx* h, int iters, double b1, double b2, doubl
   return (pa_status)out->status;
 }
 
+// The launch-shape tuner (autotune > 0, plain FP64 runs of the AUTO engine
+// on a grid of more than 16 CTAs, no explicit grid size): short timed runs
+// of the three-phase kernel with two and with one CTA per SM, the
+// merged-phase kernel and the single-pass kernel (when the matrix suits it),
+// each from x_init; the fastest is kept for the handle and, under the
+// matrix's structural signature, for later handles of the same matrix.
+// The choice sets the order of the reductions, like the partition tuner.
+static std::mutex g_launch_mu;
+static std::map<std::array<int64_t, 6>, std::array<int, 2>> g_launch_cache;
+
+static pa_status tune_launch(pa_ctx* h, pa_mode mode, int iters, double b1, double b2, double eps,
+                             int Gdef, int maxG) {
+  if (h->launch_kernel >= 0) return PA_OK;
+  const std::array<int64_t, 6> key = {h->n_rows, h->n_cols, h->nnz, h->sa.n_slices,
+                                      h->a_entries, h->t_entries};
+  {
+    std::lock_guard<std::mutex> lk(g_launch_mu);
+    auto it = g_launch_cache.find(key);
+    if (it != g_launch_cache.end()) {
+      h->launch_kernel = it->second[0];
+      h->launch_G = it->second[1];
+      h->launch_source = 2;
+      return PA_OK;
+    }
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  std::vector<std::array<int, 2>> cands = {{0, Gdef}};
+  if (Gdef > sms && sms > 16) cands.push_back({0, sms});
+  const int gm = merged_max_blocks(h->opt.loss, false);
+  if (gm > 16) cands.push_back({1, std::min(Gdef, gm)});
+  const int gs = single_max_blocks(h->opt.loss);
+  if (h->n_rows == h->n_cols && gs > 16) cands.push_back({6, std::min(Gdef, gs)});
+  const int trial = std::min(iters, 40);
+  cudaError_t e;
+  for (cudaEvent_t& ev : h->tune_ev)
+    if (!ev && (e = cudaEventCreate(&ev))) return cuda_fail(e, "creating the tuner's events");
+  h->launch_cands.clear();
+  h->launch_ms.clear();
+  double best = INFINITY;
+  std::array<int, 2> pick = cands[0];
+  for (const auto& c : cands) {
+    pa_status st;
+    if ((st = ensure_partitions(h, c[1]))) return st;
+    if (c[0] == 6 && (st = ensure_single(h, c[1]))) {
+      if (st != PA_ERR_UNSUPPORTED) return st;
+      g_err.clear();  // the single-pass engine does not take this matrix
+      continue;
+    }
+    RunState rs{};
+    float ms = 0.f;
+    if ((e = cudaEventRecord(h->tune_ev[0], h->stream))) return cuda_fail(e, "timing a trial");
+    if ((st = fp64_run(h, mode, trial, 0, true, false, b1, b2, eps, c[1], maxG, nullptr, nullptr,
+                       0, &rs, false, c[0])))
+      return st;
+    if ((e = cudaEventRecord(h->tune_ev[1], h->stream)) ||
+        (e = cudaEventSynchronize(h->tune_ev[1])) ||
+        (e = cudaEventElapsedTime(&ms, h->tune_ev[0], h->tune_ev[1])))
+      return cuda_fail(e, "timing a trial");
+    h->launch_cands.push_back(c);
+    h->launch_ms.push_back(ms);
+    if (ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  h->launch_kernel = pick[0];
+  h->launch_G = pick[1];
+  h->launch_source = 1;
+  std::lock_guard<std::mutex> lk(g_launch_mu);
+  g_launch_cache[key] = pick;
+  return PA_OK;
+}
+
 // One Algorithm 1 run from the device vector h->Xinit.
 static pa_status run_one(pa_ctx* h, pa_mode mode, int iters, double lr, double b1, double b2,
                          double eps, double* L_trace_dev, double* x_trace_dev, int n_trace,
@@ -1248,27 +1332,37 @@ static pa_status run_one(pa_ctx* h, pa_mode mode, int iters, double lr, double b
     }
   }
   pa_status st;
-  if ((st = ensure_partitions(h, G)) || (st = ensure_bias(h, iters, lr, b1, b2, eps))) return st;
-  if (single && (st = ensure_single(h, G))) return st;
+  if ((st = ensure_bias(h, iters, lr, b1, b2, eps))) return st;
+  // the merged-phase kernel in double-float for PA_DF64 (when the matrix
+  // fits it) and in FP64 on request; the single-pass kernel on request;
+  // the launch-shape tuner's choice for tuned plain FP64 runs; otherwise the
+  // three-phase kernel
+  int kernel = 0;
+  if (single) kernel = 6;
+  else if (!cluster && !mixed) {
+    if (h->opt.precision == PA_DF64 && h->df_ok) kernel = 2;
+    else if (h->opt.engine == PA_ENGINE_MERGED) kernel = 1;
+    else if (h->opt.precision == PA_FP64 && h->opt.engine == PA_ENGINE_AUTO &&
+             h->opt.autotune > 0 && iters >= 20 &&
+             h->opt.grid_blocks == 0 && h->opt.debug_skip_arrival == 0) {
+      if ((st = tune_launch(h, mode, iters, b1, b2, eps, G, maxG))) return st;
+      kernel = h->launch_kernel;
+      G = h->launch_G;
+    }
+  }
+  if ((st = ensure_partitions(h, G))) return st;
+  if (kernel == 6 && (st = ensure_single(h, G))) return st;
   if (mixed && mode == PA_SIGMA_MAX) {
     h->cont.valid = false;
     if ((st = mixed_max_run(h, iters, b1, b2, eps, G, maxG, L_trace_dev, out)) < 0) return st;
   } else {
-    const bool tuning = !cluster && !mixed && !single && h->opt.autotune > 0 &&
+    const bool tuning = !cluster && !mixed && kernel != 6 && h->opt.autotune > 0 &&
                         h->tuned_rounds < h->opt.autotune && iters >= 20;
     cudaError_t e;
     if (tuning) {
       for (cudaEvent_t& ev : h->tune_ev)
         if (!ev && (e = cudaEventCreate(&ev))) return cuda_fail(e, "creating the tuner's events");
       if ((e = cudaEventRecord(h->tune_ev[0], h->stream))) return cuda_fail(e, "timing the run");
-    }
-    // the merged-phase kernel in double-float for PA_DF64 (when the matrix
-    // fits it) and in FP64 on request; otherwise the three-phase kernel
-    int kernel = 0;
-    if (single) kernel = 6;
-    else if (!cluster && !mixed) {
-      if (h->opt.precision == PA_DF64 && h->df_ok) kernel = 2;
-      else if (h->opt.engine == PA_ENGINE_MERGED) kernel = 1;
     }
     if ((st = fp64_run(h, mode, iters, 0, true, mixed, b1, b2, eps, G, maxG, L_trace_dev,
                        x_trace_dev, n_trace, out, cluster, kernel)))
@@ -1307,8 +1401,9 @@ static pa_status run_one(pa_ctx* h, pa_mode mode, int iters, double lr, double b
   else { h->sigma_min = out->sigma; h->have_min = true; h->have_min_direct = true; }
   // the partition tuner learns from plain FP64 grid-engine runs long enough
   // to time (the FP32 and compensated kernels have other cost profiles)
-  if (!cluster && !mixed && !single && h->opt.autotune > 0 && h->tuned_rounds < h->opt.autotune &&
-      iters >= 20 && (st = tune_partitions(h, h->last_run_ms / iters)))
+  if (!cluster && !mixed && h->last_kernel != 6 && h->opt.autotune > 0 &&
+      h->tuned_rounds < h->opt.autotune && iters >= 20 &&
+      (st = tune_partitions(h, h->last_run_ms / iters)))
     return st;
   return (pa_status)out->status;
 }
@@ -1890,6 +1985,23 @@ extern "C" pa_status pa_spmv_ata(pa_handle h, const double* x, double* z, int pt
   dev_free(h, zp);
   dev_free(h, zb);
   if (e != cudaSuccess) return cuda_fail(e, "single-pass product");
+  return PA_OK;
+}
+
+extern "C" pa_status pa_launch_choice(pa_handle h, int64_t* out, int64_t* cand, double* ms) {
+  g_err.clear();
+  if (!h || !out) return fail(PA_ERR_INVALID_ARG, "NULL argument");
+  out[0] = h->launch_kernel;
+  out[1] = h->launch_G;
+  out[2] = h->launch_source;
+  out[3] = (int64_t)h->launch_cands.size();
+  for (size_t i = 0; i < h->launch_cands.size() && i < 4; ++i) {
+    if (cand) {
+      cand[2 * i] = h->launch_cands[i][0];
+      cand[2 * i + 1] = h->launch_cands[i][1];
+    }
+    if (ms) ms[i] = h->launch_ms[i];
+  }
   return PA_OK;
 }
 

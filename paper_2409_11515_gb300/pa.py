@@ -39,7 +39,7 @@ EXPORTS = ("pa_options_default", "pa_create", "pa_estimate", "pa_run", "pa_estim
            "pa_get_vector", "pa_spmv", "pa_spmv_t", "pa_get_transpose", "pa_get_equilibration",
            "pa_kernel_launches", "pa_destroy", "pa_last_error", "pa_set_allocator",
            "pa_last_run_profile", "pa_last_run_info", "pa_continue", "pa_sigma_noalloc", "pa_last_batch_graph", "pa_error_bounds", "pa_attach_lu",
-           "pa_spmv_ata", "pa_single_pass_info")
+           "pa_spmv_ata", "pa_single_pass_info", "pa_launch_choice")
 
 ERROR_BOUND_KEYS = ("residual_norm", "b_norm", "x_hat_norm", "thm1_lower", "thm1_upper",
                     "thm2_lower", "thm2_upper", "thm3_upper", "thm4_rounding", "singular")
@@ -108,6 +108,8 @@ def _declare(L):
     L.pa_spmv_t.argtypes = [vp, vp, vp, C.c_int]
     L.pa_spmv_ata.restype = C.c_int
     L.pa_spmv_ata.argtypes = [vp, vp, vp, C.c_int]
+    L.pa_launch_choice.restype = C.c_int
+    L.pa_launch_choice.argtypes = [vp, vp, vp, vp]
     L.pa_single_pass_info.restype = C.c_int
     L.pa_single_pass_info.argtypes = [vp, vp]
     L.pa_get_transpose.restype = C.c_int
@@ -293,6 +295,16 @@ class Handle:
     def spmv_ata(self, x):
         """pa_spmv_ata: A^T (A x) through the single-pass engine's plans."""
         return self._product(load().pa_spmv_ata, x, self.n_cols)
+
+    def launch_choice(self):
+        """pa_launch_choice: {kernel, grid, source, trials: [(kernel, grid, ms)]}."""
+        out = np.zeros(4, dtype=np.int64)
+        cand = np.zeros(8, dtype=np.int64)
+        ms = np.zeros(4)
+        _check(load().pa_launch_choice(self._h, out.ctypes.data, cand.ctypes.data, ms.ctypes.data))
+        n = int(out[3])
+        return dict(kernel=int(out[0]), grid=int(out[1]), source=int(out[2]),
+                    trials=[(int(cand[2 * i]), int(cand[2 * i + 1]), float(ms[i])) for i in range(n)])
 
     def single_pass_info(self):
         """pa_single_pass_info: {grid, window_cols, plan_entries, plan_slots, groups,
