@@ -489,13 +489,21 @@ def sub_c3(stream, it=(300, 300)):
     from paper_2409_11515_gb300 import pa, synth
     n_mat, k = 64, 8
     mats = synth.hydro_batch(n_mat, 51, 301, seed=3)
-    hs = [pa.create(A, stream=stream, autotune=1 if i == 0 else 0) for i, A in enumerate(mats)]
-    try:
-        pa.estimate_batched(hs, pa.BOTH, k, (5, 5), seed=3, **HYPER)
-        rb, tb = _timed_events(stream, lambda: pa.estimate_batched(hs, pa.BOTH, k, it, seed=3, **HYPER))
-    finally:
-        for h in hs:
-            h.destroy()
+
+    def timed_batch(prec):
+        hs = [pa.create(A, stream=stream, precision=prec, autotune=1 if i == 0 else 0)
+              for i, A in enumerate(mats)]
+        try:
+            pa.estimate_batched(hs, pa.BOTH, k, (5, 5), seed=3, **HYPER)
+            rb, tb = _timed_events(stream, lambda: pa.estimate_batched(hs, pa.BOTH, k, it, seed=3, **HYPER))
+            fb = hs[0].last_run_info()["df_fallbacks"]
+        finally:
+            for h in hs:
+                h.destroy()
+        return rb, tb, fb
+
+    rb, tb, _ = timed_batch(pa.FP64)
+    rd, td, fbd = timed_batch(pa.DF64)
     full_T = EST_ITERS[0] + EST_ITERS[1]
     K = 8
     B = sum(2 * (12 * A.nnz + 4 * (A.n_rows + 1)) + 72 * A.n_cols * K for A in mats)  # per batch iteration
@@ -516,7 +524,9 @@ def sub_c3(stream, it=(300, 300)):
         rows_cpu += A.n_rows
         errs.append({"item": i, "restart": 0, "rows": int(A.n_rows),
                      "sigma_max": abs(rb["sigma_max"][i, 0] / rM.sigma - 1),
-                     "sigma_min": abs(rb["sigma_min"][i, 0] / rm.sigma - 1)})
+                     "sigma_min": abs(rb["sigma_min"][i, 0] / rm.sigma - 1),
+                     "df64_sigma_max": abs(rd["sigma_max"][i, 0] / rM.sigma - 1),
+                     "df64_sigma_min": abs(rd["sigma_min"][i, 0] / rm.sigma - 1)})
     rows = sum(A.n_rows for A in mats)
     # the oracle's seconds per row-iteration, scaled to one estimate of every item
     est_cpu = (t_cpu / (rows_cpu * (it[0] + it[1]))) * rows * k * full_T
@@ -531,6 +541,14 @@ def sub_c3(stream, it=(300, 300)):
                      "frac": ach / hbm_peak, "bytes_per_batch_iteration": B,
                      "fp64_pipe_TFLOPs": F * batch_its / tb / 1e12},
         "rel_err_vs_oracle_sampled": errs,
+        "df64": {"engine": "k_batched_df<8> (double-float products and Adam per column, FP64 "
+                           "reductions)",
+                 "vector_iterations_per_s": n_mat * k * batch_its / td,
+                 "kappa_estimates_per_s": n_mat * k / (td * full_T / batch_its),
+                 "vs_fp64": tb / td, "range_fallbacks": fbd,
+                 "roofline": {"bound": "hbm", "achieved": B * batch_its / td / 1e9,
+                              "peak": hbm_peak, "unit": "GB/s",
+                              "frac": B * batch_its / td / 1e9 / hbm_peak}},
         "cpu_baseline": {"value": n_mat * k / est_cpu, "unit": "estimates/s", "cores": 1,
                          "kind": "oracle",
                          "sample": f"items 0 and 32, restart 0, {it[0]} + {it[1]} iterations "
@@ -809,7 +827,7 @@ def run_batched_workload(args):
     mats = synth.hydro_batch(n_mat, 51, 301, seed=3)
     stream = torch.cuda.Stream()
     mixed = args.precision == "mixed"
-    prec = pa.MIXED if mixed else pa.FP64
+    prec = pa.MIXED if mixed else (pa.DF64 if args.precision == "df64" else pa.FP64)
     # the first handle's autotune picks the restart-block width on a short trial
     hs = [pa.create(A, stream=stream, precision=prec, autotune=1 if i == 0 else 0)
           for i, A in enumerate(mats)]

@@ -160,6 +160,7 @@ struct pa_ctx {
   // PA_DF64: values of 2^-df_k P A Q^T and its transpose as (hi, lo) float
   // pairs, the vectors in the same form, and the bias table as pairs
   bool df_ok = false;     // the matrix's exponent range fits the variant
+  bool df_checked = false;  // the range was measured (and the values split if it fits)
   int df_k = 0;
   float2 *a_val2 = nullptr, *t_val2 = nullptr;
   float2 *XD0 = nullptr, *XD1 = nullptr, *XD2 = nullptr;
@@ -479,7 +480,12 @@ extern "C" pa_status pa_create(pa_handle* out, int32_t n_rows, int32_t n_cols, i
 // whether the double-float variant applies (2^-k A with max |a| in [1/2, 1)
 // must keep every non-zero above 2^-100, so that its low part stays a normal
 // float); if so, the (hi, lo) copies of both sliced matrices and the vectors.
-static pa_status build_df(pa_ctx* h) {
+// The double-float values (PA_DF64): the exponent range of the sliced
+// values decides whether the variant can take the matrix (df_ok); if so, the
+// values of 2^-k P A Q^T and of its transpose as (hi, lo) pairs.  Once per
+// handle; shared by the single-vector and the batched kernels.
+static pa_status build_df_values(pa_ctx* h) {
+  if (h->df_checked) return PA_OK;
   pa_status st;
   int* rng = nullptr;
   if ((st = alloc_n(h, &rng, 2, "exponent range"))) return st;
@@ -493,15 +499,28 @@ static pa_status build_df(pa_ctx* h) {
     return cuda_fail(e, "measuring the value range");
   dev_free(h, rng);
   h->df_ok = false;
+  h->df_checked = true;
   if (h->opt.loss != PA_LOSS_LOGRATIO || got[0] == INT_MIN || got[0] >= 2047 || got[1] < 1 ||
       got[0] - got[1] > 99)
-    return PA_OK;  // runs use the FP64 kernel
+    return PA_OK;  // runs use the FP64 kernels
   h->df_k = got[0] - 1022;  // 2^-k max|a| lies in [1/2, 1)
   if (h->df_k < -400 || h->df_k > 400) return PA_OK;
-  const size_t n = (size_t)std::max(h->n_rows, h->n_cols);
   if ((st = alloc_n(h, &h->a_val2, (size_t)h->a_entries + 32, "values (double-float)")) ||
-      (st = alloc_n(h, &h->t_val2, (size_t)h->t_entries + 32, "values (double-float)")) ||
-      (st = alloc_n(h, &h->XD0, n, "iterate (double-float)")) ||
+      (st = alloc_n(h, &h->t_val2, (size_t)h->t_entries + 32, "values (double-float)")))
+    return st;
+  if ((e = launch_split_df(h->a_entries, h->sa.val, h->df_k, h->a_val2, h->stream, &h->launches)) ||
+      (e = launch_split_df(h->t_entries, h->sq.val, h->df_k, h->t_val2, h->stream, &h->launches)))
+    return cuda_fail(e, "splitting the values");
+  h->df_ok = true;
+  return PA_OK;
+}
+
+// The values and the single-vector kernel's double-float vectors.
+static pa_status build_df(pa_ctx* h) {
+  pa_status st;
+  if ((st = build_df_values(h)) || !h->df_ok) return st;
+  const size_t n = (size_t)std::max(h->n_rows, h->n_cols);
+  if ((st = alloc_n(h, &h->XD0, n, "iterate (double-float)")) ||
       (st = alloc_n(h, &h->XD1, n, "iterate (double-float)")) ||
       (st = alloc_n(h, &h->XD2, n, "iterate (double-float)")) ||
       (st = alloc_n(h, &h->ud, n, "u (double-float)")) ||
@@ -509,10 +528,6 @@ static pa_status build_df(pa_ctx* h) {
       (st = alloc_n(h, &h->vd, n, "second moment (double-float)")) ||
       (st = alloc_n(h, &h->yd, (size_t)std::max(h->n_rows, 1), "A x (double-float)")))
     return st;
-  if ((e = launch_split_df(h->a_entries, h->sa.val, h->df_k, h->a_val2, h->stream, &h->launches)) ||
-      (e = launch_split_df(h->t_entries, h->sq.val, h->df_k, h->t_val2, h->stream, &h->launches)))
-    return cuda_fail(e, "splitting the values");
-  h->df_ok = true;
   return PA_OK;
 }
 
@@ -2163,10 +2178,17 @@ std::vector<int> share_ctas(const std::vector<double>& work, int G) {
 static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_used, int K,
                               int k_restarts, pa_mode mode, const int* iters, double lr, double b1,
                               double b2, double eps, uint64_t seed, double* out,
-                              pa_status* item_status, bool* captured) {
+                              pa_status* item_status, bool* captured, bool allow_df = true) {
   pa_ctx* h0 = hs[0];
   cudaStream_t s = h0->stream;  // replaced below by a capturable stream joined to it
   BatchScratch sc{h0, {}};
+  // PA_DF64: the double-float kernel when every matrix of the wave fits it
+  bool dfb = allow_df && h0->opt.precision == PA_DF64;
+  for (int i = 0; dfb && i < m; ++i) {
+    pa_status sd;
+    if ((sd = build_df_values(hs[i0 + i]))) return sd;
+    dfb = hs[i0 + i]->df_ok;
+  }
   // MIXED: sigma_max runs an FP32 stage (k_batched32) and an FP64 tail
   const bool mixed = h0->opt.precision == PA_MIXED && (mode & PA_SIGMA_MAX);
   const int tail = !mixed ? 0 : (h0->opt.fp64_tail < 0 ? iters[0] / 10 : std::min(h0->opt.fp64_tail, iters[0]));
@@ -2176,6 +2198,7 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
   int Gmax = batched_max_blocks(K);
   if (mixed) Gmax = std::min(Gmax, batched32_max_blocks(K));
   if (dd_min) Gmax = std::min(Gmax, batched_max_blocks(K, true));
+  if (dfb) Gmax = std::min(Gmax, batched_df_max_blocks(K));
   if (Gmax < m) return fail(PA_ERR_LAUNCH, "batched kernel: %d items exceed %d co-resident CTAs", m, Gmax);
   // ---- CTA groups, sized by padded entries plus a per-row weight
   std::vector<double> work(m);
@@ -2202,6 +2225,11 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
     it.t_wp = hi->sq.wp; it.t_col = hi->sq.col; it.t_val = hi->sq.val;
     it.pos_c = hi->sq.pos;
     it.n_slices_a = hi->sa.n_slices;
+    if (dfb) {
+      it.a_val2 = hi->a_val2;
+      it.t_val2 = hi->t_val2;
+      it.s_scale = ldexp(1.0, 2 * hi->df_k);
+    }
     it.cta0 = cta;
     it.ncta = ncta[i];
     for (int c = 0; c < ncta[i]; ++c) cta_item[cta + c] = i;
@@ -2267,6 +2295,17 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
   }
   double2* bias_d = nullptr;
   if ((st = sc.get(&bias_d, tab.size(), "batch bias table"))) return st;
+  // the same constants as double-word pairs: hi = float(K), lo = float(K - hi)
+  std::vector<float4> tab2(dfb ? tab.size() : 0);
+  for (size_t t = 0; t < tab2.size(); ++t) {
+    const float k1 = (float)tab[t].x, k2 = (float)tab[t].y;
+    tab2[t] = make_float4(k1, (float)(tab[t].x - (double)k1), k2, (float)(tab[t].y - (double)k2));
+  }
+  float4* bias2_d = nullptr;
+  if (dfb && (st = sc.get(&bias2_d, tab2.size(), "batch bias table (double-float)"))) return st;
+  if (dfb && (e = cudaMemcpyAsync(bias2_d, tab2.data(), sizeof(float4) * tab2.size(),
+                                  cudaMemcpyHostToDevice, s)))
+    return cuda_fail(e, "uploading the batch tables");
   // tables to the device (pageable host memory: synchronous copies, before capture)
   if ((e = cudaMemcpyAsync(items_d, items.data(), sizeof(BatchItem) * m, cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemcpyAsync(cta_item_d, cta_item.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, s)) ||
@@ -2288,6 +2327,7 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
   bp.w2 = (1.0 - b2) / ((1.0 - b1) * (1.0 - b1));
   bp.beta2 = b2;
   bp.timeout_ns = h0->opt.barrier_timeout_ns;
+  bp.bias2 = bias2_d;
 
   // The whole call as one sequence: start vectors, state reset, the
   // persistent launch, sigma -- for sigma_max, then sigma_min.
@@ -2358,7 +2398,23 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
         q.iters = tail;
       }
       const bool dd = md == PA_SIGMA_MIN && dd_min;
-      if ((err = launch_batched(q, K, G, dd, s, L))) return err;
+      if (dfb) {
+        // x_init and x_min as float pairs in place, the double-float run,
+        // then x_min back to FP64 for the sigma kernel
+        for (int i = 0; i < m; ++i) {
+          const int64_t nx = (int64_t)items[i].n_cols * K;
+          if ((err = launch_split_df(nx, items[i].X0, 0, reinterpret_cast<float2*>(items[i].X0), s, L)) ||
+              (err = launch_split_df(nx, items[i].XMIN, 0, reinterpret_cast<float2*>(items[i].XMIN), s, L)))
+            return err;
+        }
+        if ((err = launch_batched_df(q, K, G, s, L))) return err;
+        for (int i = 0; i < m; ++i)
+          if ((err = launch_join_df((int64_t)items[i].n_cols * K,
+                                    reinterpret_cast<const float2*>(items[i].XMIN), items[i].XMIN, s, L)))
+            return err;
+      } else if ((err = launch_batched(q, K, G, dd, s, L))) {
+        return err;
+      }
       if ((err = launch_batch_sigma(items_d, m, K, blk_item_d, blk_row0_d, nb, 256, blockpart,
                                     item_blk0_d, sig + (md == PA_SIGMA_MAX ? 0 : (size_t)m * K), dd,
                                     s, L)))
@@ -2426,6 +2482,12 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
     int v[3] = {0, 0, 0};
     if ((e = cudaMemcpy(v, items[i].status, sizeof(v), cudaMemcpyDeviceToHost)))
       return cuda_fail(e, "reading the batched status");
+    if (dfb && (v[0] == kStatusDfRange || v[1] == kStatusDfRange || v[2] == kStatusDfRange)) {
+      // a column left the double-float range: the whole wave again in FP64
+      ++h0->df_fallbacks;
+      return batched_wave(hs, i0, m, r0, k_used, K, k_restarts, mode, iters, lr, b1, b2, eps,
+                          seed, out, item_status, captured, false);
+    }
     // the item's status over every launch that ran for it: the first error
     // (< 0), else a warning (> 0), else PA_OK
     int worst = v[0];

@@ -174,6 +174,11 @@ struct BatchItem {
   // FP32 (positions of the sliced copies), and the FP32 block vectors
   const float* a_val32; const float* t_val32; const float* dr32; const float* dc32;
   float *X0f, *X1f, *XMINf, *Mf, *Vf, *DXf, *Yf, *Wf;
+  // PA_DF64 (k_batched_df): the sliced values of 2^-k A and of its
+  // transpose as (hi, lo) float pairs, and 4^k (||A x||^2 = 4^k ||2^-k A x||^2);
+  // the block vectors above are then read as float pairs
+  const float2* a_val2; const float2* t_val2;
+  double s_scale;
 };
 
 struct BatchParams {
@@ -186,6 +191,7 @@ struct BatchParams {
   double beta1, beta2;
   double w2;  // (1 - beta2) / (1 - beta1)^2
   long long timeout_ns;
+  const float4* bias2;       // [iters] the bias constants as (hi, lo) pairs (k_batched_df)
 };
 
 int batched_threads();
@@ -197,6 +203,11 @@ cudaError_t launch_batched(const BatchParams& p, int k, int G, bool dd, cudaStre
 // FP32 Adam state on A_hat, per-column norms reduced in FP64, the same CTA
 // groups, partitions and result layout as k_batched.  Reads X0f (x_init);
 // leaves x_{iters} in X0f (iters even) or X1f, the tracked minimisers in XMINf.
+// The PA_DF64 form of k_batched (log-ratio loss): double-float products and
+// Adam state per column, FP64 reductions; the same groups, partitions and
+// result layout.  Reads X0 and XMIN as float pairs (x_init), M and V zero.
+int batched_df_max_blocks(int k);
+cudaError_t launch_batched_df(const BatchParams& p, int k, int G, cudaStream_t s, int64_t* launches);
 int batched32_max_blocks(int k);
 cudaError_t launch_batched32(const BatchParams& p, int k, int G, cudaStream_t s, int64_t* launches);
 
