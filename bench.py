@@ -962,8 +962,9 @@ def run_stress2001(args):
     1e-22..1e-10, seed 5): 32 seeded restarts as SpMM blocks (k = 8 per
     launch, four waves), mixed precision (sigma_max: FP32 stage + FP64 tail;
     sigma_min: Dot2 products) and plain FP64, against the FP64 and mixed-precision
-    single-vector paths, each on a short timed run (--iters-max/--iters-min,
-    extrapolated to one estimate), plus one full FP64 estimate for kappa_2."""
+    single-vector paths and PA_DF64 (k = 1 and the double-float SpMM at k = 32),
+    each on a short timed run (--iters-max/--iters-min, extrapolated to one
+    estimate), plus one full FP64 estimate for kappa_2."""
     if _dist()[0] > 1:
         raise SystemExit("this workload runs on one GPU (launch it without torchrun)")
     import torch
@@ -1004,20 +1005,27 @@ def run_stress2001(args):
         rd, td = _timed(stream, lambda: (hd.estimate(pa.SIGMA_MAX, it[0], seed=START_SEED, **HYPER),
                                          hd.estimate(pa.SIGMA_MIN, it[1], seed=START_SEED, **HYPER)))
         df_info = hd.last_run_info()
+        pa.estimate_batched([hd], pa.BOTH, 8, (5, 5), seed=START_SEED, **HYPER)  # warm-up
+        rbd, tbd = _timed(stream, lambda: pa.estimate_batched([hd], pa.BOTH, 32, it,
+                                                              seed=START_SEED, **HYPER))
     out["df64_k1_vector_iterations_per_s"] = (it[0] + it[1]) / td
+    out["df64_k32_vector_iterations_per_s"] = 32 * (it[0] + it[1]) / tbd
     kappa = rf[0]["sigma_max"] / rf[1]["sigma_min"]
-    est_k32 = 32 * (it[0] + it[1]) / tbm / full_T
+    est_k32 = 32 * (it[0] + it[1]) / tbd / full_T
     line = {
-        "metric": "kappa2_estimates_per_s (32 restarts, mixed-precision SpMM)", "value": est_k32,
+        "metric": "kappa2_estimates_per_s (32 restarts, double-float SpMM)", "value": est_k32,
         "unit": "estimates/s", "n_gpus": 1, "steps": 1, "warmup": args.warmup,
-        "ms_per_step": 1e3 * tbm, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (seeded hydro-mechanical operator)",
+        "ms_per_step": 1e3 * tbd, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "df64 (2xf32)", "data": "synthetic (seeded hydro-mechanical operator)",
         "config": {"workload": "hydro-mechanical 2001x1001 cells, 12,018,006 rows, viscosity "
                                "contrast 1e8, 32 restarts", "n_rows": int(A.n_rows),
                    "nnz": int(A.nnz), "iters_timed": list(it), "estimate_iters": list(EST_ITERS)},
+        "mixed_k32_estimates_per_s": 32 * (it[0] + it[1]) / tbm / full_T,
         "fp64_k1_estimates_per_s": out["fp64_k1_vector_iterations_per_s"] / full_T,
         "fp64_k32_estimates_per_s": out["fp64_k32_vector_iterations_per_s"] / full_T,
         "df64_k1_estimates_per_s": out["df64_k1_vector_iterations_per_s"] / full_T,
+        "df64_k32_estimates_per_s": out["df64_k32_vector_iterations_per_s"] / full_T,
+        "df64_batched_sigma_max_spread": [float(rbd["sigma_max"].min()), float(rbd["sigma_max"].max())],
         "df64_run_info": df_info,
         "df64_short_run_sigmas": [rd[0]["sigma_max"], rd[1]["sigma_min"]],
         "throughput": out,
@@ -1027,8 +1035,9 @@ def run_stress2001(args):
         "batched_sigma_max_spread": [float(rb["sigma_max"].min()), float(rb["sigma_max"].max())],
         "mixed_batched_sigma_max_spread": [float(rbm["sigma_max"].min()), float(rbm["sigma_max"].max())],
         "note": "value and the k=1 figures extrapolate the timed iterations to the 5000 + 20000 "
-                "of one estimate; mixed precision: sigma_max FP32 stage + FP64 tail, sigma_min "
-                "with Dot2 products (k = 1 and k = 32 alike)",
+                "of one estimate; value: PA_DF64 handles in pa_estimate_batched (k_batched_df, "
+                "four waves of K = 8); mixed precision: sigma_max FP32 stage + FP64 tail, "
+                "sigma_min with Dot2 products (k = 1 and k = 32 alike)",
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_estimate_baseline(A, 10)
