@@ -813,7 +813,7 @@ def run_ours(args):
 def run_batched_workload(args):
     """64 hydro operators with sides drawn from 51..301 (seed 3), 8 restarts
     each, FP64 (or --precision mixed: FP32 sigma_max stage + FP64 tail, Dot2
-    sigma_min): vector-iterations per second of pa_estimate_batched (one
+    sigma_min; --precision df64: the double-float SpMM): vector-iterations per second of pa_estimate_batched (one
     persistent launch sequence per sigma mode, one CUDA graph) against the
     single-vector path looping over the same (matrix, restart) items."""
     if _dist()[0] > 1:
@@ -861,11 +861,13 @@ def run_batched_workload(args):
         h.destroy()
     full_T = EST_ITERS[0] + EST_ITERS[1]
     line = {
-        "metric": "kappa2_estimates_per_s (batched, %s)" % ("mixed precision" if mixed else "FP64"),
+        "metric": "kappa2_estimates_per_s (batched, %s)" % {
+            "mixed": "mixed precision", "df64": "double-float"}.get(args.precision, "FP64"),
         "value": n_mat * k / (tb * full_T / (it[0] + it[1])),
         "unit": "estimates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": tb * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64" if mixed else "f64", "data": "synthetic (seeded hydro-mechanical operators)",
+        "dtype": {"mixed": "f32+f64", "df64": "df64 (2xf32)"}.get(args.precision, "f64"),
+        "data": "synthetic (seeded hydro-mechanical operators)",
         "config": {"workload": "64 hydro operators, sides U[51,301] (seed 3), 8 restarts each, "
                                "one persistent SpMM launch per sigma mode in a CUDA graph",
                    "rows_total": rows, "nnz_total": nnz, "k": k,
