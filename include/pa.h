@@ -230,7 +230,11 @@ pa_status pa_run(pa_handle h, pa_mode mode, int iters, double lr, double beta1, 
  * FP64) for iters[0] - fp64_tail iterations and then the FP64 tail from that
  * state (fp64_tail of the first handle); each item's sigma_max is the larger
  * of the two stages' tracked minimisers scored in FP64; sigma_min runs with
- * Dot2 (compensated) products, as in pa_estimate.  Host outputs:
+ * Dot2 (compensated) products, as in pa_estimate.  With PA_DF64 handles the
+ * products and Adam run in double-float per vector (FP64 reductions), as in
+ * pa_estimate, in blocks of 4 restarts by default; a batch with a matrix
+ * outside the double-float range, or a block whose ||A x|| leaves it, runs
+ * in FP64.  Host outputs:
  *   out[(i * k_restarts + r) * 3 + {0,1,2}] = {sigma_max, sigma_min, kappa}
  *   item_status[i * k_restarts + r]  (may be NULL)
  * mode selects which sigmas run (the others are written as NaN). */

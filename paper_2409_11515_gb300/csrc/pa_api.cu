@@ -2195,10 +2195,10 @@ static pa_status batched_wave(const pa_handle* hs, int i0, int m, int r0, int k_
   const int t32 = iters[0] - tail;
   // ... and sigma_min with Dot2 products, like the single-vector MIXED run
   const bool dd_min = h0->opt.precision == PA_MIXED && (mode & PA_SIGMA_MIN);
-  int Gmax = batched_max_blocks(K);
+  // the co-resident grid of the kernels this wave launches
+  int Gmax = dfb ? batched_df_max_blocks(K) : batched_max_blocks(K);
   if (mixed) Gmax = std::min(Gmax, batched32_max_blocks(K));
   if (dd_min) Gmax = std::min(Gmax, batched_max_blocks(K, true));
-  if (dfb) Gmax = std::min(Gmax, batched_df_max_blocks(K));
   if (Gmax < m) return fail(PA_ERR_LAUNCH, "batched kernel: %d items exceed %d co-resident CTAs", m, Gmax);
   // ---- CTA groups, sized by padded entries plus a per-row weight
   std::vector<double> work(m);
@@ -2676,10 +2676,11 @@ extern "C" pa_status pa_estimate_batched(int n_mat, const pa_handle* handles, pa
     return batched_lu(handles, n_mat, k_restarts, iters[1], lr, beta1, beta2, eps, seed, false, out,
                       item_status);
   }
-  // restart-block width: K = 8 by default; with autotune on the first handle,
-  // the fastest of 8, 4 and 2 on a short trial of this batch (cached per k)
-  int kb = 8;
+  // restart-block width: K = 8 by default (4 for PA_DF64, whose narrower
+  // blocks run three CTAs per SM); with autotune on the first handle, the
+  // fastest of 8, 4 and 2 on a short trial of this batch (cached per k)
   pa_ctx* h0 = handles[0];
+  int kb = h0->opt.precision == PA_DF64 ? 4 : 8;
   if (h0->opt.autotune > 0 && k_restarts >= 2) {
     auto hit = h0->batch_kb.find(k_restarts);
     if (hit != h0->batch_kb.end()) {

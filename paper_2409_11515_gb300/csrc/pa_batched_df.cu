@@ -85,8 +85,10 @@ __device__ __forceinline__ void group_partials(SharedBD<K>& sh, double* part, in
   }
 }
 
+// Two CTAs per SM at K = 8 (128 registers), three at K <= 4 (80 registers):
+// the gathers are latency-bound, so the narrower blocks gain from the third CTA.
 template <int K>
-__global__ void __launch_bounds__(kBTD, 2) k_batched_df(const BatchParams bp) {
+__global__ void __launch_bounds__(kBTD, (K <= 4 ? 3 : 2)) k_batched_df(const BatchParams bp) {
   __shared__ SharedBD<K> sh;
   const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = kBTD / 32;
