@@ -1038,7 +1038,7 @@ def run_stress2001(args):
         "mixed_batched_sigma_max_spread": [float(rbm["sigma_max"].min()), float(rbm["sigma_max"].max())],
         "note": "value and the k=1 figures extrapolate the timed iterations to the 5000 + 20000 "
                 "of one estimate; value: PA_DF64 handles in pa_estimate_batched (k_batched_df, "
-                "four waves of K = 8); mixed precision: sigma_max FP32 stage + FP64 tail, "
+                "restart blocks of the default width K = 4); mixed precision: sigma_max FP32 stage + FP64 tail, "
                 "sigma_min with Dot2 products (k = 1 and k = 32 alike)",
     }
     if not args.no_cpu_baseline:
