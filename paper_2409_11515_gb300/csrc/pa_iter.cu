@@ -37,6 +37,7 @@
 #include <math.h>
 
 #include <cooperative_groups.h>
+#include <type_traits>
 
 #include "pa_device.cuh"
 #include "pa_internal.h"
@@ -64,6 +65,49 @@ struct Shared {
   long long tmark, tc;
 };
 
+// The cluster engine adds two tables of per-warp partial pairs, one slot per
+// (CTA, warp) of the cluster: phase A's (||y||^2, ||x||^2) and phase B's
+// (x.dx, dx.dx).  Every warp writes its pair into the slot of every CTA of
+// the cluster (distributed shared memory) before the cluster barrier, and
+// each CTA then sums its own table in a fixed order: no block barrier and no
+// round trip through global memory on the reduction's path.  Two tables, so
+// that a CTA already writing the next reduction never meets one still being
+// read (a CTA passes the following cluster barrier only after every CTA has
+// finished reading).
+constexpr int kMaxCluster = 16;
+struct SharedCL : Shared {
+  double ctab[2][kMaxCluster * (kBlock / 32)][2];
+};
+
+// Cluster engine: this warp's two partial sums into slot (b, warp) of table
+// `tab` in every CTA of the cluster.
+__device__ __forceinline__ void cluster_scatter(double (*tab)[2], double v0, double v1, int b,
+                                                int warp, int lane, unsigned G) {
+  v0 = warp_sum(v0);
+  v1 = warp_sum(v1);
+  if (lane < (int)G) {
+    double* dst = cooperative_groups::this_cluster().map_shared_rank(&tab[0][0], (unsigned)lane);
+    const int slot = b * (kBlock / 32) + warp;
+    dst[2 * slot] = v0;
+    dst[2 * slot + 1] = v1;
+  }
+}
+
+// Cluster engine: component k of the sum over the table's first n slots, in
+// a fixed order (one warp; loads first, a pairwise tree, then the butterfly).
+__device__ __forceinline__ double cluster_total(const double (*tab)[2], int n, int k) {
+  const int lane = threadIdx.x & 31;
+  double u[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int i = lane + 32 * j;
+    u[j] = i < n ? tab[i][k] : 0.0;
+  }
+  u[0] += u[1]; u[2] += u[3]; u[4] += u[5]; u[6] += u[7];
+  u[0] += u[2]; u[4] += u[6];
+  return warp_sum(u[0] + u[4]);
+}
+
 __device__ __forceinline__ double* pick(const IterParams& p, int k) {
   return k == 0 ? p.X0 : (k == 1 ? p.X1 : p.X2);
 }
@@ -79,7 +123,7 @@ __device__ __forceinline__ double loss_value(int mode, int loss, double s, doubl
 // at cluster scope), for matrices too small to fill the GPU.
 template <int LOSS, bool DD, bool CL>
 __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const IterParams p) {
-  __shared__ Shared sh;
+  __shared__ typename std::conditional<CL, SharedCL, Shared>::type sh;
   constexpr int NW = kBlock / 32;
   const unsigned G = gridDim.x;
   const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -114,8 +158,11 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
 
   const int dlo = p.dep[2 * b], dhi = p.dep[2 * b + 1];
   // every thread reads sh.cur at t = 1: shared memory starts with whatever
-  // the SM's previous launch left there
-  __syncthreads();
+  // the SM's previous launch left there.  The cluster engine waits for the
+  // whole cluster instead: its warps write into the other CTAs' shared
+  // memory, which must have started.
+  if constexpr (CL) cooperative_groups::this_cluster().sync();
+  else __syncthreads();
 
   // per-thread partial of ||x||^2 over the own rows, carried into phase A
   double qloc = 0.0;
@@ -156,10 +203,16 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
           v[0] = fma(yr, yr, v[0]);
         }
       }
-      block_sum_to0<2>(v, sh.scratch);
+      if constexpr (CL) {
+        cluster_scatter(sh.ctab[0], v[0], v[1], b, warp, lane, G);
+      } else {
+        block_sum_to0<2>(v, sh.scratch);
+      }
       if (tid == 0) {
-        part[b * kPartSlots + 0] = v[0];
-        part[b * kPartSlots + 1] = v[1];
+        if (!CL) {
+          part[b * kPartSlots + 0] = v[0];
+          part[b * kPartSlots + 1] = v[1];
+        }
         const long long now = globaltimer_ns();
         sh.busy_a += (unsigned long long)(now - sh.tmark);
         // how late this CTA's y is: phase C, the neighbour wait and phase A
@@ -170,8 +223,14 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
     if (CL) cooperative_groups::this_cluster().sync();
     else if (!grid_barrier(st, target, G, p.timeout_ns, skip, site++, sh.ok)) { status = PA_ERR_TIMEOUT; break; }
     if (tid < 32) {
-      const double s_ = ordered_sum(part, G, kPartSlots, 0);
-      const double q = ordered_sum(part, G, kPartSlots, 1);
+      double s_, q;
+      if constexpr (CL) {
+        s_ = cluster_total(sh.ctab[0], (int)G * NW, 0);
+        q = cluster_total(sh.ctab[0], (int)G * NW, 1);
+      } else {
+        s_ = ordered_sum(part, G, kPartSlots, 0);
+        q = ordered_sum(part, G, kPartSlots, 1);
+      }
       // g' = (1 - beta1) g = ca x + cb z (the first moment's weight folded
       // in): lanes 0 and 1 run one division sequence for both coefficients
       double coef = 0.0;
@@ -269,18 +328,30 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksPerSM) k_persistent(const It
           v[1] = fma(d, d, v[1]);
         }
       }
-      block_sum_to0<2>(v, sh.scratch);
+      if constexpr (CL) {
+        cluster_scatter(sh.ctab[1], v[0], v[1], b, warp, lane, G);
+      } else {
+        block_sum_to0<2>(v, sh.scratch);
+      }
       if (tid == 0) {
-        part[b * kPartSlots + 2] = v[0];
-        part[b * kPartSlots + 3] = v[1];
+        if (!CL) {
+          part[b * kPartSlots + 2] = v[0];
+          part[b * kPartSlots + 3] = v[1];
+        }
         sh.busy_b += (unsigned long long)(globaltimer_ns() - sh.tmark);
       }
     }
     if (CL) cooperative_groups::this_cluster().sync();
     else if (!grid_barrier(st, target, G, p.timeout_ns, false, site++, sh.ok)) { status = PA_ERR_TIMEOUT; break; }
     if (tid < 32) {
-      const double p1 = ordered_sum(part, G, kPartSlots, 2);
-      const double p2 = ordered_sum(part, G, kPartSlots, 3);
+      double p1, p2;
+      if constexpr (CL) {
+        p1 = cluster_total(sh.ctab[1], (int)G * NW, 0);
+        p2 = cluster_total(sh.ctab[1], (int)G * NW, 1);
+      } else {
+        p1 = ordered_sum(part, G, kPartSlots, 2);
+        p2 = ordered_sum(part, G, kPartSlots, 3);
+      }
       if (tid == 0) {
         int brk = 0;
         if (!isfinite(p1) || !isfinite(p2)) {
