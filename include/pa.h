@@ -192,10 +192,14 @@ pa_status pa_estimate(pa_handle h, pa_mode mode, int iters, double lr, double be
  *   column of A that is column j of A Q (int32[n]; NULL = identity).
  *   Host pointers (ptr_kind = PA_HOST) or device pointers (PA_DEVICE); all
  *   are copied, a second call replaces the factors.
- * The host orders each triangular system by dependency level once here; the
- * iteration runs as one CTA that walks the levels (cost per iteration grows
- * with the number of levels, so fill-reducing orderings with short
- * elimination trees run fastest).
+ * The host orders each triangular system by dependency level once here.  The
+ * iteration runs as one CTA that walks the levels while the solve vector fits
+ * its shared memory; past that (engine AUTO) as one thread-block cluster of
+ * 16 CTAs that walks the same levels with the solve vector spread over their
+ * shared memories (up to about 430k rows on GB300); past that on the whole
+ * grid, each row solved as soon as the values it depends on are written.
+ * Engine GRID forces the grid, CLUSTER the cluster (when the vector fits).  The cost per iteration grows with the number of dependency levels,
+ * so fill-reducing orderings with short elimination trees run fastest.
  * Errors: PA_ERR_NOT_SQUARE, PA_ERR_INVALID_ARG (NULL pointers, a factor that
  * is not triangular, has an entry out of range or a zero or missing
  * diagonal, p or q not a permutation), PA_ERR_OOM, PA_ERR_CUDA. */
@@ -348,7 +352,8 @@ pa_status pa_single_pass_info(pa_handle h, int64_t* out);
  *   out[0] kernel: 0 the three-phase grid kernel, 1 the merged-phase grid
  *          kernel in FP64, 2 the merged-phase grid kernel in double-float
  *          (PA_DF64), 3 the cluster kernel, 4 the LU route on one CTA, 5 the
- *          LU route on the grid, 6 the single-pass kernel; -1 before any run;
+ *          LU route on the grid, 6 the single-pass kernel, 7 the LU route on
+ *          one thread-block cluster; -1 before any run;
  *   out[1] iterations of the merged-phase kernel that multiplied x itself
  *          instead of folding the update of x into the product (see the
  *          engine option);

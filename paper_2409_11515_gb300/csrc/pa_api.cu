@@ -19,6 +19,7 @@
 
 #include "pa_device.cuh"
 #include "pa_internal.h"
+#include "pa_lu_cluster.h"
 
 using namespace pa;
 
@@ -119,7 +120,7 @@ struct pa_ctx {
   double* lu_y4 = nullptr;        // the grid kernel's four solve vectors [4][n]
   double* lu_part = nullptr;      // its per-CTA partial sums
   int lu_part_G = 0;
-  int lu_last_kernel = -1;        // 0: one CTA (level steps), 1: the grid (row waits)
+  int lu_last_kernel = -1;        // 0: one CTA (level steps), 1: the grid (row waits), 2: a cluster
   int32_t* lu_p = nullptr;        // row permutation (null = identity)
   std::vector<void*> lu_bufs;     // device arrays of the factors
   double* xmin_lu = nullptr;      // x_min of the latest LU-route run (source order)
@@ -1616,13 +1617,19 @@ static pa_status lu_run(pa_ctx* h, const double* x0, int iters, double lr, doubl
   p.beta2 = b2;
   const size_t smem = lu_layout(&p);
   // one CTA stepping through the levels while the solve vector fits in its
-  // shared memory; past that, the whole grid with per-row waits (engine
-  // GRID / CLUSTER force one or the other)
-  const bool grid = h->opt.engine == PA_ENGINE_GRID ||
-                    (h->opt.engine != PA_ENGINE_CLUSTER && p.smem_mode == 0);
-  h->lu_last_kernel = grid ? 1 : 0;
-  if (grid) {
-    const int G = lu_grid_max_blocks();
+  // shared memory; past that, one cluster with the solve vectors in
+  // distributed shared memory while they fit there, else the whole grid
+  // (engine GRID forces the grid; CLUSTER the cluster when the vectors fit)
+  int lgC = 0, R = 0, C = 0;
+  if (h->opt.engine == PA_ENGINE_CLUSTER ||
+      (h->opt.engine != PA_ENGINE_GRID && p.smem_mode == 0))
+    C = lu_cluster_plan(p.n, &lgC, &R);
+  const bool cluster = C > 0;
+  const bool grid = !cluster && (h->opt.engine == PA_ENGINE_GRID || p.smem_mode == 0 ||
+                                 h->opt.engine == PA_ENGINE_CLUSTER);
+  h->lu_last_kernel = cluster ? 2 : (grid ? 1 : 0);
+  if (grid || cluster) {
+    const int G = cluster ? C : lu_grid_max_blocks();
     if (G <= 0) return fail(PA_ERR_LAUNCH, "the LU grid kernel does not fit on this GPU");
     if (h->lu_part_G < G) {
       if (h->lu_part) dev_free(h, h->lu_part);
@@ -1645,10 +1652,15 @@ static pa_status lu_run(pa_ctx* h, const double* x0, int iters, double lr, doubl
     g.iters = p.iters; g.t0 = p.t0;
     g.beta1 = p.beta1; g.beta2 = p.beta2;
     g.timeout_ns = h->opt.barrier_timeout_ns;
-    if ((e = launch_lu_grid(g, G, h->stream, &h->launches)) ||
+    LuClusterParams cp{};
+    cp.g = g;
+    for (int k = 0; k < 4; ++k) cp.sys[k] = h->lu_sys[k];
+    if ((e = cluster ? launch_lu_cluster(cp, lgC, R, h->stream, &h->launches)
+                     : launch_lu_grid(g, G, h->stream, &h->launches)) ||
         (e = cudaMemcpyAsync(out, h->st, sizeof(RunState), cudaMemcpyDeviceToHost, h->stream)) ||
         (e = cudaStreamSynchronize(h->stream)))
-      return cuda_fail(e, "running the LU route on the grid");
+      return cuda_fail(e, cluster ? "running the LU route on a cluster"
+                                  : "running the LU route on the grid");
   } else {
     if (!h->lu_params && (st = alloc_n(h, &h->lu_params, 1, "LU run parameters"))) return st;
     if ((e = cudaMemcpyAsync(h->lu_params, &p, sizeof(LuParams), cudaMemcpyHostToDevice, h->stream)) ||
@@ -1664,7 +1676,7 @@ static pa_status lu_run(pa_ctx* h, const double* x0, int iters, double lr, doubl
   h->sigma_min = out->sigma;
   h->have_min = true;
   h->have_min_lu = true;
-  h->last_kernel = grid ? 5 : 4;
+  h->last_kernel = cluster ? 7 : (grid ? 5 : 4);
   h->last_refreshes = 0;
   return (pa_status)out->status;
 }

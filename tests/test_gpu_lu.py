@@ -48,9 +48,11 @@ CASES = {
 
 
 # engine AUTO runs these small factors on one CTA (level steps, kernel 4);
-# engine GRID forces the grid kernel with per-row waits (kernel 5)
-@pytest.mark.parametrize("engine,kernel", [(pa.ENGINE_AUTO, 4), (pa.ENGINE_GRID, 5)],
-                         ids=["one_cta", "grid"])
+# engine GRID forces the grid kernel with per-row waits (kernel 5), CLUSTER
+# the cluster kernel with the solve vectors in distributed shared memory (7)
+@pytest.mark.parametrize("engine,kernel", [(pa.ENGINE_AUTO, 4), (pa.ENGINE_GRID, 5),
+                                           (pa.ENGINE_CLUSTER, 7)],
+                         ids=["one_cta", "grid", "cluster"])
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_lu_route_iterates_match_oracle(name, engine, kernel):
     A = CASES[name]()
@@ -74,7 +76,8 @@ def test_lu_route_iterates_match_oracle(name, engine, kernel):
     assert np.linalg.norm(rg["x_min"] - ro.x_min) <= 1e-10
 
 
-@pytest.mark.parametrize("engine", [pa.ENGINE_AUTO, pa.ENGINE_GRID], ids=["auto", "grid"])
+@pytest.mark.parametrize("engine", [pa.ENGINE_AUTO, pa.ENGINE_GRID, pa.ENGINE_CLUSTER],
+                         ids=["auto", "grid", "cluster"])
 @pytest.mark.parametrize("name", ["hydro13", "hydro21"])
 def test_lu_route_kappa_matches_dense_inverse(name, engine):
     """kappa ~ 1e22: Algorithm 2's sigma_min against 1 / sigma_max of the
@@ -189,21 +192,31 @@ def test_batched_lu_needs_factors_on_every_handle():
             h.destroy()
 
 
-def test_lu_grid_route_100k_rows_matches_oracle():
-    """The 129 x 129 operator (99,846 rows; COLAMD factors with about 27M
-    non-zeros and 5,400 levels per system): the solve vector no longer fits
-    in one CTA's shared memory, so the grid kernel runs (per-row waits).
-    Iterates and L_t for t <= 10 and sigma after 10 iterations against the
-    oracle; the run is reproducible."""
+@pytest.fixture(scope="module")
+def hydro129_lu():
     A = synth.hydro_operator(129, seed=7)
     Lf, Uf, p, q = lu_factors(A)
     T = 10
     x0 = oracle.start_vector(A.n_cols, 1)
     ro = oracle.projected_adam_lu(Lf, Uf, p, q, T, x0, n_trace=T, trace_L=True, **HYPER)
-    with pa.create(A) as h:
+    return A, (Lf, Uf, p, q), x0, ro
+
+
+# AUTO: past one CTA's shared memory the cluster kernel (7) takes these
+# factors; GRID forces the grid kernel (5)
+@pytest.mark.parametrize("engine,kernel", [(pa.ENGINE_AUTO, 7), (pa.ENGINE_GRID, 5)],
+                         ids=["cluster", "grid"])
+def test_lu_route_100k_rows_matches_oracle(hydro129_lu, engine, kernel):
+    """The 129 x 129 operator (99,846 rows; COLAMD factors with about 27M
+    non-zeros and 5,400 levels per system): the solve vector no longer fits
+    in one CTA's shared memory.  Iterates and L_t for t <= 10 and sigma after
+    10 iterations against the oracle; the run is reproducible."""
+    A, (Lf, Uf, p, q), x0, ro = hydro129_lu
+    T = 10
+    with pa.create(A, engine=engine) as h:
         h.attach_lu(Lf, Uf, p, q)
         rg = h.run(pa.SIGMA_MIN_LU, T, x0, trace_L=True, n_trace=T, **HYPER)
-        assert h.last_run_info()["kernel"] == 5
+        assert h.last_run_info()["kernel"] == kernel
         rg2 = h.run(pa.SIGMA_MIN_LU, T, x0, **HYPER)
     assert rg["status"] == ro.status == 0
     err_x = np.linalg.norm(rg["x_trace"] - ro.x_trace, axis=1)
