@@ -19,7 +19,7 @@ PA_DF64 and mixed precision -- each with its roofline, its CPU-oracle
 baseline and its errors against the oracle.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload hydro401|hydro21|batched|mixed1001|stress2001|lu64]
+                  [--workload hydro401|hydro21|batched|mixed1001|stress2001|lu64|lu129]
 
 --impl reference times the CPU oracle (the plain serial FP64 program under
 oracle/) on a bounded sample of the same workload.  Under torchrun with N > 1
@@ -652,8 +652,8 @@ def sub_lu129(stream, it_min=100, it_max=2000):
     """The paper's route to kappa_2 at 99,846 rows: the 129 x 129 operator
     (seed 7) with caller-supplied COLAMD LU factors (SuperLU on the host),
     sigma_min by Algorithm 1 on A^{-1} with Algorithm 2's gradient -- the
-    factors (27M non-zeros) too large for one CTA, so the grid kernel with
-    per-row waits runs -- and sigma_max by Algorithm 1; sigma_min's error
+    factors (27M non-zeros) too large for one CTA's shared memory, so the
+    thread-block-cluster kernel runs -- and sigma_max by Algorithm 1; sigma_min's error
     against the oracle's same run, which also gives the CPU baseline."""
     import oracle
     from paper_2409_11515_gb300 import pa, synth
@@ -1228,6 +1228,63 @@ def run_lu64(args):
     return 0
 
 
+def run_lu129(args):
+    """Algorithm 2's route to sigma_min at 99,846 rows: the 129 x 129 hydro
+    operator (seed 7) with caller-supplied COLAMD LU factors (SuperLU on the
+    host, 27M non-zeros), Algorithm 1 on A^{-1}; each step one estimate of
+    --lu-iters iterations on the thread-block-cluster kernel (engine AUTO),
+    the grid kernel's time beside it, and the serial oracle on 5 iterations."""
+    if _dist()[0] > 1:
+        raise SystemExit("this workload runs on one GPU (launch it without torchrun)")
+    import torch
+    from paper_2409_11515_gb300 import build, pa, synth
+    build.build()
+    pa.load()
+    torch.cuda.set_device(0)
+    A = synth.hydro_operator(129, seed=7)
+    f = _lu_factors(A)
+    stream = torch.cuda.Stream()
+    it = args.lu_iters
+    res = {}
+    for name, engine in (("auto", pa.ENGINE_AUTO), ("grid", pa.ENGINE_GRID)):
+        with pa.create(A, stream=stream, engine=engine) as h:
+            h.attach_lu(*f)
+            for _ in range(args.warmup):
+                h.estimate(pa.SIGMA_MIN_LU, it, seed=START_SEED, **HYPER)
+            times = []
+            for _ in range(args.steps):
+                r, dt = _timed_events(stream, lambda: h.estimate(pa.SIGMA_MIN_LU, it,
+                                                                 seed=START_SEED, **HYPER))
+                times.append(dt)
+            res[name] = {"kernel": h.last_run_info()["kernel"],
+                         "ms_per_iteration": 1e3 * sum(times) / (it * len(times)),
+                         "sigma_min": r["sigma_min"]}
+    import oracle
+    oracle.build()
+    x0 = oracle.start_vector(A.n_cols, START_SEED)
+    t0 = time.perf_counter()
+    ro = oracle.projected_adam_lu(*f, 5, x0, **HYPER)
+    t_cpu = (time.perf_counter() - t0) / 5
+    a = res["auto"]
+    nnz_f = int(f[0].nnz + f[1].nnz)
+    line = {
+        "metric": "sigma_min_lu_iterations_per_s", "value": 1e3 / a["ms_per_iteration"],
+        "unit": "iterations/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": a["ms_per_iteration"] * it, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded hydro-mechanical operator)",
+        "config": {"workload": f"hydro 129x129 cells, 99,846 rows, COLAMD LU factors "
+                               f"({nnz_f:,} non-zeros), {it} sigma_min iterations per step "
+                               "through Algorithm 2",
+                   "n_rows": int(A.n_rows), "factor_nnz": nnz_f, "l2": "factors larger than L2"},
+        "engines": res,
+        "cpu_baseline": {"value": 1.0 / t_cpu, "unit": "iterations/s", "cores": 1, "kind": "oracle",
+                         "sample": "5 iterations of the same operator (serial C oracle)"},
+        "oracle_sigma_min_5_iterations": ro.sigma_min,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _start_vector_host(n):
     import oracle
     return oracle.start_vector(n, START_SEED)
@@ -1247,12 +1304,15 @@ def main():
     ap.add_argument("--no-sub", action="store_true",
                     help="skip the bounded runs of the other configurations (C1, C3, C4, DF64)")
     ap.add_argument("--workload", choices=["hydro401", "hydro21", "batched", "mixed1001",
-                                           "stress2001", "lu64"],
+                                           "stress2001", "lu64", "lu129"],
                     default="hydro401",
                     help="hydro401: the benchmark line; hydro21: the small operator (cluster "
                          "engine, LU route); batched: 64 operators x 8 restarts; "
                          "mixed1001: 1001x1001 mixed vs FP64; stress2001: 2001x1001, 32 restarts; "
-                         "lu64: 64 small operators, kappa through the LU route")
+                         "lu64: 64 small operators, kappa through the LU route; "
+                         "lu129: sigma_min through the LU route at 99,846 rows")
+    ap.add_argument("--lu-iters", type=int, default=20,
+                    help="lu129 only: sigma_min iterations per step")
     ap.add_argument("--precision", choices=["fp64", "mixed", "df64"], default="fp64",
                     help="the handles' precision mode: the default workload takes fp64 "
                          "(the benchmark line) or df64; the batched workload fp64 or mixed")
@@ -1281,6 +1341,8 @@ def main():
         return run_stress2001(args)
     if args.workload == "lu64":
         return run_lu64(args)
+    if args.workload == "lu129":
+        return run_lu129(args)
     if args.workload == "hydro21":
         return run_hydro21(args)
     return run_ours(args)

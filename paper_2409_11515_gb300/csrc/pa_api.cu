@@ -121,6 +121,9 @@ struct pa_ctx {
   double* lu_part = nullptr;      // its per-CTA partial sums
   int lu_part_G = 0;
   int lu_last_kernel = -1;        // 0: one CTA (level steps), 1: the grid (row waits), 2: a cluster
+  LcSys lc_sys[4] = {};           // the four systems in the cluster kernel's form
+  LcPlan lc_plan;                 // its cluster, vector slots and staging slots
+  bool lc_ready = false;          // lc_sys built (for lc_plan)
   int32_t* lu_p = nullptr;        // row permutation (null = identity)
   std::vector<void*> lu_bufs;     // device arrays of the factors
   double* xmin_lu = nullptr;      // x_min of the latest LU-route run (source order)
@@ -1430,6 +1433,7 @@ static pa_status free_lu(pa_ctx* h) {
   for (void* b : h->lu_bufs) dev_free(h, b);
   h->lu_bufs.clear();
   h->have_lu = false;
+  h->lc_ready = false;
   h->lu_p = nullptr;
   return PA_OK;
 }
@@ -1554,6 +1558,35 @@ extern "C" pa_status pa_attach_lu(pa_handle h, const int32_t* l_row_ptr, const i
       (st = upload_tri(h, tut, &h->lu_sys[2])) || (st = upload_tri(h, tlt, &h->lu_sys[3])) ||
       (p && (st = upload(h, pp, &h->lu_p, "LU permutation"))))
     return (free_lu(h), st);
+  {  // the cluster kernel's form, where that kernel may run: the solve vector
+     // past one CTA's shared memory, or engine CLUSTER
+    LuParams probe{};
+    probe.n = n;
+    probe.L = h->lu_sys[0];
+    probe.U = h->lu_sys[1];
+    probe.Ut = h->lu_sys[2];
+    probe.Lt = h->lu_sys[3];
+    lu_layout(&probe);
+    if ((h->opt.engine == PA_ENGINE_CLUSTER ||
+         (h->opt.engine != PA_ENGINE_GRID && probe.smem_mode == 0)) &&
+        lu_cluster_plan(n, &h->lc_plan)) {
+      const TriHost* ts[4] = {&tl, &tu, &tut, &tlt};
+      LcHost c;
+      for (int k = 0; k < 4; ++k) {
+        lc_build(*ts[k], h->lc_plan.lgC, h->lc_plan.cap, &c);
+        int4 *stream, *batch;
+        int32_t* bbase;
+        uint8_t* fin0;
+        if ((st = upload(h, c.stream, &stream, "LU cluster steps")) ||
+            (st = upload(h, c.batch, &batch, "LU cluster steps")) ||
+            (st = upload(h, c.bbase, &bbase, "LU cluster steps")) ||
+            (st = upload(h, c.fin0, &fin0, "LU cluster steps")))
+          return (free_lu(h), st);
+        h->lc_sys[k] = LcSys{c.nproc, stream, batch, bbase, fin0, h->lu_sys[k].dinv};
+      }
+      h->lc_ready = true;
+    }
+  }
   {  // the row form for the grid kernel
     TriRowsHost r;
     const int32_t* rps[4] = {lrp.data(), urp.data(), utrp.data(), ltrp.data()};
@@ -1620,11 +1653,9 @@ static pa_status lu_run(pa_ctx* h, const double* x0, int iters, double lr, doubl
   // shared memory; past that, one cluster with the solve vectors in
   // distributed shared memory while they fit there, else the whole grid
   // (engine GRID forces the grid; CLUSTER the cluster when the vectors fit)
-  int lgC = 0, R = 0, C = 0;
-  if (h->opt.engine == PA_ENGINE_CLUSTER ||
-      (h->opt.engine != PA_ENGINE_GRID && p.smem_mode == 0))
-    C = lu_cluster_plan(p.n, &lgC, &R);
-  const bool cluster = C > 0;
+  const bool cluster = h->lc_ready && (h->opt.engine == PA_ENGINE_CLUSTER ||
+                                       (h->opt.engine != PA_ENGINE_GRID && p.smem_mode == 0));
+  const int C = cluster ? 1 << h->lc_plan.lgC : 0;
   const bool grid = !cluster && (h->opt.engine == PA_ENGINE_GRID || p.smem_mode == 0 ||
                                  h->opt.engine == PA_ENGINE_CLUSTER);
   h->lu_last_kernel = cluster ? 2 : (grid ? 1 : 0);
@@ -1654,8 +1685,8 @@ static pa_status lu_run(pa_ctx* h, const double* x0, int iters, double lr, doubl
     g.timeout_ns = h->opt.barrier_timeout_ns;
     LuClusterParams cp{};
     cp.g = g;
-    for (int k = 0; k < 4; ++k) cp.sys[k] = h->lu_sys[k];
-    if ((e = cluster ? launch_lu_cluster(cp, lgC, R, h->stream, &h->launches)
+    for (int k = 0; k < 4; ++k) cp.sys[k] = h->lc_sys[k];
+    if ((e = cluster ? launch_lu_cluster(cp, h->lc_plan, h->stream, &h->launches)
                      : launch_lu_grid(g, G, h->stream, &h->launches)) ||
         (e = cudaMemcpyAsync(out, h->st, sizeof(RunState), cudaMemcpyDeviceToHost, h->stream)) ||
         (e = cudaStreamSynchronize(h->stream)))

@@ -3,7 +3,8 @@ against the library's pa_lu.cu with nvcc (a host program: no GPU needed) and
 runs it.  The program replays the step schedule on the CPU, lanes and
 butterflies included, and compares it with plain substitution on random
 triangular factors (1e-12), checks the staging windows against the padded
-arrays and that malformed factors are rejected."""
+arrays, that malformed factors are rejected, and the cluster kernel's form of
+each system (lc_build): split by owning CTA, replayed against substitution."""
 import shutil
 import subprocess
 from pathlib import Path
@@ -21,7 +22,8 @@ def test_step_schedule_replays_substitution(tmp_path):
     cmd = [nvcc, "-std=c++17", "-O1", "-gencode", "arch=compute_103a,code=sm_103a",
            "-I", str(ROOT / "include"), "-I", str(ROOT / "paper_2409_11515_gb300" / "csrc"),
            str(ROOT / "tests" / "lu_schedule_check.cu"),
-           str(ROOT / "paper_2409_11515_gb300" / "csrc" / "pa_lu.cu"), "-o", str(exe)]
+           str(ROOT / "paper_2409_11515_gb300" / "csrc" / "pa_lu.cu"),
+           str(ROOT / "paper_2409_11515_gb300" / "csrc" / "pa_lu_cluster.cu"), "-o", str(exe)]
     r = subprocess.run(cmd, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
