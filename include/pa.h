@@ -192,14 +192,17 @@ pa_status pa_estimate(pa_handle h, pa_mode mode, int iters, double lr, double be
  *   column of A that is column j of A Q (int32[n]; NULL = identity).
  *   Host pointers (ptr_kind = PA_HOST) or device pointers (PA_DEVICE); all
  *   are copied, a second call replaces the factors.
- * The host orders each triangular system by dependency level once here.  The
- * iteration runs as one CTA that walks the levels while the solve vector fits
- * its shared memory; past that (engine AUTO) as one thread-block cluster of
- * 16 CTAs that walks the same levels with the solve vector spread over their
- * shared memories (up to about 430k rows on GB300); past that on the whole
- * grid, each row solved as soon as the values it depends on are written.
- * Engine GRID forces the grid, CLUSTER the cluster (when the vector fits).  The cost per iteration grows with the number of dependency levels,
- * so fill-reducing orderings with short elimination trees run fastest.
+ * The host orders each triangular system by dependency level once here.  With
+ * engine AUTO the iteration runs as one CTA that walks the levels while the
+ * factors have fewer than 8,192 rows and the solve vector fits its shared
+ * memory; past that as one thread-block cluster of 16 CTAs that walks the
+ * same levels, each CTA applying the entries of the rows it holds (the solve
+ * vector spread over their shared memories, up to about 430k rows on GB300);
+ * past that on the whole grid, each row solved as soon as the values it
+ * depends on are written.  Engine GRID forces the grid, CLUSTER the cluster
+ * (when the vector fits).  The cost per iteration grows with the number of
+ * dependency levels, so fill-reducing orderings with short elimination trees
+ * run fastest.
  * Errors: PA_ERR_NOT_SQUARE, PA_ERR_INVALID_ARG (NULL pointers, a factor that
  * is not triangular, has an entry out of range or a zero or missing
  * diagonal, p or q not a permutation), PA_ERR_OOM, PA_ERR_CUDA. */
@@ -346,6 +349,15 @@ pa_status pa_launch_choice(pa_handle h, int64_t* out, int64_t* cand, double* ms)
  * entries (one per non-zero), plan slots (entries plus the padding of the
  * 32-column groups), groups, and padded entries of the sliced copy of A. */
 pa_status pa_single_pass_info(pa_handle h, int64_t* out);
+
+/* The route the LU route's next run takes for the attached factors (Algorithm
+ * 2; see pa_attach_lu), into out[4] (host): route (0 one CTA, 1 the grid,
+ * 2 a thread-block cluster), the cluster's CTAs, its staging-slot records,
+ * and 1 when its CTAs also keep the rows' final values (steps then end
+ * without memory ordering) or 0 when its steps end with a release barrier;
+ * the last three are 0 for the other routes.
+ * Errors: PA_ERR_INVALID_ARG (NULL argument, no factors attached). */
+pa_status pa_lu_route_info(pa_handle h, int64_t* out);
 
 /* Facts about the handle's latest single-vector run (pa_estimate, pa_run),
  * into out[4] (host):

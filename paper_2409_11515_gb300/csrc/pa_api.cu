@@ -124,6 +124,7 @@ struct pa_ctx {
   LcSys lc_sys[4] = {};           // the four systems in the cluster kernel's form
   LcPlan lc_plan;                 // its cluster, vector slots and staging slots
   bool lc_ready = false;          // lc_sys built (for lc_plan)
+  int lu_route = 0;               // the route of the next LU run: 0 one CTA, 1 grid, 2 cluster
   int32_t* lu_p = nullptr;        // row permutation (null = identity)
   std::vector<void*> lu_bufs;     // device arrays of the factors
   double* xmin_lu = nullptr;      // x_min of the latest LU-route run (source order)
@@ -1491,6 +1492,14 @@ static pa_status upload_tri(pa_ctx* h, const TriHost& t, TriSys* out) {
   return PA_OK;
 }
 
+// Whether the LU route runs on a cluster (once its form is built): engine
+// CLUSTER, or AUTO when the solve vector does not fit one CTA's shared memory
+// or the factors have kLuClusterMinRows rows or more.
+static bool lu_on_cluster(const pa_ctx* h, const LuParams& p) {
+  return h->opt.engine == PA_ENGINE_CLUSTER ||
+         (h->opt.engine != PA_ENGINE_GRID && (p.smem_mode == 0 || p.n >= kLuClusterMinRows));
+}
+
 static bool is_permutation(const std::vector<int32_t>& p, int32_t n) {
   std::vector<char> seen((size_t)n, 0);
   for (int32_t v : p) {
@@ -1558,8 +1567,7 @@ extern "C" pa_status pa_attach_lu(pa_handle h, const int32_t* l_row_ptr, const i
       (st = upload_tri(h, tut, &h->lu_sys[2])) || (st = upload_tri(h, tlt, &h->lu_sys[3])) ||
       (p && (st = upload(h, pp, &h->lu_p, "LU permutation"))))
     return (free_lu(h), st);
-  {  // the cluster kernel's form, where that kernel may run: the solve vector
-     // past one CTA's shared memory, or engine CLUSTER
+  {  // the cluster kernel's form, where that kernel may run (lu_on_cluster)
     LuParams probe{};
     probe.n = n;
     probe.L = h->lu_sys[0];
@@ -1567,9 +1575,7 @@ extern "C" pa_status pa_attach_lu(pa_handle h, const int32_t* l_row_ptr, const i
     probe.Ut = h->lu_sys[2];
     probe.Lt = h->lu_sys[3];
     lu_layout(&probe);
-    if ((h->opt.engine == PA_ENGINE_CLUSTER ||
-         (h->opt.engine != PA_ENGINE_GRID && probe.smem_mode == 0)) &&
-        lu_cluster_plan(n, &h->lc_plan)) {
+    if (lu_on_cluster(h, probe) && lu_cluster_plan(n, &h->lc_plan)) {
       const TriHost* ts[4] = {&tl, &tu, &tut, &tlt};
       LcHost c;
       for (int k = 0; k < 4; ++k) {
@@ -1586,6 +1592,12 @@ extern "C" pa_status pa_attach_lu(pa_handle h, const int32_t* l_row_ptr, const i
       }
       h->lc_ready = true;
     }
+    h->lu_route = h->lc_ready && lu_on_cluster(h, probe)
+                      ? 2
+                      : (h->opt.engine == PA_ENGINE_GRID || probe.smem_mode == 0 ||
+                                 h->opt.engine == PA_ENGINE_CLUSTER
+                             ? 1
+                             : 0);
   }
   {  // the row form for the grid kernel
     TriRowsHost r;
@@ -1649,15 +1661,14 @@ static pa_status lu_run(pa_ctx* h, const double* x0, int iters, double lr, doubl
   p.beta1 = b1;
   p.beta2 = b2;
   const size_t smem = lu_layout(&p);
-  // one CTA stepping through the levels while the solve vector fits in its
-  // shared memory; past that, one cluster with the solve vectors in
-  // distributed shared memory while they fit there, else the whole grid
-  // (engine GRID forces the grid; CLUSTER the cluster when the vectors fit)
-  const bool cluster = h->lc_ready && (h->opt.engine == PA_ENGINE_CLUSTER ||
-                                       (h->opt.engine != PA_ENGINE_GRID && p.smem_mode == 0));
+  // the route chosen when the factors were attached (h->lu_route): one CTA
+  // stepping through the levels while the solve vector fits in its shared
+  // memory and the factors are small; past that, one cluster with the solve
+  // vector in distributed shared memory while it fits there, else the whole
+  // grid (engine GRID forces the grid; CLUSTER the cluster when the vector
+  // fits)
+  const bool cluster = h->lu_route == 2, grid = h->lu_route == 1;
   const int C = cluster ? 1 << h->lc_plan.lgC : 0;
-  const bool grid = !cluster && (h->opt.engine == PA_ENGINE_GRID || p.smem_mode == 0 ||
-                                 h->opt.engine == PA_ENGINE_CLUSTER);
   h->lu_last_kernel = cluster ? 2 : (grid ? 1 : 0);
   if (grid || cluster) {
     const int G = cluster ? C : lu_grid_max_blocks();
@@ -2072,6 +2083,18 @@ extern "C" pa_status pa_single_pass_info(pa_handle h, int64_t* out) {
   out[3] = h->sp_plan_slots;
   out[4] = h->sp_groups;
   out[5] = h->a_entries;
+  return PA_OK;
+}
+
+extern "C" pa_status pa_lu_route_info(pa_handle h, int64_t* out) {
+  g_err.clear();
+  if (!h || !out) return fail(PA_ERR_INVALID_ARG, "NULL argument");
+  if (!h->have_lu) return fail(PA_ERR_INVALID_ARG, "no LU factors attached (pa_attach_lu)");
+  const bool cl = h->lu_route == 2;
+  out[0] = h->lu_route;
+  out[1] = cl ? 1 << h->lc_plan.lgC : 0;
+  out[2] = cl ? h->lc_plan.cap : 0;
+  out[3] = cl ? h->lc_plan.fin : 0;
   return PA_OK;
 }
 

@@ -116,16 +116,21 @@ __device__ __noinline__ double lc_poll_slow(uint32_t ra, volatile int* stall) {
     }
   }
 }
-// Column value at cluster address ra: FIN reads the final-value array,
-// waiting for the value; else a plain load (ordered by the step barrier).
+// Column value at cluster address ra, in two parts so that several loads can
+// be in flight before the first is checked: the load (FIN: from the
+// final-value array; else a plain load, ordered by the step barrier), then
+// (FIN) the wait for a value not yet written.
 template <bool FIN>
-__device__ __forceinline__ double lc_col(uint32_t ra, volatile int* stall) {
-  if constexpr (FIN) {
-    const double v = lc_load_relaxed(ra);
+__device__ __forceinline__ double lc_col(uint32_t ra) {
+  if constexpr (FIN) return lc_load_relaxed(ra);
+  else return lc_load(ra);
+}
+template <bool FIN>
+__device__ __forceinline__ double lc_col_ready(double v, uint32_t ra, volatile int* stall) {
+  if constexpr (FIN)
     return __double_as_longlong(v) != kLcUnset ? v : lc_poll_slow(ra, stall);
-  } else {
-    return lc_load(ra);
-  }
+  else
+    return v;
 }
 
 // Element i of the solve vector (slots start at shared address `base`, the
@@ -234,16 +239,37 @@ __device__ __forceinline__ double lc_item(const int4& r, const LcBatch& B, int p
     const int row = r.x & kItemMask;
     *slot = row >> lgC;
     *last = (r.x & kLcLast) != 0;
-    return gl == 0 ? fma(__hiloint2double(r.w, r.z), lc_col<FIN>(lc_elem(base, r.y, lgC), stall),
-                         vec[row >> lgC])
-                   : 0.0;
+    if (gl != 0) return 0.0;
+    const double xr = vec[row >> lgC];
+    const uint32_t ra = lc_elem(base, r.y, lgC);
+    const double xc = lc_col_ready<FIN>(lc_col<FIN>(ra), ra, stall);
+    return fma(__hiloint2double(r.w, r.z), xc, xr);
   }
   *slot = (~r.x) >> lgC;
   *last = r.w != 0;
   double acc = gl == 0 ? vec[(~r.x) >> lgC] : 0.0;
-  for (int e = r.y + gl; e < r.z; e += G) {
+  int e = r.y + gl;
+  // four entries at a time: their loads in flight together, the sum in
+  // entry order
+  for (; e + 3 * G < r.z; e += 4 * G) {
+    int4 q[4];
+    uint32_t ra[4];
+    double c[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q[k] = B.at(pos + e + k * G);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      ra[k] = lc_elem(base, q[k].x, lgC);
+      c[k] = lc_col<FIN>(ra[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      acc = fma(__hiloint2double(q[k].w, q[k].z), lc_col_ready<FIN>(c[k], ra[k], stall), acc);
+  }
+  for (; e < r.z; e += G) {
     const int4 q = B.at(pos + e);
-    acc = fma(__hiloint2double(q.w, q.z), lc_col<FIN>(lc_elem(base, q.x, lgC), stall), acc);
+    const uint32_t ra = lc_elem(base, q.x, lgC);
+    acc = fma(__hiloint2double(q.w, q.z), lc_col_ready<FIN>(lc_col<FIN>(ra), ra, stall), acc);
   }
   return acc;
 }
@@ -265,14 +291,17 @@ __device__ void lc_steps(const LcSys& T, double* vec, double* fin, uint32_t base
   const int4* BT = T.batch + b0;
   bool ok = true;  // every staging wait of this thread succeeded
   if (tid < 32) {  // warp 0: staging
-    int issued = 0;                        // thread 0: batches issued
-    int4 next = make_int4(0, 0, 0, 0);     // thread 0: record of batch `issued`
+    // thread 0: batches issued, and the records of the next two batches
+    // (loaded a refill ahead of their use, so no refill waits for a load)
+    int issued = 0;
+    int4 next = make_int4(0, 0, 0, 0), next2 = next;
     if (tid == 0) {
       for (; issued < min(kLcSlots, nb); ++issued) lc_issue(T, __ldg(BT + issued), rg.u + issued, rg, sh);
       if (issued < nb) {
         next = __ldg(BT + issued);
         lc_prefetch(T, next);
       }
+      if (issued + 1 < nb) next2 = __ldg(BT + issued + 1);
     }
     for (int l = 0; l < np; ++l) {
       asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
@@ -283,10 +312,10 @@ __device__ void lc_steps(const LcSys& T, double* vec, double* fin, uint32_t base
           if (sh.meta[s].y > l) break;
           if (!(ok = lc_wait(&sh.bar[s], (k / kLcSlots - 1) & 1, &sh.stall))) break;
           lc_issue(T, next, k, rg, sh);
-          if (++issued < nb) {  // the next batch into L2 while the slots are busy
-            next = __ldg(BT + issued);
-            lc_prefetch(T, next);
-          }
+          ++issued;
+          next = next2;
+          if (issued < nb) lc_prefetch(T, next);  // into L2 while the slots are busy
+          if (issued + 1 < nb) next2 = __ldg(BT + issued + 1);
         }
       asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
     }

@@ -41,6 +41,12 @@ constexpr int32_t kLcLast = 1 << 30;  // mark of a row's last one-entry item
 // batches of at most cap records.
 void lc_build(const TriHost& t, int lgC, int cap, LcHost* out);
 
+// From this many rows on, engine AUTO runs the LU route on a cluster even
+// where the solve vector fits one CTA's shared memory (GB300, ms per
+// iteration, one CTA against the cluster: 5,766 rows 1.93 / 2.27, 10,086
+// rows 3.70 / 3.34, 19,494 rows 11.2 / 4.9).
+constexpr int kLuClusterMinRows = 8192;
+
 struct LuClusterParams {
   LuGridParams g;  // vectors, reductions and run state (g.sys and g.y unused)
   LcSys sys[4];    // L, U, U^T, L^T

@@ -39,7 +39,7 @@ EXPORTS = ("pa_options_default", "pa_create", "pa_estimate", "pa_run", "pa_estim
            "pa_get_vector", "pa_spmv", "pa_spmv_t", "pa_get_transpose", "pa_get_equilibration",
            "pa_kernel_launches", "pa_destroy", "pa_last_error", "pa_set_allocator",
            "pa_last_run_profile", "pa_last_run_info", "pa_continue", "pa_sigma_noalloc", "pa_last_batch_graph", "pa_error_bounds", "pa_attach_lu",
-           "pa_spmv_ata", "pa_single_pass_info", "pa_launch_choice")
+           "pa_spmv_ata", "pa_single_pass_info", "pa_launch_choice", "pa_lu_route_info")
 
 ERROR_BOUND_KEYS = ("residual_norm", "b_norm", "x_hat_norm", "thm1_lower", "thm1_upper",
                     "thm2_lower", "thm2_upper", "thm3_upper", "thm4_rounding", "singular")
@@ -112,6 +112,8 @@ def _declare(L):
     L.pa_launch_choice.argtypes = [vp, vp, vp, vp]
     L.pa_single_pass_info.restype = C.c_int
     L.pa_single_pass_info.argtypes = [vp, vp]
+    L.pa_lu_route_info.restype = C.c_int
+    L.pa_lu_route_info.argtypes = [vp, vp]
     L.pa_get_transpose.restype = C.c_int
     L.pa_get_transpose.argtypes = [vp, vp, vp, vp]
     L.pa_get_equilibration.restype = C.c_int
@@ -313,6 +315,12 @@ class Handle:
         _check(load().pa_single_pass_info(self._h, out.ctypes.data))
         return dict(grid=int(out[0]), window_cols=int(out[1]), plan_entries=int(out[2]),
                     plan_slots=int(out[3]), groups=int(out[4]), a_entries=int(out[5]))
+
+    def lu_route_info(self):
+        """pa_lu_route_info: {route (0 one CTA, 1 grid, 2 cluster), ctas, cap, fin}."""
+        out = np.zeros(4, dtype=np.int64)
+        _check(load().pa_lu_route_info(self._h, out.ctypes.data))
+        return dict(route=int(out[0]), ctas=int(out[1]), cap=int(out[2]), fin=int(out[3]))
 
     def get_transpose(self):
         rpt = np.empty(self.n_cols + 1, dtype=np.int32)

@@ -62,9 +62,13 @@ def test_lu_route_iterates_match_oracle(name, engine, kernel):
     ro = oracle.projected_adam_lu(Lf, Uf, p, q, T, x0, n_trace=T, trace_L=True, **HYPER)
     with pa.create(A, engine=engine) as h:
         h.attach_lu(Lf, Uf, p, q)
+        ri = h.lu_route_info()
         rg = h.run(pa.SIGMA_MIN_LU, T, x0, trace_L=True, n_trace=T, **HYPER)
         xv = h.get_vector(pa.SIGMA_MIN_LU)
         assert h.last_run_info()["kernel"] == kernel
+    assert ri["route"] == {4: 0, 5: 1, 7: 2}[kernel]
+    if kernel == 7:  # small factors: 16 CTAs keeping the final values
+        assert ri["ctas"] == 16 and ri["fin"] == 1 and ri["cap"] >= 160
     assert rg["status"] == ro.status == 0
     err_x = np.linalg.norm(rg["x_trace"] - ro.x_trace, axis=1)
     err_L = np.abs(rg["L_trace"] - ro.L_trace) / np.maximum(1.0, np.abs(ro.L_trace))
@@ -226,3 +230,45 @@ def test_lu_route_100k_rows_matches_oracle(hydro129_lu, engine, kernel):
     assert rg["t_min"] == ro.t_min
     assert abs(rg["sigma"] / ro.sigma_min - 1) <= 1e-12
     assert np.array_equal(rg2["x_last"], rg["x_last"])
+
+
+def _lu_parity(A, engine, T, route, fin):
+    """The LU route's iterates, L_t and sigma after T iterations against the
+    oracle on A's COLAMD factors, with the route pa_lu_route_info reports."""
+    Lf, Uf, p, q = lu_factors(A)
+    x0 = oracle.start_vector(A.n_cols, 1)
+    ro = oracle.projected_adam_lu(Lf, Uf, p, q, T, x0, n_trace=T, trace_L=True, **HYPER)
+    with pa.create(A, engine=engine) as h:
+        h.attach_lu(Lf, Uf, p, q)
+        ri = h.lu_route_info()
+        assert ri["route"] == route and ri["fin"] == fin, ri
+        rg = h.run(pa.SIGMA_MIN_LU, T, x0, trace_L=True, n_trace=T, **HYPER)
+        assert h.last_run_info()["kernel"] == {0: 4, 1: 5, 2: 7}[route]
+    assert rg["status"] == ro.status == 0
+    err_x = np.linalg.norm(rg["x_trace"] - ro.x_trace, axis=1)
+    err_L = np.abs(rg["L_trace"] - ro.L_trace) / np.maximum(1.0, np.abs(ro.L_trace))
+    assert np.max(err_x) <= 1e-10, np.max(err_x)
+    assert np.max(err_L) <= 1e-10
+    assert rg["t_min"] == ro.t_min
+    assert abs(rg["sigma"] / ro.sigma_min - 1) <= 1e-12
+
+
+def test_lu_route_cluster_from_8192_rows():
+    """The 41 x 41 operator (10,086 rows): the solve vector fits one CTA's
+    shared memory, but from 8,192 rows on engine AUTO takes the cluster
+    (faster there), with the final values kept; smaller factors (5,766 rows)
+    stay on one CTA."""
+    _lu_parity(synth.hydro_operator(41, seed=7), pa.ENGINE_AUTO, 20, route=2, fin=1)
+    A = synth.hydro_operator(31, seed=7)  # 5,766 rows
+    with pa.create(A) as h:
+        h.attach_lu(*lu_factors(A))
+        assert h.lu_route_info() == dict(route=0, ctas=0, cap=0, fin=0)
+
+
+def test_lu_route_214k_rows_release_barrier():
+    """The 189 x 189 operator (214,326 rows; COLAMD factors with about 72M
+    non-zeros): the final-value arrays no longer fit next to the solve vector
+    in the cluster's shared memory, so the cluster's steps end with a release
+    barrier instead.  Iterates, L_t and sigma after 5 iterations against the
+    oracle."""
+    _lu_parity(synth.hydro_operator(189, seed=7), pa.ENGINE_AUTO, 5, route=2, fin=0)
