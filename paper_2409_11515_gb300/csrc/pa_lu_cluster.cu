@@ -64,6 +64,7 @@ struct LcShared {
   double ca, cb, c, inv, q_keep, L_min, L_last;
   int brk, improved, t_min, iters_run, status;
   int stall;                               // a staging wait gave up
+  unsigned done;                           // FIN: steps the item warps have finished (running)
   unsigned long long bar[kLcSlots];        // one mbarrier per staging slot
   int4 meta[kLcSlots];                     // the batch record of each slot
 };
@@ -108,6 +109,7 @@ constexpr long long kLcPollTimeoutNs = 1000000000LL;  // 1 s
 __device__ __noinline__ double lc_poll_slow(uint32_t ra, volatile int* stall) {
   const long long t0 = globaltimer_ns();
   for (int spins = 1;; ++spins) {
+    __nanosleep(16);  // a short pause keeps the polls from crowding the writers' stores
     const double v = lc_load_relaxed(ra);
     if (__double_as_longlong(v) != kLcUnset) return v;
     if ((spins & 15) == 0 && (*stall || globaltimer_ns() - t0 > kLcPollTimeoutNs)) {
@@ -195,7 +197,31 @@ struct LcRing {
   int4* rec;  // [kLcSlots][cap]
   int cap;
   unsigned u;
+  unsigned steps;  // steps of the earlier solves (running, wraps)
 };
+
+// Thread 0 (FIN): wait until the item warps have finished `target` steps
+// (running count).  Gives up after kLcTimeoutNs, sets the stall flag and
+// returns false.
+__device__ __noinline__ bool lc_wait_done(const unsigned* done, unsigned target,
+                                          volatile int* stall) {
+  long long t0 = -1;
+  for (int spins = 0;; ++spins) {
+    unsigned d;
+    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(d) : "r"(lc_saddr(done)) : "memory");
+    if ((int)(d - target) >= 0) return true;
+    if (*stall) return false;
+    if ((spins & 15) == 15) {
+      const long long now = globaltimer_ns();
+      if (t0 < 0) t0 = now;
+      else if (now - t0 > kLcTimeoutNs) {
+        *stall = 1;
+        return false;
+      }
+    }
+    __nanosleep(32);
+  }
+}
 
 // Thread 0: batch record bt (the batch's k-th use of the ring, counted
 // modulo 2 kLcSlots) into slot k mod kLcSlots: its record first, then its
@@ -303,21 +329,36 @@ __device__ void lc_steps(const LcSys& T, double* vec, double* fin, uint32_t base
       }
       if (issued + 1 < nb) next2 = __ldg(BT + issued + 1);
     }
-    for (int l = 0; l < np; ++l) {
-      asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
-      // steps before l are done: refill the slots whose batches ended
+    // refill the slot of the oldest batch once its steps are done
+    auto refill = [&](unsigned k) {
+      lc_issue(T, next, k, rg, sh);
+      ++issued;
+      next = next2;
+      if (issued < nb) lc_prefetch(T, next);  // into L2 while the slots are busy
+      if (issued + 1 < nb) next2 = __ldg(BT + issued + 1);
+    };
+    if constexpr (FIN) {
+      // the item warps report their finished steps in sh.done
       if (tid == 0)
         while (ok && issued < nb) {
           const unsigned k = rg.u + (unsigned)issued, s = k % kLcSlots;
-          if (sh.meta[s].y > l) break;
-          if (!(ok = lc_wait(&sh.bar[s], (k / kLcSlots - 1) & 1, &sh.stall))) break;
-          lc_issue(T, next, k, rg, sh);
-          ++issued;
-          next = next2;
-          if (issued < nb) lc_prefetch(T, next);  // into L2 while the slots are busy
-          if (issued + 1 < nb) next2 = __ldg(BT + issued + 1);
+          ok = lc_wait_done(&sh.done, rg.steps + (unsigned)sh.meta[s].y, &sh.stall) &&
+               lc_wait(&sh.bar[s], (k / kLcSlots - 1) & 1, &sh.stall);
+          if (ok) refill(k);
         }
-      asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
+    } else {
+      for (int l = 0; l < np; ++l) {
+        asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+        // steps before l are done: refill the slots whose batches ended
+        if (tid == 0)
+          while (ok && issued < nb) {
+            const unsigned k = rg.u + (unsigned)issued, s = k % kLcSlots;
+            if (sh.meta[s].y > l) break;
+            if (!(ok = lc_wait(&sh.bar[s], (k / kLcSlots - 1) & 1, &sh.stall))) break;
+            refill(k);
+          }
+        asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
+      }
     }
     // thread 0: the last batches' copies have landed before the slots are
     // reused or the kernel ends
@@ -374,12 +415,14 @@ __device__ void lc_steps(const LcSys& T, double* vec, double* fin, uint32_t base
         pos += 1 + cnt + h.y;
       }
       if constexpr (FIN) {
-        // partial sums stay in this CTA (ordered by the item threads' own
-        // barrier); readers of final values wait for them, so the cluster
-        // barrier only paces the steps
+        // partial sums stay in this CTA, ordered by the item warps' own
+        // barrier; readers of final values wait for them, so the CTAs need
+        // no common barrier per step and each runs as its inputs arrive
         asm volatile("bar.sync 1, %0;" ::"r"(kLcWork) : "memory");
-        asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
-        asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
+        if (tid == 32)  // the step's reads of its slot are done (release)
+          asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(lc_saddr(&sh.done)),
+                       "r"(rg.steps + (unsigned)l + 1u)
+                       : "memory");
       } else {
         // the step's rows are written before the next step reads them
         asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
@@ -387,8 +430,15 @@ __device__ void lc_steps(const LcSys& T, double* vec, double* fin, uint32_t base
       }
     }
   }
-  if constexpr (FIN) __syncthreads();  // the final values are complete in this CTA
+  // FIN: every CTA has finished reading this solve's final values before any
+  // CTA resets them for the next one (the non-aligned form: thread 0 may
+  // come from its refill loop after the rest of its warp)
+  if constexpr (FIN) {
+    asm volatile("barrier.cluster.arrive;" ::: "memory");
+    asm volatile("barrier.cluster.wait;" ::: "memory");
+  }
   rg.u = (rg.u + (unsigned)nb) % (2 * kLcSlots);
+  rg.steps += (unsigned)np;
 }
 
 // Bytes of dynamic shared memory below the vector slots.
@@ -410,6 +460,7 @@ __global__ void __launch_bounds__(kLcThreads, 1) k_lu_cluster(const LuClusterPar
   rg.rec = lc_dyn;
   rg.cap = cap;
   rg.u = 0;
+  rg.steps = 0;
   // this CTA's partial sums, and (FIN) its rows' final values; a solve's
   // result is in res
   double* const lc_vec = reinterpret_cast<double*>(rg.rec + (size_t)kLcSlots * cap);
@@ -424,6 +475,7 @@ __global__ void __launch_bounds__(kLcThreads, 1) k_lu_cluster(const LuClusterPar
     sh.iters_run = 0;
     sh.status = PA_OK;
     sh.stall = 0;
+    sh.done = 0;
     for (int k = 0; k < kLcSlots; ++k) lc_mbar_init(&sh.bar[k]);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
