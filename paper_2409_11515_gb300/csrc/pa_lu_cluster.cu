@@ -17,27 +17,29 @@
 // spread over their shared memories (element i in CTA i mod C, slot i / C),
 // and each CTA applies the items of its own rows: a row's partial sum is
 // read and written in the CTA's own shared memory, only column values come
-// from the other CTAs (distributed shared memory loads).  The hardware
-// cluster barrier paces the steps (80 ns measured without memory ordering).
-// Where shared memory allows, each CTA also keeps its rows' final values in
-// a second array, reset to a marker before every solve and written once, by
-// a row's last item; a column read waits for the marker to go (almost never:
-// the barrier already separates writer and reader), so the barrier needs no
-// release -- measured, a release arrive costs 0.3 to 0.6 us a step, waiting
-// for the staging copies in flight.  Without room for the second array the
-// steps end with a release/acquire barrier instead.  Each CTA's records are
-// one stream of per-step blocks cut into batches; warp 0 copies the next
-// batches into a ring of shared-memory slots with the bulk-copy (TMA)
-// engine and fetches the one after into L2, so no load from global memory is
-// left on a step's path.  Every solve of the chain L t = P x, U u = t,
-// U^T a = u, L^T c = a starts from the previous solve's result at the same
-// index (b_i / T_ii), so one vector serves the whole chain, transformed in
-// place.  Nothing waits on anything but the cluster barrier, the ring's
-// mbarriers and the marked values (each wait bounded in time); every CTA
-// passes the cluster barrier the same number of times.  The reductions are
-// the grid kernel's (fixed orders: runs are reproducible), and every row adds
-// its entries in the single-CTA kernel's order (a segment's lanes may
-// differ).
+// from the other CTAs (distributed shared memory loads).  Where shared
+// memory allows (FIN), each CTA also keeps its rows' final values in a
+// second array, reset to a marker before every solve and written once, by a
+// row's last item.  A column read waits for the marker to go, so no step
+// needs a cluster barrier: each CTA runs its steps, ordered by a barrier of
+// its own item warps, as the column values it reads arrive, and one cluster
+// barrier closes each solve.  Measured on GB300, a release arrive at a
+// per-step cluster barrier cost 0.3 to 0.6 us a step (it waits for the
+// staging copies in flight) against 80 ns without memory ordering.  Without
+// room for the second array every step ends with a release/acquire cluster
+// barrier instead.  Each CTA's records are one stream of per-step blocks
+// cut into batches; warp 0 copies the next batches into a ring of
+// shared-memory slots with the bulk-copy (TMA) engine and fetches the one
+// after into L2, so no load from global memory is left on a step's path.
+// Every solve of the chain L t = P x, U u = t, U^T a = u, L^T c = a starts
+// from the previous solve's result at the same index (b_i / T_ii), so one
+// vector serves the whole chain, transformed in place.  Nothing waits on
+// anything but the cluster and CTA barriers, the ring's mbarriers, the
+// item warps' step count and the marked values (each wait bounded in time);
+// every CTA passes each cluster barrier the same number of times.  The
+// reductions are the grid kernel's (fixed orders: runs are reproducible),
+// and every row adds its entries in the single-CTA kernel's order (a
+// segment's lanes may differ).
 #include <math.h>
 #include <string.h>
 
@@ -300,13 +302,16 @@ __device__ __forceinline__ double lc_item(const int4& r, const LcBatch& B, int p
   return acc;
 }
 
-// T x = b for x holding b / diag on entry (vec: this CTA's slots, base their
-// shared address): the steps, each CTA applying its own rows' items, each
-// step ended by the cluster barrier.  Warp 0 stages: it arrives at a step's
-// barrier without memory ordering (it writes nothing the other CTAs read),
-// then thread 0 refills the slot of a finished batch while the barrier
-// completes.  Warps 1.. apply the items and arrive with release semantics
-// (their stores of the step's rows); every thread's wait acquires.
+// T x = b for x holding b / diag on entry (vec: this CTA's partial sums,
+// fin its final values (FIN), base the shared address column values are read
+// from): the steps, each CTA applying its own rows' items.  Warp 0 stages:
+// thread 0 refills the slot of a batch whose steps are done.  Warps 1..
+// apply the items.  FIN: the item warps end each step with their own CTA
+// barrier and publish the count of finished steps, which thread 0 waits on.
+// Otherwise every step ends with the cluster barrier: warp 0 arrives without
+// memory ordering (it writes nothing the other CTAs read) and refills while
+// the barrier completes; the item warps arrive with release semantics (their
+// stores of the step's rows); every thread's wait acquires.
 template <bool FIN>
 __device__ void lc_steps(const LcSys& T, double* vec, double* fin, uint32_t base, int lgC,
                          LcRing& rg, LcShared& sh) {
